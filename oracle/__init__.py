@@ -1,0 +1,271 @@
+"""CPU oracle of the batched Active-SLAM step -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference
+leg may import this package.  It shares no code with the CUDA path
+(paper_2603_25834_gb300); both only take inputs from the seeded generators in
+paper_2603_25834_gb300.synth.
+
+The arithmetic lives in plain C (aslam_oracle.c, soft_range_oracle.c,
+raycast3d_oracle.c); this module compiles them with gcc and marshals numpy
+arrays through ctypes.  Every function cites the passage it follows in the
+C sources.  Pins: tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SOURCES = ["aslam_oracle.c"]
+_LIB = None
+_LOCK = threading.Lock()
+
+CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-Wall", "-Wno-unused-function"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle sources into oracle/_build/liborc.so (gcc, no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "liborc.so")
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    if not force and os.path.exists(out):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(out) >= newest:
+            return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            _LIB = C.CDLL(build())
+            _declare(_LIB)
+    return _LIB
+
+
+P = C.c_void_p
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class OrcCfg(C.Structure):
+    _fields_ = [
+        ("n_envs", C.c_int32), ("b_max", C.c_int32), ("n_spawn", C.c_int32),
+        ("hit_q", C.c_int32), ("miss_q", C.c_int32), ("clamp_q", C.c_int32),
+        ("t_episode", C.c_int32), ("pad0", C.c_int32), ("seed", C.c_uint64),
+        ("res", C.c_float), ("r_max", C.c_float), ("fov", C.c_float), ("sigma", C.c_float),
+        ("dt", C.c_float), ("v_max", C.c_float), ("w_max", C.c_float), ("d_crash", C.c_float),
+        ("d_full", C.c_float), ("visit_cell", C.c_float),
+        ("logodds_scale", C.c_double),
+        ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
+        ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
+        ("map_w", P), ("map_h", P), ("n_beams", P), ("map_off", P), ("visit_off", P),
+    ]
+
+
+class OrcState(C.Structure):
+    _fields_ = [("gt", P), ("belief", P), ("x", P), ("y", P), ("th", P), ("u_prev", P),
+                ("t", P), ("g", P), ("ep", P), ("done", P), ("visit", P), ("spawn", P)]
+
+
+class OrcOut(C.Structure):
+    _fields_ = [("z", P), ("z_true", P), ("hit", P), ("cnt_h", P), ("cnt_m", P),
+                ("terms", P), ("reward_ent", P), ("reward_comp", P), ("obs", P),
+                ("ray_cells", P), ("gt_cells", P)]
+
+
+N_TERMS = 12
+TERM_NAMES = ["dH", "dcells", "I", "alpha_hug", "r_explore", "r_abs", "r_delta", "R",
+              "collision", "dmin_meas", "dmin_true", "H"]
+
+
+def _declare(L):
+    L.orc_sincosf.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.orc_cos2pi.argtypes = [C.c_float]
+    L.orc_cos2pi.restype = C.c_float
+    L.orc_logf.argtypes = [C.c_float]
+    L.orc_logf.restype = C.c_float
+    L.orc_philox4x32_10.argtypes = [P, P, P]
+    L.orc_gauss.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+    L.orc_gauss.restype = C.c_float
+    L.orc_walk2d.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                             C.c_int32, C.c_int32, P, P, P, C.c_int, C.POINTER(C.c_int)]
+    L.orc_walk2d.restype = C.c_int
+    L.orc_beam_dirs.argtypes = [C.c_int, C.c_double, P, P]
+    L.orc_ray_setup.argtypes = [C.c_float] * 7 + [C.POINTER(C.c_int32)] * 4
+    L.orc_cell_entropy.argtypes = [C.c_double]
+    L.orc_cell_entropy.restype = C.c_double
+    L.orc_map_entropy.argtypes = [P, C.c_int64, C.c_double]
+    L.orc_map_entropy.restype = C.c_double
+    L.orc_visit_dims.argtypes = [C.c_int32, C.c_int32, C.c_float, C.c_float,
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.orc_step2d.argtypes = [C.POINTER(OrcCfg), C.POINTER(OrcState), P, P, C.POINTER(OrcOut)]
+    L.orc_step2d.restype = C.c_int
+
+
+# ---------------------------------------------------------------- scalar helpers
+def sincosf(x):
+    s, c = C.c_float(), C.c_float()
+    lib().orc_sincosf(C.c_float(x), C.byref(s), C.byref(c))
+    return s.value, c.value
+
+
+def cos2pi(u):
+    return lib().orc_cos2pi(C.c_float(u))
+
+
+def logf(u):
+    return lib().orc_logf(C.c_float(u))
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def gauss(seed, env, step, beam):
+    return lib().orc_gauss(C.c_uint64(seed), env, step, beam)
+
+
+def walk2d(Px, Py, Dx, Dy, T, W, H):
+    """Visited in-map cells (flat j*W+i), entry numerators/denominators, left-map flag."""
+    cap = W + H + 8
+    cells = np.zeros(cap, dtype=np.int64)
+    en = np.zeros(cap, dtype=np.int64)
+    ea = np.zeros(cap, dtype=np.int64)
+    left = C.c_int()
+    n = lib().orc_walk2d(Px, Py, Dx, Dy, T, W, H, _ptr(cells), _ptr(en), _ptr(ea), cap,
+                         C.byref(left))
+    return cells[:n].copy(), en[:n].copy(), ea[:n].copy(), bool(left.value)
+
+
+def beam_dirs(B, fov):
+    cb = np.zeros(max(B, 1), dtype=np.float32)
+    sb = np.zeros(max(B, 1), dtype=np.float32)
+    lib().orc_beam_dirs(B, C.c_double(fov), _ptr(cb), _ptr(sb))
+    return cb[:B], sb[:B]
+
+
+def ray_setup(x, y, c, s, cb, sb, res):
+    o = [C.c_int32() for _ in range(4)]
+    lib().orc_ray_setup(x, y, c, s, cb, sb, res, *[C.byref(v) for v in o])
+    return tuple(v.value for v in o)
+
+
+def cell_entropy(l):
+    return lib().orc_cell_entropy(C.c_double(l))
+
+
+def map_entropy(L, scale):
+    L = np.ascontiguousarray(L, dtype=np.int16)
+    return lib().orc_map_entropy(_ptr(L), L.size, C.c_double(scale))
+
+
+def visit_dims(W, H, res, vc):
+    a, b = C.c_int32(), C.c_int32()
+    lib().orc_visit_dims(W, H, C.c_float(res), C.c_float(vc), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------- batched 2-D step
+DEFAULTS = dict(r_max=5.0, fov=0.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0,
+                hit_q=870, miss_q=-410, clamp_q=3584, logodds_scale=1.0 / 1024.0,
+                t_episode=2048, d_crash=0.15, d_full=0.5, visit_cell=0.5,
+                lam_col=10.0, lam_explore=1.0, lam_abs=0.1, lam_delta=1.0, kappa=0.05,
+                u_hi=1.0, seed=20260325)
+
+
+class OracleBatch2D:
+    """Owns the numpy state of E environments and steps them with orc_step2d."""
+
+    def __init__(self, inputs, **params):
+        p = dict(DEFAULTS)
+        p.update(params)
+        self.p = p
+        self.inp = inputs
+        E = inputs.n_envs
+        self.E = E
+        self.map_w = np.ascontiguousarray(inputs.map_w, dtype=np.int32)
+        self.map_h = np.ascontiguousarray(inputs.map_h, dtype=np.int32)
+        self.n_beams = np.ascontiguousarray(inputs.n_beams, dtype=np.int32)
+        self.map_off = np.ascontiguousarray(inputs.map_off, dtype=np.int64)
+        self.b_max = int(self.n_beams.max()) if E else 0
+        dims = [visit_dims(int(w), int(h), inputs.res, p["visit_cell"])
+                for w, h in zip(self.map_w, self.map_h)]
+        self.visit_dims = dims
+        self.visit_off = np.zeros(E + 1, dtype=np.int64)
+        self.visit_off[1:] = np.cumsum([a * b for a, b in dims])
+        self.gt = np.ascontiguousarray(inputs.gt, dtype=np.uint8)
+        self.spawn = np.ascontiguousarray(inputs.spawn, dtype=np.float32)
+        ncell = int(self.map_off[-1])
+        self.belief = np.zeros(ncell, dtype=np.int16)
+        self.x = self.spawn[:, 0, 0].copy()
+        self.y = self.spawn[:, 0, 1].copy()
+        self.th = self.spawn[:, 0, 2].copy()
+        self.u_prev = np.zeros(E, dtype=np.float32)
+        self.t = np.zeros(E, dtype=np.int32)
+        self.g = np.zeros(E, dtype=np.int32)
+        self.ep = np.zeros(E, dtype=np.int32)
+        self.done = np.zeros(E, dtype=np.uint8)
+        self.visit = np.full(int(self.visit_off[-1]), -1, dtype=np.int32)
+        self.cfg = OrcCfg(
+            n_envs=E, b_max=self.b_max, n_spawn=self.spawn.shape[1],
+            hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"],
+            t_episode=p["t_episode"], pad0=0, seed=p["seed"], res=inputs.res,
+            r_max=p["r_max"], fov=p["fov"], sigma=p["sigma"], dt=p["dt"], v_max=p["v_max"],
+            w_max=p["w_max"], d_crash=p["d_crash"], d_full=p["d_full"],
+            visit_cell=p["visit_cell"], logodds_scale=p["logodds_scale"],
+            lam_col=p["lam_col"], lam_explore=p["lam_explore"], lam_abs=p["lam_abs"],
+            lam_delta=p["lam_delta"], kappa=p["kappa"], u_hi=p["u_hi"],
+            map_w=_ptr(self.map_w), map_h=_ptr(self.map_h), n_beams=_ptr(self.n_beams),
+            map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off))
+
+    def _state(self):
+        return OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x),
+                        y=_ptr(self.y), th=_ptr(self.th), u_prev=_ptr(self.u_prev),
+                        t=_ptr(self.t), g=_ptr(self.g), ep=_ptr(self.ep), done=_ptr(self.done),
+                        visit=_ptr(self.visit), spawn=_ptr(self.spawn))
+
+    def step(self, actions, u=None, counts=False):
+        """One step for all envs; returns a dict of this step's outputs."""
+        E, Bm = self.E, self.b_max
+        a = np.ascontiguousarray(actions, dtype=np.float32).reshape(E, 2)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float32).reshape(E)
+        ncell = int(self.map_off[-1])
+        o = dict(z=np.zeros((E, Bm), np.float32), z_true=np.zeros((E, Bm), np.float32),
+                 hit=np.zeros((E, Bm), np.uint8), terms=np.zeros((E, N_TERMS), np.float64),
+                 reward_ent=np.zeros(E, np.float32), reward_comp=np.zeros(E, np.float32),
+                 obs=np.zeros((E, Bm + 2), np.float32), ray_cells=np.zeros(E, np.int64),
+                 gt_cells=np.zeros(E, np.int64))
+        if counts:
+            o["cnt_h"] = np.zeros(ncell, np.int32)
+            o["cnt_m"] = np.zeros(ncell, np.int32)
+        out = OrcOut(z=_ptr(o["z"]), z_true=_ptr(o["z_true"]), hit=_ptr(o["hit"]),
+                     cnt_h=_ptr(o.get("cnt_h")), cnt_m=_ptr(o.get("cnt_m")),
+                     terms=_ptr(o["terms"]), reward_ent=_ptr(o["reward_ent"]),
+                     reward_comp=_ptr(o["reward_comp"]), obs=_ptr(o["obs"]),
+                     ray_cells=_ptr(o["ray_cells"]), gt_cells=_ptr(o["gt_cells"]))
+        st = self._state()
+        rc = lib().orc_step2d(C.byref(self.cfg), C.byref(st), _ptr(a), _ptr(uu), C.byref(out))
+        if rc != 0:
+            raise RuntimeError("orc_step2d failed (%d)" % rc)
+        return o
+
+    def env_belief(self, e):
+        a, b = int(self.map_off[e]), int(self.map_off[e + 1])
+        return self.belief[a:b].reshape(int(self.map_h[e]), int(self.map_w[e]))
