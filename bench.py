@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the batched Active-SLAM environment step on GB300.
+
+Workload (default): 750 envs, each a 256x256 grid at 0.05 m with 20-40
+rectangles and 5-15 discs, 360 beams over 360 deg, 12 m range, Gaussian range
+noise sigma = 0.01 m, int16 log-odds, 1000 steps of random (v, w) actions
+and a synthetic uncertainty signal U_t (composite reward, Eq. 7-17).
+
+A "step" is one call of the whole path (action integration, raycast, log-odds
+update, reward, observation) for all envs: one kernel launch.  Inputs (all
+steps' actions and U_t) are resident in HBM before timing; L2 is flushed
+(256 MiB write) between timed steps, each step is timed with its own CUDA
+event pair on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank steps its own 750 envs (weak scaling, no
+collective on the data path); the max over ranks of the timed total is used.
+`--impl reference` times the CPU oracle (the plain C definition of the
+method) on this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s and ray-cells/s at 750/4096 envs on 1 GB300; % of HBM roofline"
+UNIT = "env-steps/s"
+WORKLOAD = dict(workload="paper_scale: 750 envs x 256^2 cells @0.05 m, 360 beams, 12 m, sigma 0.01 m",
+                envs=750, map_side=256, beams=360, res_m=0.05, r_max_m=12.0, noise_sigma_m=0.01,
+                reward="composite Eq. 7-17", steps_of_actions="random (v,w)",
+                l2="flushed (256 MiB write) between timed steps")
+KERNEL_SOURCES = ["paper_2603_25834_gb300/csrc/step2d.cu",
+                  "paper_2603_25834_gb300/csrc/aslam_internal.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step2d_paper_scale_traffic.json")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(inputs, n_envs, steps, seed_actions=2026):
+    """Env-steps/s of the CPU oracle on the first n_envs envs (single thread)."""
+    import oracle
+    from paper_2603_25834_gb300 import synth
+    sub = synth.subset(inputs, list(range(n_envs)))
+    ob = oracle.OracleBatch2D(sub, r_max=12.0, sigma=0.01)
+    acts = synth.random_actions(steps, n_envs, seed_actions)
+    u = synth.random_uncertainty(steps, n_envs, seed_actions + 1)
+    t0 = time.perf_counter()
+    rc = 0
+    for s in range(steps):
+        o = ob.step(acts[s], u[s])
+        rc += int(o["ray_cells"].sum())
+    dt = time.perf_counter() - t0
+    return n_envs * steps / dt, rc / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2603_25834_gb300 import synth
+    # bounded sample: a few envs of the same workload per step
+    n_sample = 4
+    inp = synth.paper_scale(E=n_sample)
+    import oracle
+    ob = oracle.OracleBatch2D(inp, r_max=12.0, sigma=0.01)
+    total = args.warmup + args.steps
+    acts = synth.random_actions(total, n_sample, 2026)
+    u = synth.random_uncertainty(total, n_sample, 2027)
+    for s in range(args.warmup):
+        ob.step(acts[s], u[s])
+    t0 = time.perf_counter()
+    rc = 0
+    for s in range(args.warmup, total):
+        rc += int(ob.step(acts[s], u[s])["ray_cells"].sum())
+    dt = time.perf_counter() - t0
+    val = n_sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i16+f32", "data": "synthetic", "config": WORKLOAD,
+        "ray_cells_per_s": rc / dt,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d of the 750 envs per step, %d steps, single thread"
+                                   % (n_sample, args.steps)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=750)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2603_25834_gb300 import aslam, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+
+    E = args.envs
+    inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+    batch = aslam.Batch2D(inp, device=dev, r_max_m=12.0, noise_sigma_m=0.01,
+                          reward_mode=aslam.REWARD_COMPOSITE)
+    tuned = None
+    if not args.no_autotune:
+        tuned = batch.autotune()
+    K, W = args.steps, args.warmup
+    acts = torch.from_numpy(synth.random_actions(K + W, E, 7 + rank)).to(dev)
+    uu = torch.from_numpy(synth.random_uncertainty(K + W, E, 8 + rank)).to(dev)
+    reward = torch.empty(E, device=dev)
+    obs = torch.empty(E, batch.b_max + 2, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rc_acc = torch.zeros((), dtype=torch.int64, device=dev)
+    gc_acc = torch.zeros((), dtype=torch.int64, device=dev)
+    st = batch.state()
+    for s in range(W):
+        batch.step_fused(acts[s], uu[s], reward, obs)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.1)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        batch.step_fused(acts[W + k], uu[W + k], reward, obs)
+        ends[k].record(stream)
+        rc_acc += st["ray_cells"].sum()
+        gc_acc += st["gt_cells"].sum()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ray_cells = int(rc_acc.item())
+    gt_cells = int(gc_acc.item())
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    batch.sync_status()
+
+    # ---- graph-captured replay of the same step (reported beside) ----
+    gstream = torch.cuda.Stream(dev)
+    abuf = acts[0].clone()
+    ubuf = uu[0].clone()
+    with torch.cuda.stream(gstream):
+        batch.capture_graph(abuf, ubuf, reward, obs, stream=gstream)
+    torch.cuda.synchronize(dev)
+    gk = min(K, 200)
+    g_ms = 0.0
+    with torch.cuda.stream(gstream):
+        for k in range(gk):
+            abuf.copy_(acts[W + k])
+            ubuf.copy_(uu[W + k])
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(gstream)
+            batch.graph_step(stream=gstream)
+            e1.record(gstream)
+            e1.synchronize()
+            g_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize(dev)
+
+    # ---- end to end through the public API with host buffers ----
+    K2 = min(args.e2e_steps, K)
+    h_acts = torch.from_numpy(synth.random_actions(K2, E, 17 + rank)).pin_memory()
+    h_u = torch.from_numpy(synth.random_uncertainty(K2, E, 18 + rank)).pin_memory()
+    h_rew = torch.empty(K2, E).pin_memory()
+    h_obs = torch.empty(K2, E, batch.b_max + 2).pin_memory()
+    d_a = torch.empty(E, 2, device=dev)
+    d_u = torch.empty(E, device=dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e2e_ms = 0.0
+    for k in range(K2):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_a.copy_(h_acts[k], non_blocking=True)
+        d_u.copy_(h_u[k], non_blocking=True)
+        batch.step_fused(d_a, d_u, reward, obs)
+        h_rew[k].copy_(reward, non_blocking=True)
+        h_obs[k].copy_(obs, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t2.item())
+    h2d = E * 2 * 4 + E * 4
+    d2h = E * 4 + E * (batch.b_max + 2) * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * E * K / (total_ms_max / 1e3)
+    ms_step = total_ms_max / K
+    # Algorithmic bytes of one launch: every updated cell read+written as
+    # int16 (4 B), every ground-truth cell read (1 B), ranges and observation
+    # written, pose/action/reward (24 B per env).
+    B = int(inp.n_beams[0])
+    alg_bytes = (ray_cells * 4 + gt_cells * 1) / K + E * B * 4 + E * (B + 2) * 4 + E * 24
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_hash") == kernel_hash():
+            traffic = tr.get("dram_bytes_per_launch")
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_s, steps_s = 48, 60
+        rate, rcs, dt = oracle_rate(inp, n_s, steps_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d of the %d envs x %d steps (%.1f s), single thread; "
+                         "oracle ray-cells/s %.3g" % (n_s, E, steps_s, dt, rcs)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i16+f32", "data": "synthetic",
+        "config": dict(WORKLOAD, autotuned=({"threads_per_cta": tuned[0], "window_cells": tuned[1]}
+                                            if tuned else None)),
+        "ray_cells_per_s": world * ray_cells / (total_ms_max / 1e3),
+        "ray_cells_per_step": ray_cells / K,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)",
+                     "bytes_per_launch": alg_bytes, "kernel": "step2d_kernel"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * E * K2 / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "graph": {"value": world * E * gk / (g_ms / 1e3), "unit": UNIT, "steps": gk,
+                  "ms_per_step": g_ms / gk},
+        "gpu_launches": K,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

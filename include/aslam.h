@@ -1,0 +1,235 @@
+/*
+ * aslam.h -- C ABI of libaslam, the GB300 (sm_103a) batched Active-SLAM
+ * environment step of "Massive Parallel Deep Reinforcement Learning for
+ * Active SLAM" (arXiv 2603.25834).
+ *
+ * One call advances E independent robots by one control period: action
+ * integration (Eq. 4, Sec. IV-A robot), LiDAR raycasting into each robot's
+ * ground-truth world (Sec. IV-A sensor), the inverse-sensor log-odds update
+ * of each robot's occupancy grid (Sec. III-D), and the per-environment
+ * reward (Sec. III-E, Eq. 7-17; or the map-entropy information gain, Table I
+ * "Map entropy") and observation (Eq. 3).  A differentiable soft-range
+ * raycaster with its adjoint and a batched scan-to-map Gauss-Newton pose
+ * correction (Sec. III-D, Eq. 5-6) sit beside the step.
+ *
+ * Conventions shared by every call:
+ *   - Device pointers ("d_") are CUDA global-memory addresses on the current
+ *     device; host pointers ("h_") are ordinary process memory.  The caller
+ *     owns every buffer it passes; the library never allocates device
+ *     memory (no cudaMalloc) and keeps no pointer to caller buffers beyond
+ *     the call, except the workspace given to aslam_create_batch.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Every call is stream-ordered and asynchronous unless stated.
+ *   - Argument errors are detected before any launch and leave device state
+ *     untouched; the call returns a non-zero status and aslam_last_error()
+ *     gives a message.  Device-side failures set a sticky error word that the
+ *     next aslam_sync_status() returns.
+ *   - A batch is thread-compatible, not thread-safe: calls on one batch must
+ *     not overlap in time from several host threads.
+ *
+ * Grid conventions (both dims): cell (i, j) covers [i*res, (i+1)*res) x
+ * [j*res, (j+1)*res) in metres, flat index j*W + i (3-D: (k*H + j)*W + i);
+ * a ground-truth byte != 0 is occupied.  Beam b of B over a full turn sits
+ * at angle th + b*2*pi/B; over a front arc of width fov at th - fov/2 +
+ * b*fov/(B-1).  Log-odds are int16 in units of logodds_scale (1/1024).
+ */
+#ifndef ASLAM_H
+#define ASLAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aslam_batch aslam_batch;   /* opaque host-side handle */
+
+typedef enum {
+    ASLAM_OK = 0,
+    ASLAM_ERR_INVALID_ARG = 1,   /* a size, pointer or value is out of range */
+    ASLAM_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    ASLAM_ERR_WORKSPACE = 3,     /* workspace missing, misaligned or too small */
+    ASLAM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    ASLAM_ERR_STATE = 5,         /* call not valid in the batch's current state */
+    ASLAM_ERR_UNSUPPORTED = 6,   /* valid request this build does not support */
+    ASLAM_ERR_DEVICE = 7         /* a device-side check failed (sticky error word) */
+} aslam_status;
+
+/* Config flags. */
+#define ASLAM_FLAG_DEBUG   0x1   /* keep per-beam true ranges/hit flags and per-cell counts */
+#define ASLAM_FLAG_CHECKS  0x2   /* extra device-side consistency checks */
+
+/* Reward selection (aslam_reward). */
+#define ASLAM_REWARD_ENTROPY   0  /* H_{t-1} - H_t of the robot's map, nats */
+#define ASLAM_REWARD_COMPOSITE 1  /* Eq. 7 */
+
+/* Per-env reward terms written by aslam_reward_terms, [E, ASLAM_N_TERMS] fp32. */
+#define ASLAM_N_TERMS 12
+/* 0 dH = H_{t-1} - H_t   1 dcells (Eq. 9)    2 I (Eq. 10)     3 alpha_hug (Eq. 15)
+ * 4 R_explore* (Eq. 16)  5 R_abs (Eq. 13)    6 R_delta* (Eq. 17)
+ * 7 R_t (Eq. 7)          8 collision (0/1)   9 d_min of the measured ranges
+ * 10 d_min of the noise-free ranges          11 H_t (nats) */
+
+#define ASLAM_CONFIG_VERSION 1u
+
+/*
+ * Batch configuration (POD).  Fill with aslam_config_init() and override.
+ * The defaults are the values the paper fixes (Sec. IV-A: sigma = 0.01 m,
+ * d_crash = 0.15 m, T_episode = 2048; dt = 0.1 s from "3000 timesteps (5
+ * minutes)") and, where the paper leaves a value open, documented choices.
+ */
+typedef struct {
+    uint32_t struct_size;          /* sizeof(aslam_config) */
+    uint32_t version;              /* ASLAM_CONFIG_VERSION */
+    int32_t n_envs;                /* E >= 1 */
+    int32_t dims;                  /* 2 (3: see aslam3d_*) */
+    int32_t n_spawn;               /* spawn poses per env, >= 1 */
+    int32_t reward_mode;           /* ASLAM_REWARD_* */
+    const int32_t *h_map_w;        /* HOST [E]: grid width W (cells), >= 1 */
+    const int32_t *h_map_h;        /* HOST [E]: grid height H (cells), >= 1 */
+    const int32_t *h_n_beams;      /* HOST [E]: beams B, 0..ASLAM_MAX_BEAMS */
+    float res_m;                   /* cell size (m) */
+    float r_max_m;                 /* max range (m) */
+    float fov_rad;                 /* 0 or >= 2*pi: full turn; else front arc */
+    float noise_sigma_m;           /* range noise std (m) */
+    float dt_s;                    /* control period (s) */
+    float v_max;                   /* |v| clamp, v in [0, v_max] (m/s) */
+    float w_max;                   /* w in [-w_max, w_max] (rad/s) */
+    float d_crash;                 /* collision distance (m) */
+    float d_full;                  /* Eq. 15 full-clearance distance (m) */
+    float visit_cell_m;            /* Eq. 9 workspace cell size (m) */
+    int32_t l_hit_q;               /* hit increment, logodds_scale units (870) */
+    int32_t l_miss_q;              /* miss increment (-410) */
+    int32_t l_clamp_q;             /* |L| clamp (3584) */
+    int32_t t_episode;             /* episode length in steps */
+    float logodds_scale;           /* log-odds per int16 unit (1/1024) */
+    int32_t threads_per_cta;       /* 0 = library default / autotuned */
+    double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;   /* Eq. 7-17 */
+    uint64_t seed;                 /* noise stream key (Philox4x32-10) */
+    int32_t flags;                 /* ASLAM_FLAG_* */
+    int32_t window_cells;          /* side of the shared-memory counter window; 0 = auto */
+} aslam_config;
+
+#define ASLAM_MAX_BEAMS 1024
+#define ASLAM_MAX_MAP_SIDE 8192
+
+/* Borrowed device views of the batch state (valid until destroy). */
+typedef struct {
+    float *x, *y, *th;             /* [E] pose (m, m, rad in [-pi, pi)) */
+    float *u_prev;                 /* [E] U_{t-1} */
+    int32_t *t;                    /* [E] step within the episode */
+    int32_t *g;                    /* [E] global step count (noise counter) */
+    int32_t *ep;                   /* [E] episode count */
+    int32_t *done;                 /* [E] 1 after a collision or t == T_episode */
+    int16_t *belief;               /* [map_off[E]] log-odds, env e at map_off[e] */
+    float *z;                      /* [ray_off[E]] measured ranges of the last step */
+    float *z_true;                 /* [ray_off[E]] noise-free ranges (DEBUG flag) */
+    uint8_t *hit;                  /* [ray_off[E]] 1 if the beam returned (DEBUG flag) */
+    uint32_t *counts;              /* [map_off[E]] last step's (hits<<16 | misses) (DEBUG) */
+    int64_t *ray_cells;            /* [E] cells updated by the last step */
+    int64_t *gt_cells;             /* [E] ground-truth cells read by the last step */
+    float *terms;                  /* [E, ASLAM_N_TERMS] last step's reward terms */
+    const int64_t *h_map_off;      /* HOST [E+1] cell offsets of each env's grid */
+    const int64_t *h_ray_off;      /* HOST [E+1] offsets of each env's beams */
+    int32_t b_max;                 /* max beams over envs (observation row = b_max + 2) */
+} aslam_state_ptrs;
+
+/* Fill `cfg` with defaults (version, struct_size, constants). */
+aslam_status aslam_config_init(aslam_config *cfg);
+
+/* Device workspace bytes a batch with this config needs (host-only call). */
+aslam_status aslam_workspace_bytes(const aslam_config *cfg, size_t *bytes);
+
+/*
+ * Create a batch over a caller-owned device workspace of at least
+ * aslam_workspace_bytes() bytes, 256-byte aligned, which must stay valid and
+ * untouched until aslam_destroy_batch.
+ *   d_gt     device uint8 ground-truth grids, env e at h_gt_off[e] (row-major
+ *            W x H); read during this call only (packed into the workspace).
+ *   h_gt_off host int64 [E+1] offsets into d_gt.
+ *   d_spawn  device float [E, n_spawn, 3] spawn poses (x, y, th); copied.
+ * All envs start at spawn pose 0 with an all-unknown map (L = 0).
+ * Synchronises `stream` before returning.
+ */
+aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size_t bytes,
+                                const uint8_t *d_gt, const int64_t *h_gt_off,
+                                const float *d_spawn, void *stream, aslam_batch **out);
+
+/*
+ * One environment step for every env (Sec. III-C/D/E, IV-A):
+ *   d_actions device float [E, 2] (v, w), clamped to [0, v_max] x [-w_max, w_max];
+ *   d_u       device float [E] uncertainty U_t from the SLAM backend, or NULL (0).
+ * Envs flagged done by the previous step are first reset to their next spawn
+ * pose with a cleared map.  Results stay in the workspace for
+ * aslam_reward / aslam_observe / aslam_reward_terms.
+ */
+aslam_status aslam_step(aslam_batch *b, const float *d_actions, const float *d_u, void *stream);
+
+/* aslam_step that also writes the reward [E] and observation [E, b_max+2]
+ * directly (either may be NULL). */
+aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const float *d_u,
+                              float *d_reward, float *d_obs, void *stream);
+
+/* Reward of the last step, [E] fp32, selected by cfg.reward_mode. */
+aslam_status aslam_reward(aslam_batch *b, float *d_reward, void *stream);
+
+/* All reward terms of the last step, [E, ASLAM_N_TERMS] fp32. */
+aslam_status aslam_reward_terms(aslam_batch *b, float *d_terms, void *stream);
+
+/* Observation of the last step (Eq. 3): [E, b_max + 2] fp32 rows
+ * [z_0 .. z_{B-1}, r_max padding up to b_max, yaw, U_t]. */
+aslam_status aslam_observe(aslam_batch *b, float *d_obs, void *stream);
+
+/* Reset the envs whose d_mask byte is non-zero (NULL: all) on the next step
+ * boundary: marks them done so the next aslam_step resets them. */
+aslam_status aslam_reset(aslam_batch *b, const uint8_t *d_mask, void *stream);
+
+/* Borrowed device pointers to the batch state (host call, no sync). */
+aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *out);
+
+/* Synchronise `stream` and return ASLAM_ERR_DEVICE / ASLAM_ERR_TIMEOUT if a
+ * device-side check has fired since create (the word stays set). */
+aslam_status aslam_sync_status(aslam_batch *b, void *stream);
+
+/*
+ * Capture one aslam_step_fused into a CUDA graph bound to these pointers
+ * (which must then hold the next step's inputs at every replay), and replay
+ * it with aslam_graph_step.  `stream` must not be capturing already.
+ */
+aslam_status aslam_capture_graph(aslam_batch *b, const float *d_actions, const float *d_u,
+                                 float *d_reward, float *d_obs, void *stream);
+aslam_status aslam_graph_step(aslam_batch *b, void *stream);
+
+/*
+ * Pick threads-per-CTA and the shared-memory counter window by timing
+ * candidate launches on this batch's own worlds (zero actions from the
+ * current poses), then reset every env.  Synchronises `stream`.
+ * h_best (optional, int32[2]) receives {threads_per_cta, window_cells}.
+ */
+aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream);
+
+/* Checkpoint: bytes of the mutable state; save to / load from host memory.
+ * Synchronises `stream`.  A loaded state continues bit-exactly. */
+aslam_status aslam_state_bytes(aslam_batch *b, size_t *bytes);
+aslam_status aslam_save_state(aslam_batch *b, void *h_buf, size_t bytes, void *stream);
+aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, void *stream);
+
+/* Release the host handle (the caller frees the workspace). */
+void aslam_destroy_batch(aslam_batch *b);
+
+const char *aslam_status_string(aslam_status s);
+/* Last error message of this batch (b != NULL) or of the calling thread. */
+const char *aslam_last_error(const aslam_batch *b);
+
+/* Test hook: evaluate the library's deterministic fp32 sin/cos, log,
+ * cos(2*pi*u) and Gaussian draw on n device inputs (outputs [n] each). */
+aslam_status aslam_debug_detmath(const float *d_x, const float *d_u, int32_t n,
+                                 float *d_sin, float *d_cos, float *d_log, float *d_cos2pi,
+                                 uint64_t seed, float *d_gauss, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASLAM_H */

@@ -72,6 +72,7 @@ class OrcCfg(C.Structure):
         ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
         ("map_w", P), ("map_h", P), ("n_beams", P), ("map_off", P), ("visit_off", P),
+        ("env_id", P),
     ]
 
 
@@ -193,7 +194,7 @@ DEFAULTS = dict(r_max=5.0, fov=0.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0,
 class OracleBatch2D:
     """Owns the numpy state of E environments and steps them with orc_step2d."""
 
-    def __init__(self, inputs, **params):
+    def __init__(self, inputs, env_ids=None, **params):
         p = dict(DEFAULTS)
         p.update(params)
         self.p = p
@@ -212,6 +213,7 @@ class OracleBatch2D:
         self.visit_off[1:] = np.cumsum([a * b for a, b in dims])
         self.gt = np.ascontiguousarray(inputs.gt, dtype=np.uint8)
         self.spawn = np.ascontiguousarray(inputs.spawn, dtype=np.float32)
+        self.env_ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
         ncell = int(self.map_off[-1])
         self.belief = np.zeros(ncell, dtype=np.int16)
         self.x = self.spawn[:, 0, 0].copy()
@@ -233,7 +235,8 @@ class OracleBatch2D:
             lam_col=p["lam_col"], lam_explore=p["lam_explore"], lam_abs=p["lam_abs"],
             lam_delta=p["lam_delta"], kappa=p["kappa"], u_hi=p["u_hi"],
             map_w=_ptr(self.map_w), map_h=_ptr(self.map_h), n_beams=_ptr(self.n_beams),
-            map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off))
+            map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off),
+            env_id=_ptr(self.env_ids))
 
     def _state(self):
         return OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x),

@@ -346,6 +346,7 @@ typedef struct {
     const int32_t *map_w, *map_h, *n_beams;
     const int64_t *map_off;    /* [E+1] */
     const int64_t *visit_off;  /* [E+1] */
+    const int32_t *env_id;     /* [E] index of each env in the noise stream, or NULL */
 } orc_cfg;
 
 typedef struct {
@@ -466,7 +467,8 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
             if (!hit)
                 gt_cells += nc;
             if (hit) {
-                float g = orc_gauss(cfg->seed, (uint32_t)e, (uint32_t)st->g[e], (uint32_t)b);
+                uint32_t eid = cfg->env_id ? (uint32_t)cfg->env_id[e] : (uint32_t)e;
+                float g = orc_gauss(cfg->seed, eid, (uint32_t)st->g[e], (uint32_t)b);
                 z = z_true + cfg->sigma * g;
                 z = fminf(fmaxf(z, 0.0f), cfg->r_max);
             }

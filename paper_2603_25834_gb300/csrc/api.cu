@@ -1,0 +1,782 @@
+// api.cu -- host implementation of the libaslam C ABI (include/aslam.h).
+//
+// The library owns no device memory: every device array lives in the
+// caller's workspace at offsets computed by `build_layout`, identically in
+// aslam_workspace_bytes and aslam_create_batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "aslam_internal.cuh"
+
+using namespace aslam;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+constexpr size_t kAlign = 256;
+constexpr int kCellPad = 64;     // env grids start on 128-byte (int16) boundaries
+
+struct HostInfo {
+    int E = 0, b_max = 0;
+    std::vector<int> W, H, B, Vw, Vh;
+    std::vector<long long> map_off, gtb_off, ray_off, visit_off;
+    int gt_words_max = 0;
+};
+
+struct Offsets {
+    size_t W, H, B, Vw, Vh, order, map_off, gtb_off, ray_off, visit_off, src_off;
+    size_t beam_cs, lut, gt_bits;
+    size_t x, y, th, u_prev, t, g, ep, done, Hq;
+    size_t belief, visit, spawn;
+    size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
+    size_t far_cnt, far_list, far_n, queue, err, tune_actions;
+    size_t total;
+};
+
+size_t pad_to(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Visit-workspace dims (Eq. 9 "workspace vastly larger than the environment"):
+// twice the map extent per axis, in visit cells, computed in fp32.
+void visit_dims(int W, int H, float res, float vc, int *Vw, int *Vh) {
+    float ew = 2.0f * ((float)W * res), eh = 2.0f * ((float)H * res);
+    int a = (int)std::ceil(ew / vc), b = (int)std::ceil(eh / vc);
+    *Vw = a < 1 ? 1 : a;
+    *Vh = b < 1 ? 1 : b;
+}
+
+bool validate(const aslam_config *c, std::string *msg) {
+    auto fail = [&](const char *m) { *msg = m; return false; };
+    if (!c) return fail("config is NULL");
+    if (c->struct_size != sizeof(aslam_config)) return fail("config struct_size mismatch");
+    if (c->version != ASLAM_CONFIG_VERSION) return fail("config version mismatch");
+    if (c->n_envs < 1) return fail("n_envs must be >= 1");
+    if (c->dims != 2) return fail("dims must be 2 for aslam_create_batch");
+    if (c->n_spawn < 1) return fail("n_spawn must be >= 1");
+    if (!c->h_map_w || !c->h_map_h || !c->h_n_beams) return fail("map dims / beams arrays are NULL");
+    for (int e = 0; e < c->n_envs; ++e) {
+        if (c->h_map_w[e] < 1 || c->h_map_w[e] > ASLAM_MAX_MAP_SIDE || c->h_map_h[e] < 1 ||
+            c->h_map_h[e] > ASLAM_MAX_MAP_SIDE)
+            return fail("map side out of [1, ASLAM_MAX_MAP_SIDE]");
+        if (c->h_n_beams[e] < 0 || c->h_n_beams[e] > ASLAM_MAX_BEAMS)
+            return fail("n_beams out of [0, ASLAM_MAX_BEAMS]");
+    }
+    if (!(c->res_m > 0.0f) || !(c->r_max_m > 0.0f)) return fail("res_m and r_max_m must be > 0");
+    if ((double)c->r_max_m / c->res_m > 16384.0) return fail("r_max_m / res_m must be <= 16384 cells");
+    if (!(c->dt_s >= 0.0f) || !(c->v_max >= 0.0f) || !(c->w_max >= 0.0f))
+        return fail("dt_s, v_max, w_max must be >= 0");
+    if (!(c->noise_sigma_m >= 0.0f)) return fail("noise_sigma_m must be >= 0");
+    if (c->l_clamp_q < 1 || c->l_clamp_q > 32767) return fail("l_clamp_q out of [1, 32767]");
+    if (std::abs(c->l_hit_q) > 32767 || std::abs(c->l_miss_q) > 32767)
+        return fail("|l_hit_q|, |l_miss_q| must be <= 32767");
+    if (c->t_episode < 1) return fail("t_episode must be >= 1");
+    if (!(c->d_full > c->d_crash)) return fail("d_full must exceed d_crash");
+    if (!(c->visit_cell_m > 0.0f)) return fail("visit_cell_m must be > 0");
+    if (!(c->kappa > 0.0) || !(c->u_hi > 0.0)) return fail("kappa and u_hi must be > 0");
+    if (!(c->logodds_scale > 0.0f)) return fail("logodds_scale must be > 0");
+    if (c->reward_mode != ASLAM_REWARD_ENTROPY && c->reward_mode != ASLAM_REWARD_COMPOSITE)
+        return fail("unknown reward_mode");
+    if (c->threads_per_cta != 0 &&
+        (c->threads_per_cta < 32 || c->threads_per_cta > 1024 || c->threads_per_cta % 32))
+        return fail("threads_per_cta must be 0 or a multiple of 32 in [32, 1024]");
+    if (c->window_cells != 0 && (c->window_cells < 64 || c->window_cells % 8))
+        return fail("window_cells must be 0 or a multiple of 8 >= 64");
+    return true;
+}
+
+void host_info(const aslam_config *c, HostInfo *hi) {
+    const int E = c->n_envs;
+    hi->E = E;
+    hi->W.assign(c->h_map_w, c->h_map_w + E);
+    hi->H.assign(c->h_map_h, c->h_map_h + E);
+    hi->B.assign(c->h_n_beams, c->h_n_beams + E);
+    hi->b_max = *std::max_element(hi->B.begin(), hi->B.end());
+    hi->Vw.resize(E);
+    hi->Vh.resize(E);
+    hi->map_off.assign(E + 1, 0);
+    hi->gtb_off.assign(E + 1, 0);
+    hi->ray_off.assign(E + 1, 0);
+    hi->visit_off.assign(E + 1, 0);
+    hi->gt_words_max = 0;
+    for (int e = 0; e < E; ++e) {
+        const long long n = (long long)hi->W[e] * hi->H[e];
+        const long long words = (long long)pad_to((size_t)((n + 31) / 32), 4);
+        hi->map_off[e + 1] = hi->map_off[e] + (long long)pad_to((size_t)n, kCellPad);
+        hi->gtb_off[e + 1] = hi->gtb_off[e] + words;
+        hi->ray_off[e + 1] = hi->ray_off[e] + hi->B[e];
+        visit_dims(hi->W[e], hi->H[e], c->res_m, c->visit_cell_m, &hi->Vw[e], &hi->Vh[e]);
+        hi->visit_off[e + 1] = hi->visit_off[e] + (long long)hi->Vw[e] * hi->Vh[e];
+        hi->gt_words_max = std::max(hi->gt_words_max, (int)words);
+    }
+}
+
+Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
+    Offsets o{};
+    size_t cur = 0;
+    auto add = [&](size_t bytes) {
+        size_t at = pad_to(cur, kAlign);
+        cur = at + bytes;
+        return at;
+    };
+    const size_t E = hi.E;
+    const size_t cells = (size_t)hi.map_off[E];
+    const size_t rays = (size_t)std::max<long long>(hi.ray_off[E], 1);
+    const bool debug = (c->flags & ASLAM_FLAG_DEBUG) != 0;
+    o.W = add(4 * E);
+    o.H = add(4 * E);
+    o.B = add(4 * E);
+    o.Vw = add(4 * E);
+    o.Vh = add(4 * E);
+    o.order = add(4 * E);
+    o.map_off = add(8 * (E + 1));
+    o.gtb_off = add(8 * (E + 1));
+    o.ray_off = add(8 * (E + 1));
+    o.visit_off = add(8 * (E + 1));
+    o.src_off = add(8 * (E + 1));
+    o.beam_cs = add(8 * rays);
+    o.lut = add(8 * (2 * (size_t)c->l_clamp_q + 1));
+    o.gt_bits = add(4 * (size_t)hi.gtb_off[E]);
+    o.x = add(4 * E);
+    o.y = add(4 * E);
+    o.th = add(4 * E);
+    o.u_prev = add(4 * E);
+    o.t = add(4 * E);
+    o.g = add(4 * E);
+    o.ep = add(4 * E);
+    o.done = add(4 * E);
+    o.Hq = add(8 * E);
+    o.belief = add(2 * cells);
+    o.visit = add(4 * (size_t)hi.visit_off[E]);
+    o.spawn = add(12 * E * (size_t)c->n_spawn);
+    o.z = add(4 * rays);
+    o.z_true = add(debug ? 4 * rays : 0);
+    o.hit = add(debug ? rays : 0);
+    o.dbg = add(debug ? 4 * cells : 0);
+    o.ray_cells = add(8 * E);
+    o.gt_cells = add(8 * E);
+    o.terms = add(4 * E * kTerms);
+    o.reward = add(4 * E);
+    o.far_cnt = add(4 * cells);
+    o.far_list = add(4 * cells);
+    o.far_n = add(4 * E);
+    o.queue = add(8);          // {next item, CTAs finished}
+    o.err = add(4);
+    o.tune_actions = add(8 * E);
+    o.total = pad_to(cur, kAlign);
+    return o;
+}
+
+}  // namespace
+
+struct aslam_batch {
+    aslam_config cfg;
+    HostInfo hi;
+    Offsets off;
+    Step2DParams p;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int sm_count = 0, smem_optin = 0;
+    int block = 0, window = 0, grid = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+    std::vector<int> order;
+};
+
+namespace {
+
+aslam_status fail_b(aslam_batch *b, aslam_status s, const std::string &m) {
+    if (b) b->err = m;
+    g_thread_error = m;
+    return s;
+}
+
+aslam_status cuda_fail(aslam_batch *b, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail_b(b, ASLAM_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                        \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return cuda_fail(b, _e, where); \
+    } while (0)
+
+template <class T>
+T *at(aslam_batch *b, size_t off) {
+    return reinterpret_cast<T *>(b->ws + off);
+}
+
+// Shared-memory needs of a (window side S) choice: words of ground-truth
+// bits plus words of 16-bit counters, for the largest env.
+bool plan_window(const HostInfo &hi, int S, int *win_words, std::string *msg) {
+    int ww = 0;
+    for (int e = 0; e < hi.E; ++e) {
+        const long long n = (long long)hi.W[e] * hi.H[e];
+        long long need;
+        if (n <= (long long)S * S) {
+            need = (n + 1) / 2;
+        } else {
+            if (hi.W[e] % 8) {
+                *msg = "a map larger than the shared window needs a width that is a multiple of 8";
+                return false;
+            }
+            need = ((long long)std::min(S, hi.W[e]) * std::min(S, hi.H[e]) + 1) / 2;
+        }
+        ww = std::max(ww, (int)pad_to((size_t)need, 4));
+    }
+    *win_words = ww;
+    return true;
+}
+
+constexpr int kStaticSmem = 2048;
+
+int auto_window(const HostInfo &hi, int smem_optin) {
+    long long budget_words = (smem_optin - kStaticSmem) / 4 - hi.gt_words_max;
+    int S = (int)std::floor(std::sqrt(2.0 * (double)budget_words));
+    S &= ~7;
+    return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
+}
+
+aslam_status configure_launch(aslam_batch *b, int block, int S) {
+    int ww = 0;
+    std::string msg;
+    if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
+    const size_t smem = 4 * ((size_t)b->hi.gt_words_max + ww);
+    if (smem + kStaticSmem > (size_t)b->smem_optin)
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
+    CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
+    int per_sm = 0;
+    CK(step2d_occupancy(block, smem, &per_sm), "occupancy");
+    if (per_sm < 1) return fail_b(b, ASLAM_ERR_INVALID_ARG, "launch configuration does not fit an SM");
+    b->block = block;
+    b->window = S;
+    b->smem = smem;
+    b->grid = std::min(b->hi.E, b->sm_count * per_sm);
+    b->p.window = S;
+    b->p.gt_words_max = b->hi.gt_words_max;
+    b->p.win_words_max = ww;
+    return ASLAM_OK;
+}
+
+int default_block(const HostInfo &hi) {
+    int t = (std::min(hi.b_max, 512) + 31) / 32 * 32;
+    return std::max(128, t);
+}
+
+aslam_status reset_all(aslam_batch *b, cudaStream_t s) {
+    const size_t cells = (size_t)b->hi.map_off[b->hi.E];
+    CK(cudaMemsetAsync(b->p.belief, 0, 2 * cells, s), "memset belief");
+    CK(cudaMemsetAsync(b->p.visit, 0xff, 4 * (size_t)b->hi.visit_off[b->hi.E], s), "memset visit");
+    CK(cudaMemsetAsync(b->p.far_cnt, 0, 4 * cells, s), "memset far counters");
+    if (b->p.dbg_counts) CK(cudaMemsetAsync(b->p.dbg_counts, 0, 4 * cells, s), "memset debug");
+    CK(launch_init_state(b->p, s), "init state");
+    return ASLAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+aslam_status aslam_config_init(aslam_config *c) {
+    if (!c) return ASLAM_ERR_INVALID_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->struct_size = sizeof(aslam_config);
+    c->version = ASLAM_CONFIG_VERSION;
+    c->n_envs = 1;
+    c->dims = 2;
+    c->n_spawn = 1;
+    c->reward_mode = ASLAM_REWARD_ENTROPY;
+    c->res_m = 0.05f;
+    c->r_max_m = 12.0f;
+    c->fov_rad = 0.0f;
+    c->noise_sigma_m = 0.01f;
+    c->dt_s = 0.1f;
+    c->v_max = 0.5f;
+    c->w_max = 1.0f;
+    c->d_crash = 0.15f;
+    c->d_full = 0.5f;
+    c->visit_cell_m = 0.5f;
+    c->l_hit_q = 870;
+    c->l_miss_q = -410;
+    c->l_clamp_q = 3584;
+    c->t_episode = 2048;
+    c->logodds_scale = 1.0f / 1024.0f;
+    c->lam_col = 10.0;
+    c->lam_explore = 1.0;
+    c->lam_abs = 0.1;
+    c->lam_delta = 1.0;
+    c->kappa = 0.05;
+    c->u_hi = 1.0;
+    c->seed = 20260325ull;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_workspace_bytes(const aslam_config *cfg, size_t *bytes) {
+    std::string msg;
+    if (!bytes) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "bytes is NULL");
+    if (!validate(cfg, &msg)) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, msg);
+    try {
+        HostInfo hi;
+        host_info(cfg, &hi);
+        *bytes = build_layout(cfg, hi).total;
+    } catch (const std::bad_alloc &) {
+        return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "host allocation failed");
+    }
+    return ASLAM_OK;
+}
+
+aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size_t bytes,
+                                const uint8_t *d_gt, const int64_t *h_gt_off,
+                                const float *d_spawn, void *stream, aslam_batch **out) {
+    std::string msg;
+    if (!out) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!validate(cfg, &msg)) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, msg);
+    if (!d_gt || !h_gt_off || !d_spawn) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "NULL input pointer");
+    if (!d_workspace || ((uintptr_t)d_workspace % kAlign))
+        return fail_b(nullptr, ASLAM_ERR_WORKSPACE, "workspace is NULL or not 256-byte aligned");
+    aslam_batch *b = new (std::nothrow) aslam_batch();
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "host allocation failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        b->cfg = *cfg;
+        host_info(cfg, &b->hi);
+        b->off = build_layout(cfg, b->hi);
+        for (int e = 0; e < cfg->n_envs; ++e) {
+            if (h_gt_off[e + 1] - h_gt_off[e] != (int64_t)cfg->h_map_w[e] * cfg->h_map_h[e]) {
+                delete b;
+                return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "h_gt_off does not match W*H");
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        delete b;
+        return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "host allocation failed");
+    }
+    if (bytes < b->off.total) {
+        delete b;
+        return fail_b(nullptr, ASLAM_ERR_WORKSPACE, "workspace smaller than aslam_workspace_bytes()");
+    }
+    b->ws = (char *)d_workspace;
+    b->ws_bytes = bytes;
+    aslam_status st = ASLAM_OK;
+    do {
+        int dev = 0;
+        cudaError_t ce = cudaGetDevice(&dev);
+        if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (ce == cudaSuccess)
+            ce = cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (ce != cudaSuccess) { st = cuda_fail(b, ce, "device query"); break; }
+
+        const HostInfo &hi = b->hi;
+        const Offsets &o = b->off;
+        const int E = hi.E;
+        Step2DParams &p = b->p;
+        std::memset(&p, 0, sizeof(p));
+        p.E = E;
+        p.b_max = hi.b_max;
+        p.n_spawn = cfg->n_spawn;
+        p.flags = cfg->flags;
+        p.reward_mode = cfg->reward_mode;
+        p.hit_q = cfg->l_hit_q;
+        p.miss_q = cfg->l_miss_q;
+        p.clamp_q = cfg->l_clamp_q;
+        p.t_episode = cfg->t_episode;
+        p.Tmax = (int)lrintf((cfg->r_max_m / cfg->res_m) * 65536.0f);
+        p.res = cfg->res_m;
+        p.r_max = cfg->r_max_m;
+        p.sigma = cfg->noise_sigma_m;
+        p.dt = cfg->dt_s;
+        p.v_max = cfg->v_max;
+        p.w_max = cfg->w_max;
+        p.d_crash = cfg->d_crash;
+        p.d_full = cfg->d_full;
+        p.visit_cell = cfg->visit_cell_m;
+        p.lam_col = cfg->lam_col;
+        p.lam_explore = cfg->lam_explore;
+        p.lam_abs = cfg->lam_abs;
+        p.lam_delta = cfg->lam_delta;
+        p.kappa = cfg->kappa;
+        p.u_hi = cfg->u_hi;
+        p.key = make_uint2((unsigned)cfg->seed, (unsigned)(cfg->seed >> 32));
+        p.W = at<int>(b, o.W);
+        p.H = at<int>(b, o.H);
+        p.B = at<int>(b, o.B);
+        p.Vw = at<int>(b, o.Vw);
+        p.Vh = at<int>(b, o.Vh);
+        p.order = at<int>(b, o.order);
+        p.map_off = at<long long>(b, o.map_off);
+        p.gtb_off = at<long long>(b, o.gtb_off);
+        p.ray_off = at<long long>(b, o.ray_off);
+        p.visit_off = at<long long>(b, o.visit_off);
+        p.beam_cs = at<float2>(b, o.beam_cs);
+        p.lut = at<long long>(b, o.lut);
+        p.gt_bits = at<unsigned>(b, o.gt_bits);
+        p.x = at<float>(b, o.x);
+        p.y = at<float>(b, o.y);
+        p.th = at<float>(b, o.th);
+        p.u_prev = at<float>(b, o.u_prev);
+        p.t = at<int>(b, o.t);
+        p.g = at<int>(b, o.g);
+        p.ep = at<int>(b, o.ep);
+        p.done = at<int>(b, o.done);
+        p.Hq = at<long long>(b, o.Hq);
+        p.belief = at<short>(b, o.belief);
+        p.visit = at<int>(b, o.visit);
+        p.spawn = at<float>(b, o.spawn);
+        p.z = at<float>(b, o.z);
+        const bool debug = (cfg->flags & ASLAM_FLAG_DEBUG) != 0;
+        p.z_true = debug ? at<float>(b, o.z_true) : nullptr;
+        p.hit = debug ? at<unsigned char>(b, o.hit) : nullptr;
+        p.dbg_counts = debug ? at<unsigned>(b, o.dbg) : nullptr;
+        p.ray_cells = at<long long>(b, o.ray_cells);
+        p.gt_cells = at<long long>(b, o.gt_cells);
+        p.terms = at<float>(b, o.terms);
+        p.reward = at<float>(b, o.reward);
+        p.far_cnt = at<unsigned>(b, o.far_cnt);
+        p.far_list = at<int>(b, o.far_list);
+        p.far_n = at<int>(b, o.far_n);
+        p.queue = at<unsigned>(b, o.queue);
+        p.err = at<unsigned>(b, o.err);
+
+        // Host-built tables: beam directions, entropy table, work order.
+        std::vector<float2> cs((size_t)std::max<long long>(hi.ray_off[E], 1));
+        const double two_pi = 2.0 * 3.14159265358979323846;
+        const double fov = (double)cfg->fov_rad;
+        const bool full_turn = fov <= 0.0 || fov >= two_pi - 1e-9;
+        for (int e = 0; e < E; ++e) {
+            const int B = hi.B[e];
+            for (int k = 0; k < B; ++k) {
+                double a;
+                if (full_turn) a = (two_pi * (double)k) / (double)B;
+                else if (B == 1) a = 0.0;
+                else a = -0.5 * fov + ((double)k * fov) / (double)(B - 1);
+                cs[(size_t)hi.ray_off[e] + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        }
+        // Entropy of a cell with log-odds l = L * scale, in 2^-40 nats, by
+        // the stable form h = l * q + log1p(e^-l), q = e^-l / (1 + e^-l).
+        const int C = cfg->l_clamp_q;
+        std::vector<long long> lut(2 * (size_t)C + 1);
+        for (int L = -C; L <= C; ++L) {
+            const double l = std::fabs((double)L * (double)cfg->logodds_scale);
+            const double ex = std::exp(-l);
+            const double h = l * (ex / (1.0 + ex)) + std::log1p(ex);
+            lut[(size_t)(L + C)] = std::llrint(h * kLutScale);
+        }
+        // Longest-first work order: cost ~ beams x cells a beam can cross.
+        b->order.resize(E);
+        std::iota(b->order.begin(), b->order.end(), 0);
+        std::vector<double> cost(E);
+        const double rcell = (double)cfg->r_max_m / cfg->res_m;
+        for (int e = 0; e < E; ++e)
+            cost[e] = (double)std::max(hi.B[e], 1) *
+                      std::min(rcell, std::sqrt((double)hi.W[e] * hi.W[e] + (double)hi.H[e] * hi.H[e]));
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [&](int a, int c2) { return cost[a] > cost[c2]; });
+
+        auto h2d = [&](void *dst, const void *src, size_t n) {
+            return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+        };
+        std::vector<long long> src_off(h_gt_off, h_gt_off + E + 1);
+        cudaError_t e1 = cudaSuccess;
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.W, hi.W.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.H, hi.H.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.B, hi.B.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.Vw, hi.Vw.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.Vh, hi.Vh.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.order, b->order.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.map_off, hi.map_off.data(), 8 * (size_t)(E + 1));
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.gtb_off, hi.gtb_off.data(), 8 * (size_t)(E + 1));
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.ray_off, hi.ray_off.data(), 8 * (size_t)(E + 1));
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.visit_off, hi.visit_off.data(), 8 * (size_t)(E + 1));
+        if (e1 == cudaSuccess) e1 = h2d(at<void>(b, o.src_off), src_off.data(), 8 * (size_t)(E + 1));
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.beam_cs, cs.data(), 8 * cs.size());
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.lut, lut.data(), 8 * lut.size());
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync((void *)p.spawn, d_spawn, 12 * (size_t)E * cfg->n_spawn,
+                                 cudaMemcpyDeviceToDevice, s);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.err, 0, 4, s);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.queue, 0, 8, s);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(at<void>(b, o.tune_actions), 0, 8 * (size_t)E, s);
+        if (e1 == cudaSuccess)
+            e1 = launch_pack_gt(d_gt, at<long long>(b, o.src_off), p.W, p.H, p.gtb_off,
+                                (unsigned *)p.gt_bits, E, s);
+        if (e1 != cudaSuccess) { st = cuda_fail(b, e1, "create: upload"); break; }
+        st = reset_all(b, s);
+        if (st != ASLAM_OK) break;
+        const int S = cfg->window_cells ? cfg->window_cells : auto_window(hi, b->smem_optin);
+        const int block = cfg->threads_per_cta ? cfg->threads_per_cta : default_block(hi);
+        st = configure_launch(b, block, S);
+        if (st != ASLAM_OK) break;
+        ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { st = cuda_fail(b, ce, "create: synchronize"); break; }
+    } while (0);
+    if (st != ASLAM_OK) {
+        g_thread_error = b->err;
+        delete b;
+        return st;
+    }
+    *out = b;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const float *d_u,
+                              float *d_reward, float *d_obs, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!d_actions) return fail_b(b, ASLAM_ERR_INVALID_ARG, "d_actions is NULL");
+    Step2DParams p = b->p;
+    p.actions = d_actions;
+    p.u_in = d_u;
+    p.out_reward = d_reward;
+    p.out_obs = d_obs;
+    CK(launch_step2d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_step(aslam_batch *b, const float *d_actions, const float *d_u, void *stream) {
+    return aslam_step_fused(b, d_actions, d_u, nullptr, nullptr, stream);
+}
+
+aslam_status aslam_reward(aslam_batch *b, float *d_reward, void *stream) {
+    if (!b || !d_reward) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    CK(launch_gather_reward(b->p, d_reward, (cudaStream_t)stream), "aslam_reward");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_reward_terms(aslam_batch *b, float *d_terms, void *stream) {
+    if (!b || !d_terms) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaMemcpyAsync(d_terms, b->p.terms, 4 * (size_t)b->hi.E * kTerms,
+                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "aslam_reward_terms");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_observe(aslam_batch *b, float *d_obs, void *stream) {
+    if (!b || !d_obs) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    CK(launch_gather_obs(b->p, d_obs, (cudaStream_t)stream), "aslam_observe");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_reset(aslam_batch *b, const uint8_t *d_mask, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    CK(launch_mark_done(b->p.done, d_mask, b->hi.E, (cudaStream_t)stream), "aslam_reset");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *o) {
+    if (!b || !o) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    const Step2DParams &p = b->p;
+    o->x = p.x;
+    o->y = p.y;
+    o->th = p.th;
+    o->u_prev = p.u_prev;
+    o->t = p.t;
+    o->g = p.g;
+    o->ep = p.ep;
+    o->done = p.done;
+    o->belief = p.belief;
+    o->z = p.z;
+    o->z_true = p.z_true;
+    o->hit = p.hit;
+    o->counts = p.dbg_counts;
+    o->ray_cells = reinterpret_cast<int64_t *>(p.ray_cells);
+    o->gt_cells = reinterpret_cast<int64_t *>(p.gt_cells);
+    o->terms = p.terms;
+    o->h_map_off = reinterpret_cast<const int64_t *>(b->hi.map_off.data());
+    o->h_ray_off = reinterpret_cast<const int64_t *>(b->hi.ray_off.data());
+    o->b_max = b->hi.b_max;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_sync_status(aslam_batch *b, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, b->p.err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status read");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "status synchronize");
+    if (h & kErrTimeout) return fail_b(b, ASLAM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (h & kErrChecks) return fail_b(b, ASLAM_ERR_DEVICE, "a device-side check failed");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_capture_graph(aslam_batch *b, const float *d_actions, const float *d_u,
+                                 float *d_reward, float *d_obs, void *stream) {
+    if (!b || !d_actions) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) return fail_b(b, ASLAM_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    Step2DParams p = b->p;
+    p.actions = d_actions;
+    p.u_in = d_u;
+    p.out_reward = d_reward;
+    p.out_obs = d_obs;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = launch_step2d(p, b->grid, b->block, b->smem, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(s, &g);
+    if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, le, "capture launch"); }
+    if (ee != cudaSuccess) return cuda_fail(b, ee, "end capture");
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->gexec, g, 0), "graph instantiate");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_graph_step(aslam_batch *b, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->gexec) return fail_b(b, ASLAM_ERR_STATE, "no captured graph");
+    CK(cudaGraphLaunch(b->gexec, (cudaStream_t)stream), "graph launch");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b_max = b->hi.b_max;
+    std::vector<int> blocks, windows;
+    for (int t : {128, 256, 384, 512, 768, 1024})
+        if (t >= 64 && (t <= 1024)) blocks.push_back(t);
+    const int Sa = auto_window(b->hi, b->smem_optin);
+    for (int S : {Sa, 320, 256, 224, 192, 160, 128})
+        if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
+    (void)b_max;
+    const int keep_block = b->block, keep_window = b->window;
+    float best_ms = 1e30f;
+    int best_block = keep_block, best_window = keep_window;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const float *acts = at<float>(b, b->off.tune_actions);
+    aslam_status st = ASLAM_OK;
+    for (int S : windows) {
+        for (int blk : blocks) {
+            if (configure_launch(b, blk, S) != ASLAM_OK) continue;
+            st = reset_all(b, s);
+            if (st != ASLAM_OK) break;
+            Step2DParams p = b->p;
+            p.actions = acts;
+            cudaError_t ce = launch_step2d(p, b->grid, b->block, b->smem, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && ce == cudaSuccess; ++r)
+                ce = launch_step2d(p, b->grid, b->block, b->smem, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) { st = cuda_fail(b, ce, "autotune"); break; }
+            if (ms < best_ms) { best_ms = ms; best_block = blk; best_window = S; }
+        }
+        if (st != ASLAM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != ASLAM_OK) return st;
+    st = configure_launch(b, best_block, best_window);
+    if (st != ASLAM_OK) return st;
+    st = reset_all(b, s);
+    if (st != ASLAM_OK) return st;
+    CK(cudaStreamSynchronize(s), "autotune synchronize");
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (h_best) { h_best[0] = best_block; h_best[1] = best_window; }
+    return ASLAM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+struct Region { void *ptr; size_t bytes; };
+std::vector<Region> state_regions(aslam_batch *b) {
+    const Step2DParams &p = b->p;
+    const size_t E = b->hi.E;
+    return {{p.x, 4 * E}, {p.y, 4 * E}, {p.th, 4 * E}, {p.u_prev, 4 * E}, {p.t, 4 * E},
+            {p.g, 4 * E}, {p.ep, 4 * E}, {p.done, 4 * E}, {p.Hq, 8 * E},
+            {p.belief, 2 * (size_t)b->hi.map_off[E]},
+            {p.visit, 4 * (size_t)b->hi.visit_off[E]}};
+}
+}  // namespace
+
+extern "C" {
+
+aslam_status aslam_state_bytes(aslam_batch *b, size_t *bytes) {
+    if (!b || !bytes) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    size_t n = 0;
+    for (const Region &r : state_regions(b)) n += r.bytes;
+    *bytes = n;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_save_state(aslam_batch *b, void *h_buf, size_t bytes, void *stream) {
+    size_t need = 0;
+    aslam_status st = aslam_state_bytes(b, &need);
+    if (st != ASLAM_OK) return st;
+    if (!h_buf || bytes < need) return fail_b(b, ASLAM_ERR_INVALID_ARG, "state buffer too small");
+    char *dst = (char *)h_buf;
+    for (const Region &r : state_regions(b)) {
+        CK(cudaMemcpyAsync(dst, r.ptr, r.bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "save");
+        dst += r.bytes;
+    }
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "save synchronize");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, void *stream) {
+    size_t need = 0;
+    aslam_status st = aslam_state_bytes(b, &need);
+    if (st != ASLAM_OK) return st;
+    if (!h_buf || bytes < need) return fail_b(b, ASLAM_ERR_INVALID_ARG, "state buffer too small");
+    const char *src = (const char *)h_buf;
+    for (const Region &r : state_regions(b)) {
+        CK(cudaMemcpyAsync(r.ptr, src, r.bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream), "load");
+        src += r.bytes;
+    }
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "load synchronize");
+    return ASLAM_OK;
+}
+
+void aslam_destroy_batch(aslam_batch *b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+const char *aslam_status_string(aslam_status s) {
+    switch (s) {
+        case ASLAM_OK: return "ok";
+        case ASLAM_ERR_INVALID_ARG: return "invalid argument";
+        case ASLAM_ERR_CUDA: return "CUDA error";
+        case ASLAM_ERR_WORKSPACE: return "workspace error";
+        case ASLAM_ERR_TIMEOUT: return "device wait timed out";
+        case ASLAM_ERR_STATE: return "invalid state";
+        case ASLAM_ERR_UNSUPPORTED: return "unsupported";
+        case ASLAM_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char *aslam_last_error(const aslam_batch *b) {
+    if (b) return b->err.c_str();
+    return g_thread_error.c_str();
+}
+
+aslam_status aslam_debug_detmath(const float *d_x, const float *d_u, int32_t n, float *d_sin,
+                                 float *d_cos, float *d_log, float *d_cos2pi, uint64_t seed,
+                                 float *d_gauss, void *stream) {
+    aslam_batch *b = nullptr;
+    if (n < 0 || (n > 0 && (!d_x || !d_u || !d_sin || !d_cos || !d_log || !d_cos2pi || !d_gauss)))
+        return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "bad detmath arguments");
+    if (n == 0) return ASLAM_OK;
+    CK(launch_detmath(d_x, d_u, n, d_sin, d_cos, d_log, d_cos2pi,
+                      make_uint2((unsigned)seed, (unsigned)(seed >> 32)), d_gauss,
+                      (cudaStream_t)stream), "detmath");
+    return ASLAM_OK;
+}
+
+}  // extern "C"

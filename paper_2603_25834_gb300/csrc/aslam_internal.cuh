@@ -1,0 +1,197 @@
+// aslam_internal.cuh -- private definitions of libaslam (device helpers,
+// kernel parameter blocks, launcher declarations).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/aslam.h"
+
+namespace aslam {
+
+// ---------------------------------------------------------------------------
+// Deterministic fp32 elementary functions.  Every operation is an explicit
+// round-to-nearest intrinsic so no FMA contraction can change a bit; the
+// values feed integer state (robot cell, ray direction, range endpoint), so
+// they must be reproducible by any IEEE-754 implementation that performs
+// the same operations in the same order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Maclaurin series of sin and cos truncated after x^9 / x^10: on
+// |r| <= pi/4 the first omitted term is below 2^-26 relative.
+__device__ __forceinline__ void poly_sincos(float r, float &s, float &c) {
+    const float s3 = (float)(-1.0 / 6.0), s5 = (float)(1.0 / 120.0),
+                s7 = (float)(-1.0 / 5040.0), s9 = (float)(1.0 / 362880.0);
+    const float c2 = (float)(-1.0 / 2.0), c4 = (float)(1.0 / 24.0),
+                c6 = (float)(-1.0 / 720.0), c8 = (float)(1.0 / 40320.0),
+                c10 = (float)(-1.0 / 3628800.0);
+    float r2 = fmul(r, r);
+    float ps = fadd(s7, fmul(r2, s9));
+    ps = fadd(s5, fmul(r2, ps));
+    ps = fadd(s3, fmul(r2, ps));
+    s = fadd(r, fmul(fmul(r, r2), ps));
+    float pc = fadd(c8, fmul(r2, c10));
+    pc = fadd(c6, fmul(r2, pc));
+    pc = fadd(c4, fmul(r2, pc));
+    pc = fadd(c2, fmul(r2, pc));
+    c = fadd(1.0f, fmul(r2, pc));
+}
+
+// sin/cos of an fp32 angle: the quadrant k = rint(x * 2/pi) and remainder
+// x - k*pi/2 are formed in fp64 (exact enough for |x| << 2^20), the series
+// runs in fp32 on the remainder.
+__device__ __forceinline__ void det_sincos(float x, float &s, float &c) {
+    double k = rint(__dmul_rn((double)x, 0.63661977236758134308));
+    double rem = __dsub_rn((double)x, __dmul_rn(k, 1.57079632679489661923));
+    float ps, pc;
+    poly_sincos(__double2float_rn(rem), ps, pc);
+    switch (((int)k) & 3) {
+        case 0: s = ps; c = pc; break;
+        case 1: s = pc; c = -ps; break;
+        case 2: s = -ps; c = -pc; break;
+        default: s = -pc; c = ps; break;
+    }
+}
+
+// cos(2*pi*u), u in [0, 1): the quarter-turn index is taken on u itself,
+// where the subtraction is exact.
+__device__ __forceinline__ float det_cos2pi(float u) {
+    const float two_pi = (float)(2.0 * 3.14159265358979323846);
+    float q = rintf(fmul(u, 4.0f));
+    float a = fmul(fsub(u, fmul(q, 0.25f)), two_pi);
+    float ps, pc;
+    poly_sincos(a, ps, pc);
+    switch (((int)q) & 3) {
+        case 0: return pc;
+        case 1: return -ps;
+        case 2: return -pc;
+        default: return ps;
+    }
+}
+
+// ln(u) for a positive normal float: split u = m * 2^e with m in
+// [sqrt(1/2), sqrt(2)); ln m = 2*atanh(s), s = (m-1)/(m+1), by the odd
+// series s + s^3/3 + ... + s^11/11; ln 2 in two parts (16 + 24 bits).
+__device__ __forceinline__ float det_log(float u) {
+    unsigned bits = __float_as_uint(u);
+    int e = (int)((bits >> 23) & 0xffu) - 127;
+    unsigned mb = (bits & 0x7fffffu) | 0x3f800000u;
+    float m = __uint_as_float(mb);
+    if (mb > 0x3fb504f3u) { m = fmul(m, 0.5f); e += 1; }
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = (float)(0.69314718055994530942 - 0.693145751953125);
+    float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+    float s2 = fmul(s, s);
+    float p = fadd((float)(1.0 / 9.0), fmul(s2, (float)(1.0 / 11.0)));
+    p = fadd((float)(1.0 / 7.0), fmul(s2, p));
+    p = fadd((float)(1.0 / 5.0), fmul(s2, p));
+    p = fadd((float)(1.0 / 3.0), fmul(s2, p));
+    float ts = fadd(s, s);
+    float lnm = fadd(ts, fmul(ts, fmul(s2, p)));
+    float fe = (float)e;
+    return fadd(fadd(fmul(fe, ln2_lo), lnm), fmul(fe, ln2_hi));
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// N(0,1) for (key, env, global step, beam): Box-Muller on u1 in (0, 1]
+// (never 0) and u2 in [0, 1), each from the top 24 bits of one word.
+__device__ __forceinline__ float det_gauss(uint2 key, unsigned env, unsigned step, unsigned beam) {
+    uint4 r = philox4x32_10(make_uint4(beam, env, step, 0u), key);
+    float u1 = fmul(__uint2float_rn((r.x >> 8) + 1u), 1.0f / 16777216.0f);
+    float u2 = fmul(__uint2float_rn(r.y >> 8), 1.0f / 16777216.0f);
+    float rad = __fsqrt_rn(fmul(-2.0f, det_log(u1)));
+    return fmul(rad, det_cos2pi(u2));
+}
+
+// Fixed-point helpers: metres -> Q16 cells, and the Q16 crossing count.
+__device__ __forceinline__ int q16_of(float v_m, float res) {
+    return __float2int_rn(fmul(fdiv(v_m, res), 65536.0f));
+}
+
+// Number of grid-line crossings along one axis whose ray parameter is <= T
+// (T in Q16 cells); crossing m sits at (n0 + m*2^16) * 2^14 / ad cells.
+__device__ __forceinline__ int crossings_le(long long n0, long long ad, long long T) {
+    if (ad == 0) return 0;
+    long long lhs = T * ad - (n0 << 30);
+    if (lhs < 0) return 0;
+    return (int)(lhs >> 46) + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block of the 2-D step (passed by value).
+// ---------------------------------------------------------------------------
+struct Step2DParams {
+    int E, b_max, n_spawn, flags, reward_mode;
+    int hit_q, miss_q, clamp_q, t_episode, Tmax;
+    int window;                  // S: window side (cells) of the smem counters
+    int gt_words_max;            // smem words reserved for GT bits
+    int win_words_max;           // smem words reserved for counters
+    float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
+    double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
+    uint2 key;
+    // per-env static description
+    const int *W, *H, *B, *Vw, *Vh, *order;
+    const long long *map_off, *gtb_off, *ray_off, *visit_off;
+    const float2 *beam_cs;
+    const long long *lut;        // [2*clamp_q + 1], entropy of L in 2^-40 nats
+    const unsigned *gt_bits;
+    // mutable state
+    float *x, *y, *th, *u_prev;
+    int *t, *g, *ep, *done;
+    long long *Hq;
+    short *belief;
+    int *visit;
+    const float *spawn;
+    // per-step results
+    float *z, *z_true;
+    unsigned char *hit;
+    unsigned *dbg_counts;
+    long long *ray_cells, *gt_cells;
+    float *terms, *reward;
+    unsigned *far_cnt;
+    int *far_list, *far_n;
+    // this launch
+    const float *actions, *u_in;
+    float *out_reward, *out_obs;
+    unsigned *queue, *err;
+};
+
+constexpr int kTerms = ASLAM_N_TERMS;
+constexpr double kLutScale = 1099511627776.0;   // 2^40
+
+// Error bits of the sticky device word.
+constexpr unsigned kErrChecks = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+// Launchers (defined next to their kernels).
+cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
+                          cudaStream_t s);
+cudaError_t step2d_set_smem(size_t smem);
+cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm);
+cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,
+                           const int *H, const long long *dst_words, unsigned *bits, int E,
+                           cudaStream_t s);
+cudaError_t launch_init_state(const Step2DParams &p, cudaStream_t s);
+cudaError_t launch_gather_obs(const Step2DParams &p, float *obs, cudaStream_t s);
+cudaError_t launch_gather_reward(const Step2DParams &p, float *out, cudaStream_t s);
+cudaError_t launch_mark_done(int *done, const uint8_t *mask, int E, cudaStream_t s);
+cudaError_t launch_detmath(const float *x, const float *u, int n, float *s, float *c,
+                           float *l, float *c2, uint2 key, float *g, cudaStream_t st);
+
+}  // namespace aslam

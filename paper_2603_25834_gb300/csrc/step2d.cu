@@ -1,0 +1,640 @@
+// step2d.cu -- the batched 2-D environment step on sm_103a.
+//
+// One persistent CTA takes one environment at a time from a cost-ordered
+// work queue and runs the whole step for it:
+//   A. thread 0: reset if the env was done, action integration (Euler
+//      unicycle, Sec. III-C Eq. 4 / Sec. IV-A robot), ray origin in Q16;
+//   B. all threads: stage the env's ground-truth grid (1 bit per cell) in
+//      shared memory and clear the shared hit/miss counters;
+//   C. one thread per beam: exact fixed-point grid traversal (Amanatides-Woo
+//      order with exact 64-bit comparisons) of the ground truth until the
+//      first occupied cell (Sec. IV-A LiDAR), Gaussian range noise, then a
+//      second traversal of the belief grid to the measured endpoint that
+//      adds one miss to every crossed cell and a hit to the endpoint of a
+//      returned beam (Sec. III-D log-odds grid);
+//   D. all threads: per cell, L' = clamp(L + h*HIT + m*MISS) (one clamp per
+//      scan, so the result does not depend on beam order) and the change of
+//      the cell's entropy from a fixed-point table;
+//   E. thread 0: segmented reductions -> entropy gain, Eq. 7-17 reward,
+//      visit grid (Eq. 8-9), termination; all threads: observation (Eq. 3).
+//
+// Counters: each cell has a 16-bit (hits << 8 | misses) field, two per
+// 32-bit shared word.  Outside the 3x3 block of cells around the robot's
+// cell every point of a cell is at least one cell width from the robot, so
+// the cell subtends at most 2*asin(0.7072/1.5) = 0.982 rad and at most
+// 0.982*B/(2*pi) + 1 <= 161 beams (B <= 1024) can cross it: 8-bit fields
+// never carry.  The 3x3 block keeps full 32-bit (hits << 16 | misses)
+// counters.  A map larger than the shared window keeps an S x S window
+// around the robot in shared memory and counts the rest in global memory
+// (32-bit counters + a per-env list of touched cells).
+#include "aslam_internal.cuh"
+
+namespace aslam {
+namespace {
+
+struct EnvShared {
+    int e, W, H, B, reset, partial;
+    int Px, Py, ri, rj, col_cell;
+    int wx0, wy0, SW, SH;
+    int t, gstep;
+    float x, y, th, c, s, u_prev;
+    long long map_off, gtb_off, ray_off, Hq;
+};
+
+__device__ __forceinline__ unsigned gt_bit(const unsigned *bits, int k) {
+    return (bits[k >> 5] >> (k & 31)) & 1u;
+}
+
+__device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvShared &sh) {
+    const int W = p.W[e], H = p.H[e];
+    sh.e = e;
+    sh.W = W;
+    sh.H = H;
+    sh.B = p.B[e];
+    sh.map_off = p.map_off[e];
+    sh.gtb_off = p.gtb_off[e];
+    sh.ray_off = p.ray_off[e];
+    float x, y, th, up;
+    int t;
+    long long Hq;
+    int reset = p.done[e] != 0;
+    if (reset) {
+        int ep = p.ep[e] + 1;
+        p.ep[e] = ep;
+        const float *sp = p.spawn + ((long long)e * p.n_spawn + (ep % p.n_spawn)) * 3;
+        x = sp[0];
+        y = sp[1];
+        th = sp[2];
+        t = 0;
+        up = 0.0f;
+        Hq = (long long)W * H * p.lut[p.clamp_q];
+    } else {
+        x = p.x[e];
+        y = p.y[e];
+        th = p.th[e];
+        t = p.t[e];
+        up = p.u_prev[e];
+        Hq = p.Hq[e];
+    }
+    sh.reset = reset;
+    t += 1;
+    // Euler unicycle with the pre-step heading; heading wrapped to [-pi, pi).
+    const float pi_f = (float)3.14159265358979323846;
+    const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
+    float v = fminf(fmaxf(p.actions[2 * e], 0.0f), p.v_max);
+    float w = fminf(fmaxf(p.actions[2 * e + 1], -p.w_max), p.w_max);
+    float s0, c0;
+    det_sincos(th, s0, c0);
+    x = fadd(x, fmul(fmul(v, c0), p.dt));
+    y = fadd(y, fmul(fmul(v, s0), p.dt));
+    th = fadd(th, fmul(w, p.dt));
+    if (th >= pi_f) th = fsub(th, two_pi_f);
+    if (th < -pi_f) th = fadd(th, two_pi_f);
+    p.x[e] = x;
+    p.y[e] = y;
+    p.th[e] = th;
+    p.t[e] = t;
+    sh.x = x;
+    sh.y = y;
+    sh.th = th;
+    sh.t = t;
+    sh.u_prev = up;
+    sh.Hq = Hq;
+    sh.gstep = p.g[e];
+    int Px = q16_of(x, p.res), Py = q16_of(y, p.res);
+    sh.Px = Px;
+    sh.Py = Py;
+    int ri = Px >> 16, rj = Py >> 16;
+    sh.ri = ri;
+    sh.rj = rj;
+    int inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
+    sh.col_cell = !inside || gt_bit(p.gt_bits + sh.gtb_off, rj * W + ri);
+    float s1, c1;
+    det_sincos(th, s1, c1);
+    sh.c = c1;
+    sh.s = s1;
+    const int S = p.window;
+    int partial = (long long)W * H > (long long)S * S;
+    sh.partial = partial;
+    if (partial) {
+        int SW = min(S, W), SH = min(S, H);
+        int wx0 = min(max(ri - SW / 2, 0), W - SW) & ~7;
+        int wy0 = min(max(rj - SH / 2, 0), H - SH);
+        sh.SW = SW;
+        sh.SH = SH;
+        sh.wx0 = wx0;
+        sh.wy0 = wy0;
+    } else {
+        sh.SW = W;
+        sh.SH = H;
+        sh.wx0 = 0;
+        sh.wy0 = 0;
+    }
+}
+
+// Adds one hit or miss of the cell (i, j) (flat k) to its counter.
+template <bool kPartial>
+__device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared &sh, int i,
+                                          int j, int k, bool is_hit, unsigned *s_win,
+                                          unsigned *s_core) {
+    int di = i - sh.ri, dj = j - sh.rj;
+    if ((unsigned)(di + 1) <= 2u && (unsigned)(dj + 1) <= 2u) {
+        atomicAdd(&s_core[(dj + 1) * 3 + (di + 1)], is_hit ? 0x10000u : 1u);
+        return;
+    }
+    unsigned inc = is_hit ? 0x100u : 1u;
+    if (!kPartial) {
+        atomicAdd(&s_win[k >> 1], inc << ((k & 1) << 4));
+        return;
+    }
+    int wi = i - sh.wx0, wj = j - sh.wy0;
+    if ((unsigned)wi < (unsigned)sh.SW && (unsigned)wj < (unsigned)sh.SH) {
+        int q = wj * sh.SW + wi;
+        atomicAdd(&s_win[q >> 1], inc << ((q & 1) << 4));
+        return;
+    }
+    unsigned old = atomicAdd(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
+    if (old == 0u) {
+        // each cell is listed once per step, so the list never exceeds W*H
+        int idx = atomicAdd(&p.far_n[sh.e], 1);
+        if (idx < sh.W * sh.H) p.far_list[sh.map_off + idx] = k;
+        else atomicOr(p.err, kErrChecks);
+    }
+}
+
+// One beam: ground-truth traversal, noise, belief traversal with counting.
+template <bool kPartial>
+__device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShared &sh, int b,
+                                           const unsigned *s_gt, unsigned *s_win,
+                                           unsigned *s_core, int &rc, int &gc, float &dmin_m,
+                                           float &dmin_t) {
+    const float2 cs = p.beam_cs[sh.ray_off + b];
+    const float dx = fsub(fmul(sh.c, cs.x), fmul(sh.s, cs.y));
+    const float dy = fadd(fmul(sh.s, cs.x), fmul(sh.c, cs.y));
+    const int Dx = __float2int_rn(fmul(dx, 1073741824.0f));
+    const int Dy = __float2int_rn(fmul(dy, 1073741824.0f));
+    const int W = sh.W, H = sh.H;
+    const int Px = sh.Px, Py = sh.Py;
+    const int i0 = sh.ri, j0 = sh.rj;
+    const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
+    const int sx = (Dx > 0) - (Dx < 0), sy = (Dy > 0) - (Dy < 0);
+    const long long adx = Dx < 0 ? -(long long)Dx : (long long)Dx;
+    const long long ady = Dy < 0 ? -(long long)Dy : (long long)Dy;
+    // Q16 distance from the origin to the first grid line along each axis.
+    const long long nx0 = Dx > 0 ? ((long long)(i0 + 1) << 16) - Px
+                                 : (Dx < 0 ? (long long)Px - ((long long)i0 << 16) : 65536);
+    const long long ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - Py
+                                 : (Dy < 0 ? (long long)Py - ((long long)j0 << 16) : 65536);
+    // Next X crossing is strictly earlier than the next Y crossing iff
+    // nx/adx < ny/ady, i.e. nx*ady < ny*adx (ties step Y).
+    const long long a0 = nx0 * ady, b0 = ny0 * adx;
+    const long long dA = ady << 16, dB = adx << 16;
+    const int syW = sy * W;
+
+    bool hit = false;
+    float z_true = p.r_max;
+    int cells_gt = 0;
+    if (in0) {
+        int k = j0 * W + i0;
+        cells_gt = 1;
+        if (gt_bit(s_gt, k)) {
+            hit = true;
+            z_true = 0.0f;
+        } else {
+            const int Ks = crossings_le(nx0, adx, p.Tmax) + crossings_le(ny0, ady, p.Tmax);
+            int i = i0, j = j0;
+            long long a = a0, bb = b0;
+            bool lastx = false;
+            for (int s = 0; s < Ks; ++s) {
+                lastx = a < bb;
+                if (lastx) {
+                    i += sx;
+                    k += sx;
+                    a += dA;
+                } else {
+                    j += sy;
+                    k += syW;
+                    bb += dB;
+                }
+                if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
+                ++cells_gt;
+                if (gt_bit(s_gt, k)) {
+                    hit = true;
+                    break;
+                }
+            }
+            if (hit) {
+                // entry parameter of the hit cell: the crossing that entered it
+                const long long n = lastx ? nx0 + ((long long)(abs(i - i0) - 1) << 16)
+                                          : ny0 + ((long long)(abs(j - j0) - 1) << 16);
+                const long long ad = lastx ? adx : ady;
+                z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+            }
+        }
+    }
+    float z = z_true;
+    if (hit) {
+        const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.gstep, (unsigned)b);
+        z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, gz)), 0.0f), p.r_max);
+    }
+    const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
+
+    int cells_upd = 0;
+    if (in0) {
+        const int Ku = crossings_le(nx0, adx, Tz) + crossings_le(ny0, ady, Tz);
+        int i = i0, j = j0, k = j0 * W + i0;
+        long long a = a0, bb = b0;
+        for (int s = 0;; ++s) {
+            const bool last = s == Ku;
+            add_count<kPartial>(p, sh, i, j, k, last && hit, s_win, s_core);
+            ++cells_upd;
+            if (last) break;
+            if (a < bb) {
+                i += sx;
+                k += sx;
+                a += dA;
+            } else {
+                j += sy;
+                k += syW;
+                bb += dB;
+            }
+            if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
+        }
+    }
+    const long long ro = sh.ray_off + b;
+    p.z[ro] = z;
+    if (p.flags & ASLAM_FLAG_DEBUG) {
+        p.z_true[ro] = z_true;
+        p.hit[ro] = hit ? 1 : 0;
+    }
+    if (p.out_obs) p.out_obs[(long long)sh.e * (p.b_max + 2) + b] = z;
+    rc += cells_upd;
+    gc += cells_gt;
+    dmin_m = fminf(dmin_m, z);
+    dmin_t = fminf(dmin_t, z_true);
+}
+
+// Applies (h, m) to one cell's log-odds; returns the entropy change (2^-40 nats).
+__device__ __forceinline__ long long apply_cell(const Step2DParams &p, short &L, unsigned h,
+                                                unsigned m) {
+    int l0 = L;
+    int l1 = l0 + (int)h * p.hit_q + (int)m * p.miss_q;
+    l1 = min(max(l1, -p.clamp_q), p.clamp_q);
+    L = (short)l1;
+    return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
+}
+
+// Applies the 16-bit counters of 8 consecutive cells held in one uint4.
+__device__ __forceinline__ long long apply8(const Step2DParams &p, uint4 cw, short *Lg,
+                                            unsigned *dbg) {
+    int4 lv = *reinterpret_cast<int4 *>(Lg);
+    short *L = reinterpret_cast<short *>(&lv);
+    unsigned wds[4] = {cw.x, cw.y, cw.z, cw.w};
+    long long dh = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        unsigned c16 = (wds[q >> 1] >> ((q & 1) << 4)) & 0xffffu;
+        if (c16) dh += apply_cell(p, L[q], c16 >> 8, c16 & 0xffu);
+        if (dbg) dbg[q] = ((c16 >> 8) << 16) | (c16 & 0xffu);
+    }
+    *reinterpret_cast<int4 *>(Lg) = lv;
+    return dh;
+}
+
+__global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *s_gt = smem;
+    unsigned *s_win = smem + p.gt_words_max;
+    __shared__ unsigned s_core[9];
+    __shared__ EnvShared sh;
+    __shared__ long long r_dh[32];
+    __shared__ int r_rc[32], r_gc[32];
+    __shared__ float r_dm[32], r_dt[32];
+    __shared__ int s_item, s_far_n;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(p.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= p.E) {
+            // Every CTA takes exactly one out-of-range item before leaving;
+            // the last CTA to leave re-arms the queue for the next launch.
+            if (tid == 0) {
+                __threadfence();
+                if (atomicAdd(p.queue + 1, 1u) == gridDim.x - 1) {
+                    p.queue[0] = 0u;
+                    p.queue[1] = 0u;
+                    __threadfence();
+                }
+            }
+            break;
+        }
+        if (tid == 0) env_prologue(p, p.order[item], sh);
+        __syncthreads();
+
+        // ---- B: reset, stage ground truth, clear counters --------------------
+        const int e = sh.e, W = sh.W, H = sh.H;
+        const long long ncell = (long long)W * H;
+        const int nch = (int)((ncell + 7) >> 3);
+        if (sh.reset) {
+            int4 *bz = reinterpret_cast<int4 *>(p.belief + sh.map_off);
+            for (int q = tid; q < nch; q += nt) bz[q] = make_int4(0, 0, 0, 0);
+            const long long vo = p.visit_off[e], vn = p.visit_off[e + 1] - vo;
+            for (long long q = tid; q < vn; q += nt) p.visit[vo + q] = -1;
+        }
+        {
+            const int words = (int)((ncell + 31) >> 5);
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + sh.gtb_off);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
+            for (int q = tid; q < (words + 3) >> 2; q += nt) dst[q] = __ldg(&src[q]);
+            const int cw = sh.partial ? (sh.SW * sh.SH + 1) >> 1 : (int)((ncell + 1) >> 1);
+            uint4 *wz = reinterpret_cast<uint4 *>(s_win);
+            for (int q = tid; q < (cw + 3) >> 2; q += nt) wz[q] = make_uint4(0, 0, 0, 0);
+            if (tid < 9) s_core[tid] = 0;
+            if (debug && sh.partial) {
+                for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0;
+            }
+        }
+        __syncthreads();
+
+        // ---- C: beams --------------------------------------------------------
+        int rc = 0, gc = 0;
+        float dmin_m = p.r_max, dmin_t = p.r_max;
+        if (sh.partial) {
+            for (int b = tid; b < sh.B; b += nt)
+                trace_beam<true>(p, sh, b, s_gt, s_win, s_core, rc, gc, dmin_m, dmin_t);
+        } else {
+            for (int b = tid; b < sh.B; b += nt)
+                trace_beam<false>(p, sh, b, s_gt, s_win, s_core, rc, gc, dmin_m, dmin_t);
+        }
+        __syncthreads();
+
+        // ---- D: apply counters to the log-odds -------------------------------
+        long long dh = 0;
+        short *Lenv = p.belief + sh.map_off;
+        unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
+        if (!sh.partial) {
+            const uint4 *cw4 = reinterpret_cast<const uint4 *>(s_win);
+            for (int q = tid; q < nch; q += nt) {
+                uint4 cw = cw4[q];
+                if ((cw.x | cw.y | cw.z | cw.w) == 0u) {
+                    if (dbg) {
+                        for (int r = 0; r < 8 && 8LL * q + r < ncell; ++r) dbg[8 * q + r] = 0u;
+                    }
+                    continue;
+                }
+                dh += apply8(p, cw, Lenv + 8LL * q, dbg ? dbg + 8LL * q : nullptr);
+            }
+        } else {
+            const int SW = sh.SW, SH = sh.SH, rch = SW >> 3;
+            const uint4 *cw4 = reinterpret_cast<const uint4 *>(s_win);
+            for (int q = tid; q < SH * rch; q += nt) {
+                const int jj = q / rch, cc = q - jj * rch;
+                uint4 cw = cw4[(jj * SW >> 3) + cc];
+                if ((cw.x | cw.y | cw.z | cw.w) == 0u) continue;
+                const long long k = (long long)(sh.wy0 + jj) * W + sh.wx0 + 8 * cc;
+                dh += apply8(p, cw, Lenv + k, dbg ? dbg + k : nullptr);
+            }
+            if (tid == 0) s_far_n = atomicAdd(&p.far_n[e], 0);
+            __syncthreads();
+            const int nf = s_far_n;
+            for (int q = tid; q < nf; q += nt) {
+                const int k = __ldcg(&p.far_list[sh.map_off + q]);
+                const unsigned c = atomicExch(&p.far_cnt[sh.map_off + k], 0u);
+                if (c) dh += apply_cell(p, Lenv[k], c >> 16, c & 0xffffu);
+                if (dbg) dbg[k] = c;
+            }
+        }
+        __syncthreads();
+        if (tid < 9) {
+            const int i = sh.ri + tid % 3 - 1, j = sh.rj + tid / 3 - 1;
+            if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
+                const unsigned c = s_core[tid];
+                const long long k = (long long)j * W + i;
+                if (c) dh += apply_cell(p, Lenv[k], c >> 16, c & 0xffffu);
+                if (dbg) dbg[k] = c;
+            }
+        }
+
+        // ---- E: reductions, reward, observation ------------------------------
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            dh += __shfl_down_sync(0xffffffffu, dh, o);
+            rc += __shfl_down_sync(0xffffffffu, rc, o);
+            gc += __shfl_down_sync(0xffffffffu, gc, o);
+            dmin_m = fminf(dmin_m, __shfl_down_sync(0xffffffffu, dmin_m, o));
+            dmin_t = fminf(dmin_t, __shfl_down_sync(0xffffffffu, dmin_t, o));
+        }
+        if (lane == 0) {
+            r_dh[warp] = dh;
+            r_rc[warp] = rc;
+            r_gc[warp] = gc;
+            r_dm[warp] = dmin_m;
+            r_dt[warp] = dmin_t;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long dHq = 0;
+            long long RC = 0, GC = 0;
+            float dm = p.r_max, dtr = p.r_max;
+            for (int w = 0; w < nwarps; ++w) {
+                dHq += r_dh[w];
+                RC += r_rc[w];
+                GC += r_gc[w];
+                dm = fminf(dm, r_dm[w]);
+                dtr = fminf(dtr, r_dt[w]);
+            }
+            if (sh.partial) p.far_n[e] = 0;
+            const long long Hq = sh.Hq + dHq;
+            p.Hq[e] = Hq;
+            const double dH = -(double)dHq / kLutScale;    // H_{t-1} - H_t (nats)
+            const int col = sh.col_cell || (dtr < p.d_crash);
+            // Visit grid at the ground-truth position (Eq. 8-9).
+            const int Vw = p.Vw[e], Vh = p.Vh[e];
+            const float vx0 = fmul(-0.5f, fmul((float)W, p.res));
+            const float vy0 = fmul(-0.5f, fmul((float)H, p.res));
+            int vi = (int)floorf(fdiv(fsub(sh.x, vx0), p.visit_cell));
+            int vj = (int)floorf(fdiv(fsub(sh.y, vy0), p.visit_cell));
+            vi = min(max(vi, 0), Vw - 1);
+            vj = min(max(vj, 0), Vh - 1);
+            int *vc = p.visit + p.visit_off[e] + (long long)vj * Vw + vi;
+            const int last = *vc;
+            double dcells = 1.0;
+            if (last >= 0) dcells = fmin(fmax(0.5 * (double)(sh.t - last) / (double)p.t_episode, 0.0), 1.0);
+            *vc = sh.t;
+            // Reward terms, Eq. 7-17.
+            const double Up = (double)sh.u_prev;
+            const double U = p.u_in ? (double)p.u_in[e] : 0.0;
+            double cg = fmin(fmax((p.u_hi - Up) / p.u_hi, 0.0), 1.0);
+            cg = cg * cg;
+            const double iota = fmin(fmax(fmax(Up - U, 0.0) / p.kappa, 0.0), 1.0);
+            const double I = cg + (1.0 - cg) * iota;
+            const double r_explore = p.lam_explore * dcells * I;
+            const double eU = exp(Up);
+            const double r_abs = p.lam_abs * eU * Up;
+            const double r_delta = p.lam_delta * eU * (Up - U);
+            const double alpha = fmin(fmax(((double)dm - (double)p.d_crash) /
+                                               ((double)p.d_full - (double)p.d_crash), 0.0), 1.0);
+            const double r_explore_s = r_explore * alpha;
+            const double r_delta_s = (Up - U > 0.0) ? r_delta * alpha : r_delta;
+            const double R = col ? -p.lam_col : (r_explore_s - r_abs + r_delta_s);
+            float *tm = p.terms + (long long)e * kTerms;
+            tm[0] = (float)dH;
+            tm[1] = (float)dcells;
+            tm[2] = (float)I;
+            tm[3] = (float)alpha;
+            tm[4] = (float)r_explore_s;
+            tm[5] = (float)r_abs;
+            tm[6] = (float)r_delta_s;
+            tm[7] = (float)R;
+            tm[8] = (float)col;
+            tm[9] = dm;
+            tm[10] = dtr;
+            tm[11] = (float)((double)Hq / kLutScale);
+            const float rew = p.reward_mode == ASLAM_REWARD_COMPOSITE ? (float)R : (float)dH;
+            p.reward[e] = rew;
+            if (p.out_reward) p.out_reward[e] = rew;
+            p.done[e] = (col || sh.t >= p.t_episode) ? 1 : 0;
+            p.u_prev[e] = (float)U;
+            p.g[e] = sh.gstep + 1;
+            p.ray_cells[e] = RC;
+            p.gt_cells[e] = GC;
+            if (p.out_obs) {
+                float *o = p.out_obs + (long long)e * (p.b_max + 2);
+                o[p.b_max] = sh.th;
+                o[p.b_max + 1] = (float)U;
+            }
+        }
+        if (p.out_obs) {
+            float *o = p.out_obs + (long long)e * (p.b_max + 2);
+            for (int b = sh.B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void pack_gt_kernel(const uint8_t *gt, const long long *src_off, const int *W,
+                               const int *H, const long long *dst_words, unsigned *bits) {
+    const int e = blockIdx.x;
+    const long long n = (long long)W[e] * H[e];
+    const long long words = (n + 31) >> 5;
+    const long long padded = (words + 3) & ~3LL;
+    const uint8_t *g = gt + src_off[e];
+    unsigned *dst = bits + dst_words[e];
+    for (long long w = threadIdx.x; w < padded; w += blockDim.x) {
+        unsigned v = 0;
+        for (int q = 0; q < 32; ++q) {
+            const long long k = w * 32 + q;
+            if (k < n && g[k]) v |= 1u << q;
+        }
+        dst[w] = v;
+    }
+}
+
+__global__ void init_state_kernel(const Step2DParams p) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += gridDim.x * blockDim.x) {
+        const float *sp = p.spawn + (long long)e * p.n_spawn * 3;
+        p.x[e] = sp[0];
+        p.y[e] = sp[1];
+        p.th[e] = sp[2];
+        p.u_prev[e] = 0.0f;
+        p.t[e] = 0;
+        p.g[e] = 0;
+        p.ep[e] = 0;
+        p.done[e] = 0;
+        p.Hq[e] = (long long)p.W[e] * p.H[e] * p.lut[p.clamp_q];
+        p.far_n[e] = 0;
+        p.reward[e] = 0.0f;
+    }
+}
+
+__global__ void gather_obs_kernel(const Step2DParams p, float *obs) {
+    const int e = blockIdx.x;
+    const int B = p.B[e];
+    float *o = obs + (long long)e * (p.b_max + 2);
+    const float *z = p.z + p.ray_off[e];
+    for (int b = threadIdx.x; b < p.b_max; b += blockDim.x) o[b] = b < B ? z[b] : p.r_max;
+    if (threadIdx.x == 0) {
+        o[p.b_max] = p.th[e];
+        o[p.b_max + 1] = p.u_prev[e];
+    }
+}
+
+__global__ void gather_reward_kernel(const Step2DParams p, float *out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += gridDim.x * blockDim.x)
+        out[e] = p.reward[e];
+}
+
+__global__ void mark_done_kernel(int *done, const uint8_t *mask, int E) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+        if (!mask || mask[e]) done[e] = 1;
+}
+
+__global__ void detmath_kernel(const float *x, const float *u, int n, float *s, float *c,
+                               float *l, float *c2, uint2 key, float *g) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        float ss, cc;
+        det_sincos(x[q], ss, cc);
+        s[q] = ss;
+        c[q] = cc;
+        l[q] = det_log(u[q]);
+        c2[q] = det_cos2pi(fsub(u[q], floorf(u[q])));
+        g[q] = det_gauss(key, (unsigned)q % 7u, (unsigned)q / 7u, (unsigned)q);
+    }
+}
+
+}  // namespace
+
+cudaError_t step2d_set_smem(size_t smem) {
+    return cudaFuncSetAttribute(step2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step2d_kernel, block, smem);
+}
+
+cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
+                          cudaStream_t s) {
+    step2d_kernel<<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,
+                           const int *H, const long long *dst_words, unsigned *bits, int E,
+                           cudaStream_t s) {
+    pack_gt_kernel<<<E, 256, 0, s>>>(gt, src_off, W, H, dst_words, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const Step2DParams &p, cudaStream_t s) {
+    init_state_kernel<<<(p.E + 255) / 256, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_obs(const Step2DParams &p, float *obs, cudaStream_t s) {
+    gather_obs_kernel<<<p.E, 128, 0, s>>>(p, obs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_reward(const Step2DParams &p, float *out, cudaStream_t s) {
+    gather_reward_kernel<<<(p.E + 255) / 256, 256, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark_done(int *done, const uint8_t *mask, int E, cudaStream_t s) {
+    mark_done_kernel<<<(E + 255) / 256, 256, 0, s>>>(done, mask, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detmath(const float *x, const float *u, int n, float *s, float *c,
+                           float *l, float *c2, uint2 key, float *g, cudaStream_t st) {
+    detmath_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, u, n, s, c, l, c2, key, g);
+    return cudaGetLastError();
+}
+
+}  // namespace aslam

@@ -30,14 +30,26 @@ class World2D:
 
 
 def _raster_rects_discs(W, H, res, rects, discs):
-    cx = (np.arange(W, dtype=np.float64) + 0.5) * res
-    cy = (np.arange(H, dtype=np.float64) + 0.5) * res
-    X, Y = np.meshgrid(cx, cy)
+    """Occupancy by cell centre, touching only each shape's bounding box."""
     occ = np.zeros((H, W), dtype=np.uint8)
+
+    def box(x0, y0, hx, hy):
+        i0 = max(int(np.floor((x0 - hx) / res)) - 1, 0)
+        i1 = min(int(np.ceil((x0 + hx) / res)) + 1, W)
+        j0 = max(int(np.floor((y0 - hy) / res)) - 1, 0)
+        j1 = min(int(np.ceil((y0 + hy) / res)) + 1, H)
+        cx = (np.arange(i0, i1, dtype=np.float64) + 0.5) * res
+        cy = (np.arange(j0, j1, dtype=np.float64) + 0.5) * res
+        return i0, i1, j0, j1, cx[None, :], cy[:, None]
+
     for (x0, y0, w, h) in rects:
-        occ |= ((np.abs(X - x0) <= w / 2) & (np.abs(Y - y0) <= h / 2)).astype(np.uint8)
+        i0, i1, j0, j1, X, Y = box(x0, y0, w / 2, h / 2)
+        if i1 > i0 and j1 > j0:
+            occ[j0:j1, i0:i1] |= ((np.abs(X - x0) <= w / 2) & (np.abs(Y - y0) <= h / 2)).astype(np.uint8)
     for (x0, y0, r) in discs:
-        occ |= (((X - x0) ** 2 + (Y - y0) ** 2) <= r * r).astype(np.uint8)
+        i0, i1, j0, j1, X, Y = box(x0, y0, r, r)
+        if i1 > i0 and j1 > j0:
+            occ[j0:j1, i0:i1] |= (((X - x0) ** 2 + (Y - y0) ** 2) <= r * r).astype(np.uint8)
     return occ
 
 
@@ -63,9 +75,7 @@ def make_world_2d(W, H, res, rng, n_rect=(8, 8), rect_side=(0.3, 1.5),
 def spawn_poses_2d(world: World2D, K, rng, clearance=0.3, max_tries=200000):
     """K free poses (x, y, theta) with no occupied cell centre within `clearance` m."""
     W, H, res, occ = world.W, world.H, world.res, world.occ
-    oy, ox = np.nonzero(occ)
-    ocx = (ox + 0.5) * res
-    ocy = (oy + 0.5) * res
+    r = int(np.ceil(clearance / res)) + 1
     out = []
     tries = 0
     while len(out) < K:
@@ -74,8 +84,12 @@ def spawn_poses_2d(world: World2D, K, rng, clearance=0.3, max_tries=200000):
             raise RuntimeError("could not place spawn poses with the requested clearance")
         x = rng.uniform(clearance, W * res - clearance)
         y = rng.uniform(clearance, H * res - clearance)
-        if ocx.size:
-            d2 = (ocx - x) ** 2 + (ocy - y) ** 2
+        ci, cj = int(x / res), int(y / res)
+        i0, i1 = max(ci - r, 0), min(ci + r + 1, W)
+        j0, j1 = max(cj - r, 0), min(cj + r + 1, H)
+        oy, ox = np.nonzero(occ[j0:j1, i0:i1])
+        if ox.size:
+            d2 = ((ox + i0 + 0.5) * res - x) ** 2 + ((oy + j0 + 0.5) * res - y) ** 2
             if d2.min() < clearance * clearance:
                 continue
         th = rng.uniform(-math.pi, math.pi)
@@ -159,6 +173,17 @@ def custom_2d(occs, beams, res, spawn):
     gt = np.concatenate([np.ascontiguousarray(o, dtype=np.uint8).reshape(-1) for o in occs])
     return Batch2DInputs(map_w, map_h, np.asarray(beams, dtype=np.int32), float(res), gt, off,
                          np.ascontiguousarray(spawn, dtype=np.float32))
+
+
+def subset(inputs, envs):
+    """The listed envs of a batch as a batch of their own (same worlds and spawns)."""
+    occs, beams, spawn = [], [], []
+    for e in envs:
+        a, b = int(inputs.map_off[e]), int(inputs.map_off[e + 1])
+        occs.append(inputs.gt[a:b].reshape(int(inputs.map_h[e]), int(inputs.map_w[e])))
+        beams.append(int(inputs.n_beams[e]))
+        spawn.append(inputs.spawn[e])
+    return custom_2d(occs, beams, inputs.res, np.stack(spawn))
 
 
 def random_actions(steps, E, seed, v_max=0.5, w_max=1.0):
