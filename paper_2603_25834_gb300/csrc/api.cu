@@ -21,22 +21,22 @@ namespace {
 thread_local std::string g_thread_error;
 
 constexpr size_t kAlign = 256;
-constexpr int kCellPad = 64;     // env grids start on 128-byte (int16) boundaries
+constexpr int kCellPad = 256;    // env grids start on 512-byte (int16) boundaries
 
 struct HostInfo {
-    int E = 0, b_max = 0;
-    std::vector<int> W, H, B, Vw, Vh;
+    int E = 0, b_max = 0, r8_max = 1;
+    std::vector<int> W, H, B, Vw, Vh, R8;
     std::vector<long long> map_off, gtb_off, ray_off, visit_off;
     int gt_words_max = 0;
 };
 
 struct Offsets {
-    size_t W, H, B, Vw, Vh, order, map_off, gtb_off, ray_off, visit_off, src_off;
+    size_t W, H, B, Vw, Vh, R8, order, map_off, gtb_off, ray_off, visit_off, src_off;
     size_t beam_cs, lut, gt_bits;
     size_t x, y, th, u_prev, t, g, ep, done, Hq;
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
-    size_t far_cnt, far_list, far_n, queue, err, tune_actions;
+    size_t far_cnt, far_bits, queue, err, tune_actions;
     size_t total;
 };
 
@@ -49,6 +49,25 @@ void visit_dims(int W, int H, float res, float vc, int *Vw, int *Vh) {
     int a = (int)std::ceil(ew / vc), b = (int)std::ceil(eh / vc);
     *Vw = a < 1 ? 1 : a;
     *Vh = b < 1 ? 1 : b;
+}
+
+// Smallest Chebyshev distance d (>= 2) from the robot's cell beyond which no
+// cell can be crossed by more than 15 of the B beams: a cell at distance d
+// has its centre >= d - 1/2 cells away and lies in a disc of radius
+// sqrt(2)/2 about it, so the beams crossing it span an angle of at most
+// 2*asin(0.70711/(d - 1/2)) (+2e-6 rad for fp32 direction rounding).
+int near_radius(int B, double fov) {
+    if (B <= 15) return 1;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const bool full_turn = fov <= 0.0 || fov >= two_pi - 1e-9;
+    const double dbeta = full_turn ? two_pi / B : fov / (double)(B - 1);
+    for (int d = 2; d < 4096; ++d) {
+        const double x = 0.70711 / ((double)d - 0.5);
+        if (x >= 1.0) continue;
+        const int n = (int)std::floor((2.0 * std::asin(x) + 2e-6) / dbeta) + 1;
+        if (n <= 15) return d;
+    }
+    return 4096;
 }
 
 bool validate(const aslam_config *c, std::string *msg) {
@@ -99,6 +118,8 @@ void host_info(const aslam_config *c, HostInfo *hi) {
     hi->b_max = *std::max_element(hi->B.begin(), hi->B.end());
     hi->Vw.resize(E);
     hi->Vh.resize(E);
+    hi->R8.resize(E);
+    hi->r8_max = 1;
     hi->map_off.assign(E + 1, 0);
     hi->gtb_off.assign(E + 1, 0);
     hi->ray_off.assign(E + 1, 0);
@@ -113,6 +134,8 @@ void host_info(const aslam_config *c, HostInfo *hi) {
         visit_dims(hi->W[e], hi->H[e], c->res_m, c->visit_cell_m, &hi->Vw[e], &hi->Vh[e]);
         hi->visit_off[e + 1] = hi->visit_off[e] + (long long)hi->Vw[e] * hi->Vh[e];
         hi->gt_words_max = std::max(hi->gt_words_max, (int)words);
+        hi->R8[e] = near_radius(hi->B[e], (double)c->fov_rad);
+        hi->r8_max = std::max(hi->r8_max, hi->R8[e]);
     }
 }
 
@@ -133,6 +156,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.B = add(4 * E);
     o.Vw = add(4 * E);
     o.Vh = add(4 * E);
+    o.R8 = add(4 * E);
     o.order = add(4 * E);
     o.map_off = add(8 * (E + 1));
     o.gtb_off = add(8 * (E + 1));
@@ -163,8 +187,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.terms = add(4 * E * kTerms);
     o.reward = add(4 * E);
     o.far_cnt = add(4 * cells);
-    o.far_list = add(4 * cells);
-    o.far_n = add(4 * E);
+    o.far_bits = add(cells / 64);
     o.queue = add(8);          // {next item, CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
@@ -214,21 +237,26 @@ T *at(aslam_batch *b, size_t off) {
     return reinterpret_cast<T *>(b->ws + off);
 }
 
-// Shared-memory needs of a (window side S) choice: words of ground-truth
-// bits plus words of 16-bit counters, for the largest env.
+// Shared-memory needs of a window side S: words of 8-bit counters for the
+// largest env (the whole map when it fits in S x S, else an S x S window).
 bool plan_window(const HostInfo &hi, int S, int *win_words, std::string *msg) {
     int ww = 0;
     for (int e = 0; e < hi.E; ++e) {
         const long long n = (long long)hi.W[e] * hi.H[e];
         long long need;
         if (n <= (long long)S * S) {
-            need = (n + 1) / 2;
+            need = (n + 3) / 4;
         } else {
+            const int SW = std::min(S, hi.W[e]), SH = std::min(S, hi.H[e]);
             if (hi.W[e] % 8) {
                 *msg = "a map larger than the shared window needs a width that is a multiple of 8";
                 return false;
             }
-            need = ((long long)std::min(S, hi.W[e]) * std::min(S, hi.H[e]) + 1) / 2;
+            if (SW < 2 * hi.R8[e] + 14 || SH < 2 * hi.R8[e] + 14) {
+                *msg = "shared window too small for the beam count";
+                return false;
+            }
+            need = ((long long)SW * SH + 3) / 4;
         }
         ww = std::max(ww, (int)pad_to((size_t)need, 4));
     }
@@ -236,11 +264,16 @@ bool plan_window(const HostInfo &hi, int S, int *win_words, std::string *msg) {
     return true;
 }
 
+int near_words(const HostInfo &hi) {
+    const int nb = 2 * hi.r8_max - 1;
+    return (int)pad_to((size_t)nb * nb, 4);
+}
+
 constexpr int kStaticSmem = 2048;
 
 int auto_window(const HostInfo &hi, int smem_optin) {
-    long long budget_words = (smem_optin - kStaticSmem) / 4 - hi.gt_words_max;
-    int S = (int)std::floor(std::sqrt(2.0 * (double)budget_words));
+    long long budget_words = (smem_optin - kStaticSmem) / 4 - hi.gt_words_max - near_words(hi);
+    int S = (int)std::floor(std::sqrt(4.0 * (double)budget_words));
     S &= ~7;
     return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
 }
@@ -249,7 +282,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     int ww = 0;
     std::string msg;
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
-    const size_t smem = 4 * ((size_t)b->hi.gt_words_max + ww);
+    const size_t smem = 4 * ((size_t)b->hi.gt_words_max + ww + near_words(b->hi));
     if (smem + kStaticSmem > (size_t)b->smem_optin)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
     CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
@@ -263,6 +296,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     b->p.window = S;
     b->p.gt_words_max = b->hi.gt_words_max;
     b->p.win_words_max = ww;
+    b->p.near_words_max = near_words(b->hi);
     return ASLAM_OK;
 }
 
@@ -276,6 +310,7 @@ aslam_status reset_all(aslam_batch *b, cudaStream_t s) {
     CK(cudaMemsetAsync(b->p.belief, 0, 2 * cells, s), "memset belief");
     CK(cudaMemsetAsync(b->p.visit, 0xff, 4 * (size_t)b->hi.visit_off[b->hi.E], s), "memset visit");
     CK(cudaMemsetAsync(b->p.far_cnt, 0, 4 * cells, s), "memset far counters");
+    CK(cudaMemsetAsync(b->p.far_bits, 0, cells / 64, s), "memset far bitmap");
     if (b->p.dbg_counts) CK(cudaMemsetAsync(b->p.dbg_counts, 0, 4 * cells, s), "memset debug");
     CK(launch_init_state(b->p, s), "init state");
     return ASLAM_OK;
@@ -411,6 +446,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.B = at<int>(b, o.B);
         p.Vw = at<int>(b, o.Vw);
         p.Vh = at<int>(b, o.Vh);
+        p.R8 = at<int>(b, o.R8);
         p.order = at<int>(b, o.order);
         p.map_off = at<long long>(b, o.map_off);
         p.gtb_off = at<long long>(b, o.gtb_off);
@@ -441,8 +477,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.terms = at<float>(b, o.terms);
         p.reward = at<float>(b, o.reward);
         p.far_cnt = at<unsigned>(b, o.far_cnt);
-        p.far_list = at<int>(b, o.far_list);
-        p.far_n = at<int>(b, o.far_n);
+        p.far_bits = at<unsigned>(b, o.far_bits);
         p.queue = at<unsigned>(b, o.queue);
         p.err = at<unsigned>(b, o.err);
 
@@ -492,6 +527,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 == cudaSuccess) e1 = h2d((void *)p.B, hi.B.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.Vw, hi.Vw.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.Vh, hi.Vh.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.R8, hi.R8.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.order, b->order.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.map_off, hi.map_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d((void *)p.gtb_off, hi.gtb_off.data(), 8 * (size_t)(E + 1));

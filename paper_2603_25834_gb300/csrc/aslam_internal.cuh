@@ -139,14 +139,15 @@ __device__ __forceinline__ int crossings_le(long long n0, long long ad, long lon
 struct Step2DParams {
     int E, b_max, n_spawn, flags, reward_mode;
     int hit_q, miss_q, clamp_q, t_episode, Tmax;
-    int window;                  // S: window side (cells) of the smem counters
-    int gt_words_max;            // smem words reserved for GT bits
-    int win_words_max;           // smem words reserved for counters
+    int window;                  // S: window side (cells) of the shared 8-bit counters
+    int gt_words_max;            // shared words reserved for ground-truth bits
+    int win_words_max;           // shared words reserved for 8-bit counters (4 cells/word)
+    int near_words_max;          // shared words reserved for the 32-bit near block
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     uint2 key;
     // per-env static description
-    const int *W, *H, *B, *Vw, *Vh, *order;
+    const int *W, *H, *B, *Vw, *Vh, *order, *R8;
     const long long *map_off, *gtb_off, *ray_off, *visit_off;
     const float2 *beam_cs;
     const long long *lut;        // [2*clamp_q + 1], entropy of L in 2^-40 nats
@@ -164,8 +165,8 @@ struct Step2DParams {
     unsigned *dbg_counts;
     long long *ray_cells, *gt_cells;
     float *terms, *reward;
-    unsigned *far_cnt;
-    int *far_list, *far_n;
+    unsigned *far_cnt;           // [sum cells] (hits << 16 | misses) outside the window
+    unsigned *far_bits;          // [sum cells / 256] touched 8-cell chunks outside the window
     // this launch
     const float *actions, *u_in;
     float *out_reward, *out_obs;

@@ -18,22 +18,25 @@
 //   E. thread 0: segmented reductions -> entropy gain, Eq. 7-17 reward,
 //      visit grid (Eq. 8-9), termination; all threads: observation (Eq. 3).
 //
-// Counters: each cell has a 16-bit (hits << 8 | misses) field, two per
-// 32-bit shared word.  Outside the 3x3 block of cells around the robot's
-// cell every point of a cell is at least one cell width from the robot, so
-// the cell subtends at most 2*asin(0.7072/1.5) = 0.982 rad and at most
-// 0.982*B/(2*pi) + 1 <= 161 beams (B <= 1024) can cross it: 8-bit fields
-// never carry.  The 3x3 block keeps full 32-bit (hits << 16 | misses)
-// counters.  A map larger than the shared window keeps an S x S window
-// around the robot in shared memory and counts the rest in global memory
-// (32-bit counters + a per-env list of touched cells).
+// Counters.  A cell at Chebyshev distance d >= 2 from the robot's cell has
+// its centre at least d - 1/2 cells from the robot and lies in a disc of
+// radius sqrt(2)/2 around that centre, so every beam crossing it is within
+// asin(0.70711 / (d - 1/2)) of the direction to the centre: at most
+// floor(2*asin(0.70711/(d - 1/2)) / dbeta) + 1 beams of spacing dbeta can
+// cross it.  R8 (per env, from B) is the smallest d for which that bound is
+// <= 15.  Cells at distance >= R8 therefore get 8-bit (hits:4 | misses:4)
+// counters, four per 32-bit shared word, which never carry; the
+// (2*R8-1)^2 block around the robot keeps 32-bit (hits << 16 | misses)
+// counters.  A map too large for shared memory keeps an S x S window around
+// the robot there and counts the rest with fire-and-forget global atomics
+// (32-bit counters plus a bitmap of touched 8-cell chunks).
 #include "aslam_internal.cuh"
 
 namespace aslam {
 namespace {
 
 struct EnvShared {
-    int e, W, H, B, reset, partial;
+    int e, W, H, B, reset, partial, R8, NB;
     int Px, Py, ri, rj, col_cell;
     int wx0, wy0, SW, SH;
     int t, gstep;
@@ -45,12 +48,33 @@ __device__ __forceinline__ unsigned gt_bit(const unsigned *bits, int k) {
     return (bits[k >> 5] >> (k & 31)) & 1u;
 }
 
+// L2 prefetch of a byte range (bulk-copy engine, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void *ptr, unsigned bytes) {
+    bytes &= ~15u;
+    if (bytes == 0u) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+// Grab the next queue item; for an in-range item prefetch what its step reads.
+__device__ __forceinline__ int grab_item(const Step2DParams &p) {
+    const int item = (int)atomicAdd(p.queue, 1u);
+    if (item < p.E) {
+        const int e = p.order[item];
+        const long long n = (long long)p.W[e] * p.H[e];
+        prefetch_l2(p.gt_bits + p.gtb_off[e], (unsigned)(((n + 127) >> 7) << 4));
+        prefetch_l2(p.belief + p.map_off[e], (unsigned)min(2 * n, (long long)(1 << 30)));
+    }
+    return item;
+}
+
 __device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvShared &sh) {
     const int W = p.W[e], H = p.H[e];
     sh.e = e;
     sh.W = W;
     sh.H = H;
     sh.B = p.B[e];
+    sh.R8 = p.R8[e];
+    sh.NB = 2 * sh.R8 - 1;
     sh.map_off = p.map_off[e];
     sh.gtb_off = p.gtb_off[e];
     sh.ray_off = p.ray_off[e];
@@ -118,12 +142,10 @@ __device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvSh
     sh.partial = partial;
     if (partial) {
         int SW = min(S, W), SH = min(S, H);
-        int wx0 = min(max(ri - SW / 2, 0), W - SW) & ~7;
-        int wy0 = min(max(rj - SH / 2, 0), H - SH);
         sh.SW = SW;
         sh.SH = SH;
-        sh.wx0 = wx0;
-        sh.wy0 = wy0;
+        sh.wx0 = min(max(ri - SW / 2, 0), W - SW) & ~7;
+        sh.wy0 = min(max(rj - SH / 2, 0), H - SH);
     } else {
         sh.SW = W;
         sh.SH = H;
@@ -132,41 +154,36 @@ __device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvSh
     }
 }
 
-// Adds one hit or miss of the cell (i, j) (flat k) to its counter.
+// Adds (or, with sign < 0, removes) one hit or miss of cell (i, j) (flat k).
 template <bool kPartial>
 __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared &sh, int i,
                                           int j, int k, bool is_hit, unsigned *s_win,
-                                          unsigned *s_core) {
-    int di = i - sh.ri, dj = j - sh.rj;
-    if ((unsigned)(di + 1) <= 2u && (unsigned)(dj + 1) <= 2u) {
-        atomicAdd(&s_core[(dj + 1) * 3 + (di + 1)], is_hit ? 0x10000u : 1u);
+                                          unsigned *s_near) {
+    const int ni = i - sh.ri + sh.R8 - 1, nj = j - sh.rj + sh.R8 - 1;
+    if ((unsigned)ni < (unsigned)sh.NB && (unsigned)nj < (unsigned)sh.NB) {
+        atomicAdd(&s_near[nj * sh.NB + ni], is_hit ? 0x10000u : 1u);
         return;
     }
-    unsigned inc = is_hit ? 0x100u : 1u;
+    const unsigned inc = is_hit ? 0x10u : 0x01u;
     if (!kPartial) {
-        atomicAdd(&s_win[k >> 1], inc << ((k & 1) << 4));
+        atomicAdd(&s_win[k >> 2], inc << ((k & 3) << 3));
         return;
     }
-    int wi = i - sh.wx0, wj = j - sh.wy0;
+    const int wi = i - sh.wx0, wj = j - sh.wy0;
     if ((unsigned)wi < (unsigned)sh.SW && (unsigned)wj < (unsigned)sh.SH) {
-        int q = wj * sh.SW + wi;
-        atomicAdd(&s_win[q >> 1], inc << ((q & 1) << 4));
+        const int q = wj * sh.SW + wi;
+        atomicAdd(&s_win[q >> 2], inc << ((q & 3) << 3));
         return;
     }
-    unsigned old = atomicAdd(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
-    if (old == 0u) {
-        // each cell is listed once per step, so the list never exceeds W*H
-        int idx = atomicAdd(&p.far_n[sh.e], 1);
-        if (idx < sh.W * sh.H) p.far_list[sh.map_off + idx] = k;
-        else atomicOr(p.err, kErrChecks);
-    }
+    atomicAdd(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
+    atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
 }
 
 // One beam: ground-truth traversal, noise, belief traversal with counting.
 template <bool kPartial>
 __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShared &sh, int b,
                                            const unsigned *s_gt, unsigned *s_win,
-                                           unsigned *s_core, int &rc, int &gc, float &dmin_m,
+                                           unsigned *s_near, int &rc, int &gc, float &dmin_m,
                                            float &dmin_t) {
     const float2 cs = p.beam_cs[sh.ray_off + b];
     const float dx = fsub(fmul(sh.c, cs.x), fmul(sh.s, cs.y));
@@ -185,9 +202,9 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
                                  : (Dx < 0 ? (long long)Px - ((long long)i0 << 16) : 65536);
     const long long ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - Py
                                  : (Dy < 0 ? (long long)Py - ((long long)j0 << 16) : 65536);
-    // Next X crossing is strictly earlier than the next Y crossing iff
-    // nx/adx < ny/ady, i.e. nx*ady < ny*adx (ties step Y).
-    const long long a0 = nx0 * ady, b0 = ny0 * adx;
+    // The next X crossing is strictly earlier than the next Y crossing iff
+    // nx/adx < ny/ady, i.e. e = nx*ady - ny*adx < 0 (ties step Y).
+    const long long e0 = nx0 * ady - ny0 * adx;
     const long long dA = ady << 16, dB = adx << 16;
     const int syW = sy * W;
 
@@ -203,18 +220,18 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
         } else {
             const int Ks = crossings_le(nx0, adx, p.Tmax) + crossings_le(ny0, ady, p.Tmax);
             int i = i0, j = j0;
-            long long a = a0, bb = b0;
+            long long e = e0;
             bool lastx = false;
             for (int s = 0; s < Ks; ++s) {
-                lastx = a < bb;
+                lastx = e < 0;
                 if (lastx) {
                     i += sx;
                     k += sx;
-                    a += dA;
+                    e += dA;
                 } else {
                     j += sy;
                     k += syW;
-                    bb += dB;
+                    e -= dB;
                 }
                 if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
                 ++cells_gt;
@@ -243,20 +260,20 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
     if (in0) {
         const int Ku = crossings_le(nx0, adx, Tz) + crossings_le(ny0, ady, Tz);
         int i = i0, j = j0, k = j0 * W + i0;
-        long long a = a0, bb = b0;
+        long long e = e0;
         for (int s = 0;; ++s) {
             const bool last = s == Ku;
-            add_count<kPartial>(p, sh, i, j, k, last && hit, s_win, s_core);
+            add_count<kPartial>(p, sh, i, j, k, last && hit, s_win, s_near);
             ++cells_upd;
             if (last) break;
-            if (a < bb) {
+            if (e < 0) {
                 i += sx;
                 k += sx;
-                a += dA;
+                e += dA;
             } else {
                 j += sy;
                 k += syW;
-                bb += dB;
+                e -= dB;
             }
             if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
         }
@@ -277,51 +294,66 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
 // Applies (h, m) to one cell's log-odds; returns the entropy change (2^-40 nats).
 __device__ __forceinline__ long long apply_cell(const Step2DParams &p, short &L, unsigned h,
                                                 unsigned m) {
-    int l0 = L;
+    const int l0 = L;
     int l1 = l0 + (int)h * p.hit_q + (int)m * p.miss_q;
     l1 = min(max(l1, -p.clamp_q), p.clamp_q);
     L = (short)l1;
     return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
 }
 
-// Applies the 16-bit counters of 8 consecutive cells held in one uint4.
-__device__ __forceinline__ long long apply8(const Step2DParams &p, uint4 cw, short *Lg,
+// Applies the 8-bit counters of 8 consecutive cells (two words) to their
+// int16 log-odds held in one int4.
+__device__ __forceinline__ long long apply8(const Step2DParams &p, uint2 cw, int4 &lv,
                                             unsigned *dbg) {
-    int4 lv = *reinterpret_cast<int4 *>(Lg);
     short *L = reinterpret_cast<short *>(&lv);
-    unsigned wds[4] = {cw.x, cw.y, cw.z, cw.w};
     long long dh = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        unsigned c16 = (wds[q >> 1] >> ((q & 1) << 4)) & 0xffffu;
-        if (c16) dh += apply_cell(p, L[q], c16 >> 8, c16 & 0xffu);
-        if (dbg) dbg[q] = ((c16 >> 8) << 16) | (c16 & 0xffu);
+        const unsigned c8 = ((q < 4 ? cw.x : cw.y) >> ((q & 3) << 3)) & 0xffu;
+        if (c8) dh += apply_cell(p, L[q], c8 >> 4, c8 & 0xfu);
+        if (dbg) dbg[q] = ((c8 >> 4) << 16) | (c8 & 0xfu);
     }
-    *reinterpret_cast<int4 *>(Lg) = lv;
     return dh;
 }
+
+// Applies 32-bit (hits << 16 | misses) counters of 8 consecutive cells.
+__device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const uint4 &c0,
+                                                 const uint4 &c1, int4 &lv, unsigned *dbg) {
+    short *L = reinterpret_cast<short *>(&lv);
+    const unsigned c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    long long dh = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (c[q]) dh += apply_cell(p, L[q], c[q] >> 16, c[q] & 0xffffu);
+        if (dbg) dbg[q] = c[q];
+    }
+    return dh;
+}
+
+constexpr int kUnroll = 2;
 
 __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     unsigned *s_gt = smem;
     unsigned *s_win = smem + p.gt_words_max;
-    __shared__ unsigned s_core[9];
+    unsigned *s_near = s_win + p.win_words_max;
     __shared__ EnvShared sh;
     __shared__ long long r_dh[32];
     __shared__ int r_rc[32], r_gc[32];
     __shared__ float r_dm[32], r_dt[32];
-    __shared__ int s_item, s_far_n;
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
 
+    if (tid == 0) s_next = grab_item(p);
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(p.queue, 1u);
-        __syncthreads();
-        const int item = s_item;
+        __syncthreads();                 // previous env finished, s_next visible
+        const int item = s_next;
+        __syncthreads();                 // everyone read s_next before it is replaced
         if (item >= p.E) {
-            // Every CTA takes exactly one out-of-range item before leaving;
+            // Every CTA grabs exactly one out-of-range item before leaving;
             // the last CTA to leave re-arms the queue for the next launch.
             if (tid == 0) {
                 __threadfence();
@@ -333,7 +365,10 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             }
             break;
         }
-        if (tid == 0) env_prologue(p, p.order[item], sh);
+        if (tid == 0) {
+            env_prologue(p, p.order[item], sh);
+            s_next = grab_item(p);   // one item ahead: its data streams into L2 meanwhile
+        }
         __syncthreads();
 
         // ---- B: reset, stage ground truth, clear counters --------------------
@@ -351,12 +386,12 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + sh.gtb_off);
             uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
             for (int q = tid; q < (words + 3) >> 2; q += nt) dst[q] = __ldg(&src[q]);
-            const int cw = sh.partial ? (sh.SW * sh.SH + 1) >> 1 : (int)((ncell + 1) >> 1);
+            const int cw = sh.partial ? (sh.SW * sh.SH + 3) >> 2 : (int)((ncell + 3) >> 2);
             uint4 *wz = reinterpret_cast<uint4 *>(s_win);
             for (int q = tid; q < (cw + 3) >> 2; q += nt) wz[q] = make_uint4(0, 0, 0, 0);
-            if (tid < 9) s_core[tid] = 0;
-            if (debug && sh.partial) {
-                for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0;
+            for (int q = tid; q < sh.NB * sh.NB; q += nt) s_near[q] = 0u;
+            if (debug) {
+                for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
             }
         }
         __syncthreads();
@@ -366,10 +401,10 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
         float dmin_m = p.r_max, dmin_t = p.r_max;
         if (sh.partial) {
             for (int b = tid; b < sh.B; b += nt)
-                trace_beam<true>(p, sh, b, s_gt, s_win, s_core, rc, gc, dmin_m, dmin_t);
+                trace_beam<true>(p, sh, b, s_gt, s_win, s_near, rc, gc, dmin_m, dmin_t);
         } else {
             for (int b = tid; b < sh.B; b += nt)
-                trace_beam<false>(p, sh, b, s_gt, s_win, s_core, rc, gc, dmin_m, dmin_t);
+                trace_beam<false>(p, sh, b, s_gt, s_win, s_near, rc, gc, dmin_m, dmin_t);
         }
         __syncthreads();
 
@@ -377,43 +412,75 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
         long long dh = 0;
         short *Lenv = p.belief + sh.map_off;
         unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
-        if (!sh.partial) {
-            const uint4 *cw4 = reinterpret_cast<const uint4 *>(s_win);
-            for (int q = tid; q < nch; q += nt) {
-                uint4 cw = cw4[q];
-                if ((cw.x | cw.y | cw.z | cw.w) == 0u) {
-                    if (dbg) {
-                        for (int r = 0; r < 8 && 8LL * q + r < ncell; ++r) dbg[8 * q + r] = 0u;
+        {
+            // 8-cell chunks of the shared window: the loads of kUnroll chunks
+            // are issued before any of them is used.
+            const int SW = sh.SW, rch = (SW + 7) >> 3;
+            const int nchunk = sh.partial ? sh.SH * rch : nch;
+            const uint2 *cw2 = reinterpret_cast<const uint2 *>(s_win);
+            for (int q0 = tid; q0 < nchunk; q0 += nt * kUnroll) {
+                uint2 cw[kUnroll];
+                int4 lv[kUnroll];
+                long long gk[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int q = q0 + u * nt;
+                    cw[u] = make_uint2(0u, 0u);
+                    gk[u] = -1;
+                    if (q < nchunk) {
+                        long long k;
+                        int sidx;
+                        if (sh.partial) {
+                            const int jj = q / rch, cc = q - jj * rch;
+                            k = (long long)(sh.wy0 + jj) * W + sh.wx0 + 8 * cc;
+                            sidx = (jj * SW >> 3) + cc;
+                        } else {
+                            k = 8LL * q;
+                            sidx = q;
+                        }
+                        cw[u] = cw2[sidx];
+                        if (cw[u].x | cw[u].y) {
+                            gk[u] = k;
+                            lv[u] = *reinterpret_cast<const int4 *>(Lenv + k);
+                        }
                     }
-                    continue;
                 }
-                dh += apply8(p, cw, Lenv + 8LL * q, dbg ? dbg + 8LL * q : nullptr);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (gk[u] >= 0) {
+                        dh += apply8(p, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr);
+                        *reinterpret_cast<int4 *>(Lenv + gk[u]) = lv[u];
+                    }
+                }
             }
-        } else {
-            const int SW = sh.SW, SH = sh.SH, rch = SW >> 3;
-            const uint4 *cw4 = reinterpret_cast<const uint4 *>(s_win);
-            for (int q = tid; q < SH * rch; q += nt) {
-                const int jj = q / rch, cc = q - jj * rch;
-                uint4 cw = cw4[(jj * SW >> 3) + cc];
-                if ((cw.x | cw.y | cw.z | cw.w) == 0u) continue;
-                const long long k = (long long)(sh.wy0 + jj) * W + sh.wx0 + 8 * cc;
-                dh += apply8(p, cw, Lenv + k, dbg ? dbg + k : nullptr);
-            }
-            if (tid == 0) s_far_n = atomicAdd(&p.far_n[e], 0);
-            __syncthreads();
-            const int nf = s_far_n;
-            for (int q = tid; q < nf; q += nt) {
-                const int k = __ldcg(&p.far_list[sh.map_off + q]);
-                const unsigned c = atomicExch(&p.far_cnt[sh.map_off + k], 0u);
-                if (c) dh += apply_cell(p, Lenv[k], c >> 16, c & 0xffffu);
-                if (dbg) dbg[k] = c;
+        }
+        if (sh.partial) {
+            // chunks outside the window, found through the touched-chunk bitmap
+            const long long nbw = (ncell + 255) >> 8;
+            unsigned *bits = p.far_bits + (sh.map_off >> 8);
+            for (long long w = tid; w < nbw; w += nt) {
+                unsigned m = __ldcg(&bits[w]);
+                if (!m) continue;
+                bits[w] = 0u;
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    const long long k = w * 256 + bit * 8;
+                    uint4 *cp = reinterpret_cast<uint4 *>(p.far_cnt + sh.map_off + k);
+                    const uint4 c0 = __ldcg(cp), c1 = __ldcg(cp + 1);
+                    cp[0] = make_uint4(0u, 0u, 0u, 0u);
+                    cp[1] = make_uint4(0u, 0u, 0u, 0u);
+                    int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
+                    dh += apply8_wide(p, c0, c1, lv, dbg ? dbg + k : nullptr);
+                    *reinterpret_cast<int4 *>(Lenv + k) = lv;
+                }
             }
         }
         __syncthreads();
-        if (tid < 9) {
-            const int i = sh.ri + tid % 3 - 1, j = sh.rj + tid / 3 - 1;
+        for (int q = tid; q < sh.NB * sh.NB; q += nt) {
+            const int i = sh.ri + q % sh.NB - (sh.R8 - 1), j = sh.rj + q / sh.NB - (sh.R8 - 1);
             if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
-                const unsigned c = s_core[tid];
+                const unsigned c = s_near[q];
                 const long long k = (long long)j * W + i;
                 if (c) dh += apply_cell(p, Lenv[k], c >> 16, c & 0xffffu);
                 if (dbg) dbg[k] = c;
@@ -448,7 +515,6 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
                 dm = fminf(dm, r_dm[w]);
                 dtr = fminf(dtr, r_dt[w]);
             }
-            if (sh.partial) p.far_n[e] = 0;
             const long long Hq = sh.Hq + dHq;
             p.Hq[e] = Hq;
             const double dH = -(double)dHq / kLutScale;    // H_{t-1} - H_t (nats)
@@ -513,7 +579,6 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             float *o = p.out_obs + (long long)e * (p.b_max + 2);
             for (int b = sh.B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
         }
-        __syncthreads();
     }
 }
 
@@ -547,7 +612,6 @@ __global__ void init_state_kernel(const Step2DParams p) {
         p.ep[e] = 0;
         p.done[e] = 0;
         p.Hq[e] = (long long)p.W[e] * p.H[e] * p.lut[p.clamp_q];
-        p.far_n[e] = 0;
         p.reward[e] = 0.0f;
     }
 }
