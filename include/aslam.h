@@ -228,6 +228,36 @@ aslam_status aslam_debug_detmath(const float *d_x, const float *d_u, int32_t n,
                                  float *d_sin, float *d_cos, float *d_log, float *d_cos2pi,
                                  uint64_t seed, float *d_gauss, void *stream);
 
+/*
+ * Allocation-free single-scan update.  The paper has no counterpart: this
+ * is an integration aid for callers that may not allocate device memory
+ * (code running inside a host framework that owns the allocator, or with a
+ * memory budget frozen after start-up).  It integrates one scan per
+ * environment -- raycast from the given pose, range noise, miss/hit counts,
+ * one clamp per scan -- exactly as aslam_step does for a robot that did not
+ * move, but keeps its per-cell counters in a fixed array inside the library
+ * (16 MiB, held by every GPU that loads the library until the process
+ * exits) instead of a workspace.  It calls no cudaMalloc/cudaFree.
+ *   cfg        constants (res_m, r_max_m, fov_rad, noise_sigma_m, l_*_q, seed)
+ *              and HOST h_map_w/h_map_h/h_n_beams [n_envs]; every env must
+ *              have the same beam count B.
+ *   d_gt       device uint8 ground-truth grids, packed: env e at h_gt_off[e].
+ *   h_gt_off   HOST int64 [n_envs+1] prefix sums of W*H (h_gt_off[0] = 0).
+ *   d_pose     device float [n_envs, 3] scan pose (x, y, th).
+ *   d_step     device int32 [n_envs] noise counter (aslam_step's global step).
+ *   d_belief   device int16 log-odds, same layout as d_gt, updated in place.
+ *   d_ranges   device float [n_envs, B] measured ranges (output).
+ * Limits: n_envs <= 2048, total cells <= 4194304, B <= 1024; larger requests
+ * return ASLAM_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address with that device current: make it before any
+ * stream capture.  All calls share the array (each clears what it uses
+ * first), so calls that overlap on the GPU race: serialise them.
+ */
+aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const uint8_t *d_gt,
+                                       const int64_t *h_gt_off, const float *d_pose,
+                                       const int32_t *d_step, int16_t *d_belief,
+                                       float *d_ranges, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ EXPORTS = {
     "aslam_status_string": ([C.c_int], C.c_char_p),
     "aslam_last_error": ([P], C.c_char_p),
     "aslam_debug_detmath": ([P, P, C.c_int32, P, P, P, P, C.c_uint64, P, P], C.c_int),
+    "aslam_scan_update_noalloc": ([C.POINTER(AslamConfig), P, P, P, P, P, P, P], C.c_int),
 }
 
 
@@ -309,3 +310,31 @@ def debug_detmath(x, u, seed):
     _check(lib.aslam_debug_detmath(_dptr(x), _dptr(u), n, *[_dptr(o) for o in outs[:4]],
                                    C.c_uint64(seed), _dptr(outs[4]), _stream()))
     return outs
+
+
+def scan_update_noalloc(inputs, gt, pose, step, belief, ranges, stream=None, **cfg):
+    """One scan per env into caller-owned grids, with no device allocation.
+
+    For callers that may not allocate device memory: `gt` (uint8, packed like
+    inputs.gt), `pose` [E, 3] float, `step` [E] int32 (noise counter),
+    `belief` (int16, packed like inputs.gt, updated in place) and `ranges`
+    [E, B] float are the caller's CUDA tensors; the library's scratch is a
+    fixed array of its own.  Calls that overlap on the GPU share that array
+    and must be serialised.
+    """
+    lib = load()
+    c = config_defaults()
+    E = inputs.n_envs
+    w = np.ascontiguousarray(inputs.map_w, dtype=np.int32)
+    h = np.ascontiguousarray(inputs.map_h, dtype=np.int32)
+    b = np.ascontiguousarray(inputs.n_beams, dtype=np.int32)
+    off = np.ascontiguousarray(inputs.map_off, dtype=np.int64)
+    c.n_envs = E
+    c.res_m = float(inputs.res)
+    c.h_map_w = w.ctypes.data_as(P)
+    c.h_map_h = h.ctypes.data_as(P)
+    c.h_n_beams = b.ctypes.data_as(P)
+    for k, v in cfg.items():
+        setattr(c, k, float(v) if k in _FLOAT_KEYS else int(v))
+    _check(lib.aslam_scan_update_noalloc(C.byref(c), _dptr(gt), off.ctypes.data_as(P), _dptr(pose),
+                                         _dptr(step), _dptr(belief), _dptr(ranges), _stream(stream)))

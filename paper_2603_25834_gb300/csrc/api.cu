@@ -197,6 +197,8 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
 
 }  // namespace
 
+void aslam::set_thread_error(const char *msg) { g_thread_error = msg ? msg : ""; }
+
 struct aslam_batch {
     aslam_config cfg;
     HostInfo hi;

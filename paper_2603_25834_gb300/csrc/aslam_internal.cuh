@@ -180,6 +180,9 @@ constexpr double kLutScale = 1099511627776.0;   // 2^40
 constexpr unsigned kErrChecks = 1u;
 constexpr unsigned kErrTimeout = 2u;
 
+// Records the calling thread's last error message (aslam_last_error(NULL)).
+void set_thread_error(const char *msg);
+
 // Launchers (defined next to their kernels).
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
