@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default/tuned)")
+    ap.add_argument("--window", type=int, default=0, help="shared window side (0: default/tuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -205,9 +207,10 @@ def main():
     E = args.envs
     inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
     batch = aslam.Batch2D(inp, device=dev, r_max_m=12.0, noise_sigma_m=0.01,
-                          reward_mode=aslam.REWARD_COMPOSITE)
+                          reward_mode=aslam.REWARD_COMPOSITE, threads_per_cta=args.threads,
+                          window_cells=args.window)
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not args.threads and not args.window:
         tuned = batch.autotune()
     K, W = args.steps, args.warmup
     acts = torch.from_numpy(synth.random_actions(K + W, E, 7 + rank)).to(dev)

@@ -203,3 +203,13 @@ def test_reset_mask_and_observe(aslam_gpu, orc):
         np.testing.assert_array_equal(obs[e, :45], zz[g.ray_off[e]:g.ray_off[e] + 45])
         assert obs[e, 45] == st["th"].cpu().numpy()[e]
     g.sync_status()
+
+
+@pytest.mark.parametrize("sigma,window", [(0.3, 0), (0.3, 64), (0.08, 0)])
+def test_large_noise_moves_endpoint_far_from_hit(aslam_gpu, orc, sigma, window):
+    """Noise of several cells: endpoints both far before the hit cell (the
+    committed misses past it must be removed) and far beyond it."""
+    inp = synth.paper_scale(E=4, seed=606)
+    acts = synth.random_actions(4, 4, 60)
+    run_parity(aslam_gpu, orc, inp, acts, tag="noise-%g-%d" % (sigma, window), r_max_m=12.0,
+               noise_sigma_m=sigma, gpu_kw=dict(window_cells=window))
