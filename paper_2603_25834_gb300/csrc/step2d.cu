@@ -8,10 +8,10 @@
 //      shared memory and clear the shared hit/miss counters;
 //   C. one thread per beam: exact fixed-point grid traversal (Amanatides-Woo
 //      order with exact 64-bit comparisons) of the ground truth until the
-//      first occupied cell (Sec. IV-A LiDAR) and Gaussian range noise; the
-//      same traversal counts one miss for every cell the beam crosses before
-//      its measured endpoint and a hit at the endpoint of a returned beam
-//      (Sec. III-D log-odds grid);
+//      first occupied cell (Sec. IV-A LiDAR), Gaussian range noise, then a
+//      second traversal of the belief grid to the measured endpoint that
+//      adds one miss to every crossed cell and a hit to the endpoint of a
+//      returned beam (Sec. III-D log-odds grid);
 //   D. all threads: per cell, L' = clamp(L + h*HIT + m*MISS) (one clamp per
 //      scan, so the result does not depend on beam order) and the change of
 //      the cell's entropy from a fixed-point table;
@@ -154,43 +154,32 @@ __device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvSh
     }
 }
 
-// Adds one hit or miss of cell (i, j) (flat k) to its counter, or removes
-// it again when `undo` is set (the field is >= 1 then, so nothing borrows).
+// Adds (or, with sign < 0, removes) one hit or miss of cell (i, j) (flat k).
 template <bool kPartial>
 __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared &sh, int i,
                                           int j, int k, bool is_hit, unsigned *s_win,
-                                          unsigned *s_near, bool undo = false) {
+                                          unsigned *s_near) {
     const int ni = i - sh.ri + sh.R8 - 1, nj = j - sh.rj + sh.R8 - 1;
     if ((unsigned)ni < (unsigned)sh.NB && (unsigned)nj < (unsigned)sh.NB) {
-        const unsigned v = is_hit ? 0x10000u : 1u;
-        atomicAdd(&s_near[nj * sh.NB + ni], undo ? 0u - v : v);
+        atomicAdd(&s_near[nj * sh.NB + ni], is_hit ? 0x10000u : 1u);
         return;
     }
     const unsigned inc = is_hit ? 0x10u : 0x01u;
     if (!kPartial) {
-        const unsigned v = inc << ((k & 3) << 3);
-        atomicAdd(&s_win[k >> 2], undo ? 0u - v : v);
+        atomicAdd(&s_win[k >> 2], inc << ((k & 3) << 3));
         return;
     }
     const int wi = i - sh.wx0, wj = j - sh.wy0;
     if ((unsigned)wi < (unsigned)sh.SW && (unsigned)wj < (unsigned)sh.SH) {
         const int q = wj * sh.SW + wi;
-        const unsigned v = inc << ((q & 3) << 3);
-        atomicAdd(&s_win[q >> 2], undo ? 0u - v : v);
+        atomicAdd(&s_win[q >> 2], inc << ((q & 3) << 3));
         return;
     }
-    const unsigned v = is_hit ? 0x10000u : 1u;
-    atomicAdd(&p.far_cnt[sh.map_off + k], undo ? 0u - v : v);
+    atomicAdd(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
     atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
 }
 
-// One beam, in a single traversal.  The walk follows the ground truth to the
-// first occupied cell (or the range limit / map border).  Every cell is also
-// a belief cell of the update walk up to the noisy endpoint; misses are
-// committed two cells behind the walk, so that once the endpoint is known the
-// two pending cells and the current one can still become the endpoint or be
-// left out.  If the noise pulls the endpoint back further, the misses already
-// committed past it are removed again by a second walk (exact, rare).
+// One beam: ground-truth traversal, noise, belief traversal with counting.
 template <bool kPartial>
 __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShared &sh, int b,
                                            const unsigned *s_gt, unsigned *s_win,
@@ -220,107 +209,73 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
     const int syW = sy * W;
 
     bool hit = false;
-    float z_true = p.r_max, z = p.r_max;
-    int cells_gt = 0, cells_upd = 0;
+    float z_true = p.r_max;
+    int cells_gt = 0;
     if (in0) {
-        int i = i0, j = j0;
-        long long e = e0;
-        int s = 0;                                   // index of the current cell
-        // pending cells s-1 and s-2, packed as (j << 16) | i (sides <= 8192)
-        int pb1 = (j0 << 16) | i0, pb2 = pb1;
-        hit = gt_bit(s_gt, j0 * W + i0) != 0u;
-        if (!hit) {
+        int k = j0 * W + i0;
+        cells_gt = 1;
+        if (gt_bit(s_gt, k)) {
+            hit = true;
+            z_true = 0.0f;
+        } else {
             const int Ks = crossings_le(nx0, adx, p.Tmax) + crossings_le(ny0, ady, p.Tmax);
-            while (s < Ks) {
-                const bool stepx = e < 0;
-                const int ni = stepx ? i + sx : i, nj = stepx ? j : j + sy;
-                if ((unsigned)ni >= (unsigned)W || (unsigned)nj >= (unsigned)H) break;
-                if (s >= 2) {
-                    const int ci = pb2 & 0xffff, cj = pb2 >> 16;
-                    add_count<kPartial>(p, sh, ci, cj, cj * W + ci, false, s_win, s_near);
+            int i = i0, j = j0;
+            long long e = e0;
+            bool lastx = false;
+            for (int s = 0; s < Ks; ++s) {
+                lastx = e < 0;
+                if (lastx) {
+                    i += sx;
+                    k += sx;
+                    e += dA;
+                } else {
+                    j += sy;
+                    k += syW;
+                    e -= dB;
                 }
-                pb2 = pb1;
-                pb1 = (j << 16) | i;
-                i = ni;
-                j = nj;
-                e += stepx ? dA : -dB;
-                ++s;
-                if (gt_bit(s_gt, j * W + i)) {
+                if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
+                ++cells_gt;
+                if (gt_bit(s_gt, k)) {
                     hit = true;
                     break;
                 }
             }
-        }
-        cells_gt = s + 1;
-        const int b1i = pb1 & 0xffff, b1j = pb1 >> 16, b2i = pb2 & 0xffff, b2j = pb2 >> 16;
-        int k = j * W + i;
-        if (!hit) {
-            // no return: every traversed cell gets a miss
-            if (s >= 2) add_count<kPartial>(p, sh, b2i, b2j, b2j * W + b2i, false, s_win, s_near);
-            if (s >= 1) add_count<kPartial>(p, sh, b1i, b1j, b1j * W + b1i, false, s_win, s_near);
-            add_count<kPartial>(p, sh, i, j, k, false, s_win, s_near);
-            cells_upd = s + 1;
-        } else {
-            if (s > 0) {
+            if (hit) {
                 // entry parameter of the hit cell: the crossing that entered it
-                const bool lastx = i != b1i;
                 const long long n = lastx ? nx0 + ((long long)(abs(i - i0) - 1) << 16)
                                           : ny0 + ((long long)(abs(j - j0) - 1) << 16);
                 const long long ad = lastx ? adx : ady;
                 z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
-            } else {
-                z_true = 0.0f;
             }
-            const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.gstep, (unsigned)b);
-            z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, gz)), 0.0f), p.r_max);
-            const int Tz = q16_of(z, p.res);
-            const int Kz = crossings_le(nx0, adx, Tz) + crossings_le(ny0, ady, Tz);
-            const int Hs = s;
-            if (Kz >= Hs - 2) {
-                if (Hs >= 2 && Hs - 2 <= Kz)
-                    add_count<kPartial>(p, sh, b2i, b2j, b2j * W + b2i, Hs - 2 == Kz, s_win, s_near);
-                if (Hs >= 1 && Hs - 1 <= Kz)
-                    add_count<kPartial>(p, sh, b1i, b1j, b1j * W + b1i, Hs - 1 == Kz, s_win, s_near);
-                if (Hs <= Kz) add_count<kPartial>(p, sh, i, j, k, Hs == Kz, s_win, s_near);
-                int last_idx = min(Kz, Hs);
-                // the noisy endpoint lies beyond the hit cell: keep walking
-                for (int q = Hs + 1; q <= Kz; ++q) {
-                    if (e < 0) {
-                        i += sx;
-                        k += sx;
-                        e += dA;
-                    } else {
-                        j += sy;
-                        k += syW;
-                        e -= dB;
-                    }
-                    if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
-                    add_count<kPartial>(p, sh, i, j, k, q == Kz, s_win, s_near);
-                    last_idx = q;
-                }
-                cells_upd = last_idx + 1;
+        }
+    }
+    float z = z_true;
+    if (hit) {
+        const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.gstep, (unsigned)b);
+        z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, gz)), 0.0f), p.r_max);
+    }
+    const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
+
+    int cells_upd = 0;
+    if (in0) {
+        const int Ku = crossings_le(nx0, adx, Tz) + crossings_le(ny0, ady, Tz);
+        int i = i0, j = j0, k = j0 * W + i0;
+        long long e = e0;
+        for (int s = 0;; ++s) {
+            const bool last = s == Ku;
+            add_count<kPartial>(p, sh, i, j, k, last && hit, s_win, s_near);
+            ++cells_upd;
+            if (last) break;
+            if (e < 0) {
+                i += sx;
+                k += sx;
+                e += dA;
             } else {
-                // the endpoint is more than two cells before the hit cell:
-                // remove the misses committed at cells Kz .. Hs-3, hit at Kz
-                int ii = i0, jj = j0, kk = j0 * W + i0;
-                long long ee = e0;
-                for (int q = 0; q <= Hs - 3; ++q) {
-                    if (q >= Kz) {
-                        add_count<kPartial>(p, sh, ii, jj, kk, false, s_win, s_near, true);
-                        if (q == Kz) add_count<kPartial>(p, sh, ii, jj, kk, true, s_win, s_near);
-                    }
-                    if (ee < 0) {
-                        ii += sx;
-                        kk += sx;
-                        ee += dA;
-                    } else {
-                        jj += sy;
-                        kk += syW;
-                        ee -= dB;
-                    }
-                }
-                cells_upd = Kz + 1;
+                j += sy;
+                k += syW;
+                e -= dB;
             }
+            if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
         }
     }
     const long long ro = sh.ray_off + b;
