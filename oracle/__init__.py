@@ -21,7 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["aslam_oracle.c"]
+_SOURCES = ["aslam_oracle.c", "soft_range_oracle.c"]
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -87,6 +87,11 @@ class OrcOut(C.Structure):
                 ("ray_cells", P), ("gt_cells", P)]
 
 
+class OrcSoftCfg(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("B", C.c_int32), ("K", C.c_int32),
+                ("res", C.c_double), ("ds", C.c_double), ("fov", C.c_double)]
+
+
 N_TERMS = 12
 TERM_NAMES = ["dH", "dcells", "I", "alpha_hug", "r_explore", "r_abs", "r_delta", "R",
               "collision", "dmin_meas", "dmin_true", "H"]
@@ -114,6 +119,8 @@ def _declare(L):
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.orc_step2d.argtypes = [C.POINTER(OrcCfg), C.POINTER(OrcState), P, P, C.POINTER(OrcOut)]
     L.orc_step2d.restype = C.c_int
+    L.orc_soft_ranges.argtypes = [C.POINTER(OrcSoftCfg), P, P, C.c_int, P, P, P, P]
+    L.orc_gn_batch.argtypes = [C.POINTER(OrcSoftCfg), P, P, P, C.c_int, C.c_int, C.c_double, P, P]
 
 
 # ---------------------------------------------------------------- scalar helpers
@@ -272,3 +279,35 @@ class OracleBatch2D:
     def env_belief(self, e):
         a, b = int(self.map_off[e]), int(self.map_off[e + 1])
         return self.belief[a:b].reshape(int(self.map_h[e]), int(self.map_w[e]))
+
+
+# ---------------------------------------------------------------- soft range / GN
+def soft_cfg(W, H, B, K=64, res=0.05, ds=0.05, fov=0.0):
+    return OrcSoftCfg(W=W, H=H, B=B, K=K, res=res, ds=ds, fov=fov)
+
+
+def soft_ranges(cfg, L, pose, gr=None, grad_pose=False, grad_map=False):
+    """Soft ranges [E, B] (fp64) of fp32 log-odds L [E, H, W] at poses [E, 3];
+    optionally the adjoints of sum(gr * r) w.r.t. pose and L."""
+    L = np.ascontiguousarray(L, dtype=np.float32)
+    E = L.shape[0]
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(E, 3)
+    r = np.zeros((E, cfg.B), np.float64)
+    gp = np.zeros((E, 3), np.float64) if grad_pose else None
+    gm = np.zeros(L.shape, np.float64) if grad_map else None
+    g = None if gr is None else np.ascontiguousarray(gr, dtype=np.float64).reshape(E, cfg.B)
+    lib().orc_soft_ranges(C.byref(cfg), _ptr(L), _ptr(pose), E, _ptr(g), _ptr(r), _ptr(gp), _ptr(gm))
+    return r, gp, gm
+
+
+def gn(cfg, L, pose_in, z, iters=5, mu=1e-6):
+    """Gauss-Newton pose correction: final poses [E, 3] and damped normal matrices [E, 3, 3]."""
+    L = np.ascontiguousarray(L, dtype=np.float32)
+    E = L.shape[0]
+    pin = np.ascontiguousarray(pose_in, dtype=np.float64).reshape(E, 3)
+    zz = np.ascontiguousarray(z, dtype=np.float32).reshape(E, cfg.B)
+    pout = np.zeros((E, 3), np.float64)
+    A = np.zeros((E, 9), np.float64)
+    lib().orc_gn_batch(C.byref(cfg), _ptr(L), _ptr(pin), _ptr(zz), E, iters, C.c_double(mu),
+                       _ptr(pout), _ptr(A))
+    return pout, A.reshape(E, 3, 3)

@@ -204,3 +204,21 @@ def random_uncertainty(steps, E, seed, lo=0.0, hi=1.5):
         cur = np.clip(cur + rng.normal(0.0, 0.08, size=E), lo, hi)
         u[s] = cur
     return u
+
+
+def logodds_maps(inputs, occupied=3.0, free=-3.0):
+    """fp32 natural log-odds grids [E, H, W] of a belief that has seen the whole
+    ground truth (uniform W, H): `occupied` where the world is occupied,
+    `free` elsewhere.  Input for the differentiable soft raycaster."""
+    E = inputs.n_envs
+    W, H = int(inputs.map_w[0]), int(inputs.map_h[0])
+    assert np.all(inputs.map_w == W) and np.all(inputs.map_h == H)
+    occ = inputs.gt.reshape(E, H, W)
+    return np.where(occ > 0, np.float32(occupied), np.float32(free)).astype(np.float32)
+
+
+def perturb_poses(poses, seed, sigma=(0.05, 0.05, 0.02)):
+    """poses [E, 3] plus Gaussian noise (x, y, th), float32."""
+    rng = np.random.default_rng(seed)
+    p = np.asarray(poses, dtype=np.float64)
+    return (p + rng.normal(0.0, 1.0, p.shape) * np.asarray(sigma)).astype(np.float32)
