@@ -228,6 +228,64 @@ aslam_status aslam_debug_detmath(const float *d_x, const float *d_u, int32_t n,
                                  float *d_sin, float *d_cos, float *d_log, float *d_cos2pi,
                                  uint64_t seed, float *d_gauss, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Differentiable soft expected-range raycaster and scan-to-map Gauss-Newton
+ * (Sec. III-D: pose estimate by Gauss-Newton on the scan residuals, Eq. 5,
+ * and the pose covariance block from the inverse Gauss-Newton Hessian,
+ * Eq. 6).  Grids are identical in size for all envs: fp32 natural log-odds
+ * d_logodds[E, H, W] (row-major, cell (i, j) centred at ((i+.5)res, (j+.5)res),
+ * bilinear between centres, clamped to the edge outside the map).  Beam b
+ * casts K samples s_k = (k+1)*ds; p_k = sigmoid(bilinear log-odds);
+ * T_0 = 1, T_{k+1} = T_k (1 - p_k); r = sum_k T_k p_k s_k + T_K * K*ds.
+ * ------------------------------------------------------------------------ */
+#define ASLAM_SOFT_MAX_SAMPLES 256
+
+typedef struct {
+    uint32_t struct_size;          /* sizeof(aslam_soft_config) */
+    int32_t n_envs;                /* E >= 1 */
+    int32_t map_w, map_h;          /* grid W, H (cells) for every env */
+    int32_t n_beams;               /* B in [1, ASLAM_MAX_BEAMS] */
+    int32_t n_samples;             /* K in [1, ASLAM_SOFT_MAX_SAMPLES] */
+    float res_m;                   /* cell size (m) */
+    float sample_step_m;           /* ds (m); the no-return range is K*ds */
+    float fov_rad;                 /* 0 or >= 2*pi: full turn; else front arc */
+    float gn_damping;              /* mu added to the diagonal of J^T J */
+    float range_sigma_m;           /* range noise std: Sigma = sigma^2 (J^T J + mu I)^-1 */
+} aslam_soft_config;
+
+/* Defaults: 1 env, 256 x 256 @ 0.05 m, 360 beams, 64 samples of 0.05 m,
+ * mu = 1e-6, sigma = 0.01 m. */
+aslam_status aslam_soft_config_init(aslam_soft_config *cfg);
+
+/* Soft ranges: d_pose [E, 3] (x, y, th) -> d_ranges [E, B]. */
+aslam_status aslam_soft_range_fwd(const aslam_soft_config *cfg, const float *d_logodds,
+                                  const float *d_pose, float *d_ranges, void *stream);
+
+/* Ranges (optional, may be NULL) and their Jacobian d_jac [E, B, 3] w.r.t.
+ * (x, y, th), by forward-mode differentiation. */
+aslam_status aslam_soft_range_jac(const aslam_soft_config *cfg, const float *d_logodds,
+                                  const float *d_pose, float *d_ranges, float *d_jac,
+                                  void *stream);
+
+/* Adjoint of sum(d_grad_ranges * r): d_grad_pose [E, 3] is overwritten;
+ * d_grad_logodds [E, H, W] (optional) is ACCUMULATED into (+=, atomic fp32
+ * adds, so the summation order varies from run to run).  The transmittance
+ * of every beam is recomputed inside this call (nothing is kept from
+ * aslam_soft_range_fwd). */
+aslam_status aslam_soft_range_bwd(const aslam_soft_config *cfg, const float *d_logodds,
+                                  const float *d_pose, const float *d_grad_ranges,
+                                  float *d_grad_pose, float *d_grad_logodds, void *stream);
+
+/* Gauss-Newton scan-to-map correction (Eq. 5): from d_pose_in [E, 3], `iters`
+ * (0..100) damped steps xi <- xi - (J^T J + mu I)^{-1} J^T (r(xi) - z) on the
+ * measured ranges d_z [E, B]; writes d_pose_out [E, 3] and, evaluated at
+ * the final pose, the covariance block d_cov [E, 3, 3] = sigma^2 (J^T J +
+ * mu I)^{-1} (Eq. 6, optional) and the scalar uncertainty
+ * d_u [E] = det(Sigma)^(1/3) (D-optimality, optional). */
+aslam_status aslam_gn_correct(const aslam_soft_config *cfg, const float *d_logodds,
+                              const float *d_pose_in, const float *d_z, int32_t iters,
+                              float *d_pose_out, float *d_cov, float *d_u, void *stream);
+
 /*
  * Allocation-free single-scan update.  The paper has no counterpart: this
  * is an integration aid for callers that may not allocate device memory

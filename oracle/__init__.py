@@ -120,6 +120,7 @@ def _declare(L):
     L.orc_step2d.argtypes = [C.POINTER(OrcCfg), C.POINTER(OrcState), P, P, C.POINTER(OrcOut)]
     L.orc_step2d.restype = C.c_int
     L.orc_soft_ranges.argtypes = [C.POINTER(OrcSoftCfg), P, P, C.c_int, P, P, P, P]
+    L.orc_soft_jacobian.argtypes = [C.POINTER(OrcSoftCfg), P, P, C.c_int, P, P]
     L.orc_gn_batch.argtypes = [C.POINTER(OrcSoftCfg), P, P, P, C.c_int, C.c_int, C.c_double, P, P]
 
 
@@ -311,3 +312,14 @@ def gn(cfg, L, pose_in, z, iters=5, mu=1e-6):
     lib().orc_gn_batch(C.byref(cfg), _ptr(L), _ptr(pin), _ptr(zz), E, iters, C.c_double(mu),
                        _ptr(pout), _ptr(A))
     return pout, A.reshape(E, 3, 3)
+
+
+def soft_jacobian(cfg, L, pose):
+    """Ranges [E, B] and per-beam Jacobians [E, B, 3] (fp64)."""
+    L = np.ascontiguousarray(L, dtype=np.float32)
+    E = L.shape[0]
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(E, 3)
+    r = np.zeros((E, cfg.B), np.float64)
+    J = np.zeros((E, cfg.B, 3), np.float64)
+    lib().orc_soft_jacobian(C.byref(cfg), _ptr(L), _ptr(pose), E, _ptr(r), _ptr(J))
+    return r, J

@@ -174,3 +174,17 @@ void orc_gn_batch(const orc_soft_cfg *c, const float *L, const double *pose_in, 
         orc_gn(c, L + e * n, pose_in + 3 * e, z + (int64_t)e * c->B, iters, mu,
                pose_out + 3 * e, A_out + 9 * e);
 }
+
+/* Per-beam Jacobian dr_b/d(x, y, th) [E, B, 3] by the adjoint, one beam at a time. */
+void orc_soft_jacobian(const orc_soft_cfg *c, const float *L, const double *pose, int E,
+                       double *ranges, double *jac)
+{
+    const int64_t n = (int64_t)c->W * c->H;
+    for (int e = 0; e < E; ++e)
+        for (int b = 0; b < c->B; ++b) {
+            double *J = jac + 3 * ((int64_t)e * c->B + b);
+            J[0] = J[1] = J[2] = 0.0;
+            ranges[(int64_t)e * c->B + b] = orc_soft_range(
+                c, L + e * n, pose[3 * e], pose[3 * e + 1], pose[3 * e + 2], b, 1.0, J, NULL);
+        }
+}

@@ -64,6 +64,13 @@ class AslamStatePtrs(C.Structure):
                 ("h_ray_off", P), ("b_max", C.c_int32)]
 
 
+class AslamSoftConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("n_envs", C.c_int32), ("map_w", C.c_int32),
+                ("map_h", C.c_int32), ("n_beams", C.c_int32), ("n_samples", C.c_int32),
+                ("res_m", C.c_float), ("sample_step_m", C.c_float), ("fov_rad", C.c_float),
+                ("gn_damping", C.c_float), ("range_sigma_m", C.c_float)]
+
+
 EXPORTS = {
     "aslam_config_init": ([C.POINTER(AslamConfig)], C.c_int),
     "aslam_workspace_bytes": ([C.POINTER(AslamConfig), C.POINTER(C.c_size_t)], C.c_int),
@@ -88,6 +95,11 @@ EXPORTS = {
     "aslam_last_error": ([P], C.c_char_p),
     "aslam_debug_detmath": ([P, P, C.c_int32, P, P, P, P, C.c_uint64, P, P], C.c_int),
     "aslam_scan_update_noalloc": ([C.POINTER(AslamConfig), P, P, P, P, P, P, P], C.c_int),
+    "aslam_soft_config_init": ([C.POINTER(AslamSoftConfig)], C.c_int),
+    "aslam_soft_range_fwd": ([C.POINTER(AslamSoftConfig), P, P, P, P], C.c_int),
+    "aslam_soft_range_jac": ([C.POINTER(AslamSoftConfig), P, P, P, P, P], C.c_int),
+    "aslam_soft_range_bwd": ([C.POINTER(AslamSoftConfig), P, P, P, P, P, P], C.c_int),
+    "aslam_gn_correct": ([C.POINTER(AslamSoftConfig), P, P, P, C.c_int32, P, P, P, P], C.c_int),
 }
 
 

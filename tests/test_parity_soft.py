@@ -1,0 +1,154 @@
+"""GPU parity of the differentiable soft raycaster, its adjoint, the
+forward-mode Jacobian and Gauss-Newton (through the C ABI) against the
+fp64 oracle.
+
+Tolerances, from the fp32 arithmetic of the kernels: a sample position
+x + s*cos(phi) carries an absolute error of about one fp32 ulp of the map
+extent (<= 1e-6 m at 12.8 m, i.e. 2e-5 cells at 0.05 m); with log-odds
+jumping by up to 6 per cell this moves l by <= 1.2e-4 and p by <= 3e-5,
+and a range sums such changes over the few samples where p changes,
+weighted by s <= 3.2 m: |dr| <= 5e-4 m.  Gradients scale the same relative
+error by the gradient's own magnitude: |dg| <= 2e-3 * max|g| + 1e-3 |g|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_25834_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+R_TOL = 5e-4
+
+
+@pytest.fixture(scope="module")
+def soft():
+    from paper_2603_25834_gb300 import soft as S
+    return S
+
+
+def maps_and_poses(E, W, seed, textured):
+    inp = synth.paper_scale(E=E, W=W, B=8, seed=seed)
+    L = synth.logodds_maps(inp)
+    if textured:
+        rng = np.random.default_rng(seed)
+        L = (L + rng.normal(0, 0.8, L.shape)).astype(np.float32)
+    pose = np.ascontiguousarray(inp.spawn[:, 0, :])
+    return L, pose
+
+
+@pytest.mark.parametrize("textured", [False, True])
+def test_forward_and_jacobian(aslam_gpu, orc, soft, textured):
+    E, W, B = 4, 256, 360
+    L, pose = maps_and_poses(E, W, 31 + textured, textured)
+    cfg = soft.soft_config(E, W, W, B)
+    Lt, pt = torch.from_numpy(L).cuda(), torch.from_numpy(pose).cuda()
+    r = soft.soft_range_fwd(cfg, Lt, pt).cpu().numpy()
+    rj, J = soft.soft_range_jac(cfg, Lt, pt)
+    ocfg = orc.soft_cfg(W, W, B)
+    ro, Jo = orc.soft_jacobian(ocfg, L, pose)
+    assert np.abs(r - ro).max() <= R_TOL
+    assert np.abs(rj.cpu().numpy() - ro).max() <= R_TOL
+    J = J.cpu().numpy()
+    scale = np.abs(Jo).max()
+    assert np.all(np.abs(J - Jo) <= 2e-3 * scale + 1e-3 * np.abs(Jo))
+
+
+@pytest.mark.parametrize("textured", [False, True])
+def test_adjoint_pose_and_map(aslam_gpu, orc, soft, textured):
+    E, W, B = 3, 128, 180
+    L, pose = maps_and_poses(E, W, 41 + textured, textured)
+    rng = np.random.default_rng(3)
+    gr = rng.normal(size=(E, B)).astype(np.float32)
+    cfg = soft.soft_config(E, W, W, B)
+    Lt, pt = torch.from_numpy(L).cuda(), torch.from_numpy(pose).cuda()
+    gp, gm = soft.soft_range_bwd(cfg, Lt, pt, torch.from_numpy(gr).cuda())
+    _, gpo, gmo = orc.soft_ranges(orc.soft_cfg(W, W, B), L, pose, gr=gr.astype(np.float64),
+                                  grad_pose=True, grad_map=True)
+    gp, gm = gp.cpu().numpy(), gm.cpu().numpy()
+    assert np.all(np.abs(gp - gpo) <= 2e-3 * np.abs(gpo).max() + 1e-3 * np.abs(gpo))
+    assert np.all(np.abs(gm - gmo) <= 2e-3 * np.abs(gmo).max() + 1e-3 * np.abs(gmo))
+
+
+def test_autograd_function_matches_adjoint(aslam_gpu, orc, soft):
+    E, W, B = 2, 96, 72
+    L, pose = maps_and_poses(E, W, 51, True)
+    pt = torch.from_numpy(pose).cuda().requires_grad_(True)
+    Lt = torch.from_numpy(L).cuda().requires_grad_(True)
+    r = soft.soft_range(pt, Lt, B)
+    w = torch.linspace(-1, 1, E * B, device="cuda").view(E, B)
+    (r * w).sum().backward()
+    _, gpo, gmo = orc.soft_ranges(orc.soft_cfg(W, W, B), L, pose,
+                                  gr=w.cpu().numpy().astype(np.float64), grad_pose=True,
+                                  grad_map=True)
+    gp, gm = pt.grad.cpu().numpy(), Lt.grad.cpu().numpy()
+    assert np.all(np.abs(gp - gpo) <= 2e-3 * np.abs(gpo).max() + 1e-3 * np.abs(gpo))
+    assert np.all(np.abs(gm - gmo) <= 2e-3 * np.abs(gmo).max() + 1e-3 * np.abs(gmo))
+
+
+def test_adjoint_against_gpu_finite_differences(aslam_gpu, soft):
+    """Central differences of the kernel's own fp32 forward at h = 1e-3."""
+    E, W, B = 2, 128, 90
+    L, pose = maps_and_poses(E, W, 61, False)
+    cfg = soft.soft_config(E, W, W, B)
+    Lt = torch.from_numpy(L).cuda()
+    pt = torch.from_numpy(pose).cuda()
+    gr = torch.ones(E, B, device="cuda")
+    gp, _ = soft.soft_range_bwd(cfg, Lt, pt, gr, grad_map=False)
+    h = 1e-3
+    for d in range(3):
+        e = torch.zeros(E, 3, device="cuda"); e[:, d] = h
+        fd = (soft.soft_range_fwd(cfg, Lt, pt + e).sum(1) - soft.soft_range_fwd(cfg, Lt, pt - e).sum(1)) / (2 * h)
+        # bilinear kinks inside +-h shift an FD estimate by O(h) per sample
+        assert torch.allclose(gp[:, d], fd, rtol=2e-2, atol=0.05 * B ** 0.5), (d, gp[:, d], fd)
+
+
+def test_gauss_newton_matches_oracle(aslam_gpu, orc, soft):
+    E, W, B = 6, 256, 360
+    inp = synth.paper_scale(E=E, W=W, B=8, seed=71)
+    L = synth.logodds_maps(inp)
+    true = np.ascontiguousarray(inp.spawn[:, 0, :])
+    ocfg = orc.soft_cfg(W, W, B)
+    z, _, _ = orc.soft_ranges(ocfg, L, true)
+    z = z.astype(np.float32)
+    start = synth.perturb_poses(true, 72)
+    po, Ao = orc.gn(ocfg, L, start, z, iters=5)
+    cfg = soft.soft_config(E, W, W, B)
+    pg, cov, u = soft.gn_correct(cfg, torch.from_numpy(L).cuda(), torch.from_numpy(start).cuda(),
+                                 torch.from_numpy(z).cuda(), iters=5)
+    pg, cov, u = pg.cpu().numpy(), cov.cpu().numpy(), u.cpu().numpy()
+    conv = np.all(np.abs(po - true) < 1e-3, axis=1)
+    assert conv.sum() >= 4
+    assert np.all(np.abs(pg[conv] - po[conv]) <= 1e-4)
+    cov_o = 0.01 ** 2 * np.linalg.inv(Ao)
+    u_o = np.cbrt(np.linalg.det(cov_o))
+    np.testing.assert_allclose(cov[conv], cov_o[conv], rtol=2e-2, atol=1e-3 * np.abs(cov_o).max())
+    np.testing.assert_allclose(u[conv], u_o[conv], rtol=2e-2)
+
+
+def test_full_size_gn_sampled(aslam_gpu, orc, soft):
+    """1024 envs x 256^2, 360 beams, 64 samples, 5 GN iterations (the
+    differentiable-form workload) in one launch; 3 sampled envs vs the oracle."""
+    E, W, B = 1024, 256, 360
+    inp = synth.paper_scale(E=E, W=W, B=8, seed=81)
+    L = synth.logodds_maps(inp)
+    true = np.ascontiguousarray(inp.spawn[:, 0, :])
+    start = synth.perturb_poses(true, 82)
+    cfg = soft.soft_config(E, W, W, B)
+    Lt = torch.from_numpy(L).cuda()
+    z = soft.soft_range_fwd(cfg, Lt, torch.from_numpy(true).cuda())
+    pg, cov, u = soft.gn_correct(cfg, Lt, torch.from_numpy(start).cuda(), z, iters=5)
+    torch.cuda.synchronize()
+    pg = pg.cpu().numpy()
+    assert np.all(np.isfinite(pg)) and np.all(np.isfinite(u.cpu().numpy()))
+    ocfg = orc.soft_cfg(W, W, B)
+    for e in (0, 511, 1023):
+        zo, _, _ = orc.soft_ranges(ocfg, L[e:e + 1], true[e:e + 1])
+        assert np.abs(z[e].cpu().numpy() - zo[0]).max() <= R_TOL
+        po, _ = orc.gn(ocfg, L[e:e + 1], start[e:e + 1], z[e:e + 1].cpu().numpy(), iters=5)
+        if np.all(np.abs(po[0] - true[e]) < 1e-3):
+            assert np.all(np.abs(pg[e] - po[0]) <= 1e-4)
+    # most envs converge
+    assert np.mean(np.all(np.abs(pg - true) < 2e-3, axis=1)) > 0.8
