@@ -173,12 +173,84 @@ def run_reference(args):
     return 0
 
 
+def bench_diff(args):
+    """Differentiable form: 1024 envs x 256^2 fp32 log-odds, 360 beams x 64
+    samples of 0.05 m; a step is one Gauss-Newton correction (5 iterations)
+    of every env from N(0, 5 cm, 0.02 rad) perturbed poses."""
+    import torch
+    from paper_2603_25834_gb300 import soft, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    E, W, B, K, iters = 1024, 256, 360, 64, 5
+    inp = synth.paper_scale(E=E, W=W, B=8, seed=synth.BASE_SEED + 300_000)
+    L = torch.from_numpy(synth.logodds_maps(inp)).to(dev)
+    true = torch.from_numpy(np.ascontiguousarray(inp.spawn[:, 0, :])).to(dev)
+    cfg = soft.soft_config(E, W, W, B, K)
+    z = soft.soft_range_fwd(cfg, L, true)
+    steps, warm = args.steps if args.steps != 1000 else 50, args.warmup
+    starts = [torch.from_numpy(synth.perturb_poses(inp.spawn[:, 0, :], 90 + k)).to(dev)
+              for k in range(steps + warm)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for k in range(warm):
+        soft.gn_correct(cfg, L, starts[k], z, iters)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, n):
+        tot = 0.0
+        for k in range(n):
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / n
+
+    clocks = ClockSampler(dev.index)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ms_gn = timed(lambda k: soft.gn_correct(cfg, L, starts[warm + k], z, iters), steps)
+    clk = clocks.stop()
+    ms_fwd = timed(lambda k: soft.soft_range_fwd(cfg, L, starts[k]), min(steps, 20))
+    gr = torch.ones(E, B, device=dev)
+    gmap = torch.zeros_like(L)
+    ms_bwd = timed(lambda k: soft.soft_range_bwd(cfg, L, starts[k], gr), min(steps, 20))
+    # FP32 operations per sample in the forward-mode sweep, counted from the
+    # kernel source: bilinear 34, sigmoid 5, tangents and accumulators 35.
+    flops = float(E) * B * K * (iters + 1) * 74
+    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = flops / (ms_gn / 1e3) / 1e12
+    pg, cov, u = soft.gn_correct(cfg, L, starts[0], z, iters)
+    conv = float(((pg - true).abs() < 2e-3).all(dim=1).float().mean())
+    line = {
+        "metric": "env Gauss-Newton corrections/s (differentiable form)",
+        "value": E / (ms_gn / 1e3), "unit": "env-GN-steps/s", "n_gpus": 1, "steps": steps,
+        "warmup": warm, "ms_per_step": ms_gn, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "diff: 1024 envs x 256^2 fp32 log-odds, 360 beams x 64 samples "
+                               "@0.05 m, 5 GN iterations from N(0, 5 cm, 0.02 rad)",
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "converged_frac": conv},
+        "soft_fwd_ms": ms_fwd, "soft_bwd_ms": ms_bwd,
+        "rays_per_s_gn": E * B * (iters + 1) / (ms_gn / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None,
+                     "peak_kind": "nominal FP32 FMA rate: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                     "kernel": "gn_kernel"},
+        "gpu_launches": steps, "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "uneven", "diff"])
     ap.add_argument("--envs", type=int, default=750)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,6 +262,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "diff":
+        return bench_diff(args)
 
     import torch
     import torch.distributed as dist
@@ -204,8 +278,19 @@ def main():
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
 
-    E = args.envs
-    inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+    if args.workload == "uneven":
+        E = args.envs if args.envs != 750 else 4096
+        inp = synth.uneven(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+        workload = dict(workload="uneven: %d envs, sides {128,256,384,512} @0.05 m, beams "
+                                 "{180,360,720}, 12 m, sigma 0.01 m, persistent launch, CUDA graph" % E,
+                        envs=E, res_m=0.05, r_max_m=12.0, noise_sigma_m=0.01,
+                        reward="composite Eq. 7-17", l2="flushed (256 MiB write) between timed steps",
+                        mean_beams=float(inp.n_beams.mean()),
+                        mean_cells=float((inp.map_w.astype(np.int64) * inp.map_h).mean()))
+    else:
+        E = args.envs
+        inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+        workload = dict(WORKLOAD, envs=E)
     batch = aslam.Batch2D(inp, device=dev, r_max_m=12.0, noise_sigma_m=0.01,
                           reward_mode=aslam.REWARD_COMPOSITE, threads_per_cta=args.threads,
                           window_cells=args.window)
@@ -317,8 +402,8 @@ def main():
     # Algorithmic bytes of one launch: every updated cell read+written as
     # int16 (4 B), every ground-truth cell read (1 B), ranges and observation
     # written, pose/action/reward (24 B per env).
-    B = int(inp.n_beams[0])
-    alg_bytes = (ray_cells * 4 + gt_cells * 1) / K + E * B * 4 + E * (B + 2) * 4 + E * 24
+    Bsum = int(inp.n_beams.sum())
+    alg_bytes = (ray_cells * 4 + gt_cells * 1) / K + Bsum * 4 + E * (batch.b_max + 2) * 4 + E * 24
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
     traffic = None
@@ -328,7 +413,7 @@ def main():
         if tr.get("kernel_hash") == kernel_hash():
             traffic = tr.get("dram_bytes_per_launch")
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.workload == "paper_scale":
         n_s, steps_s = 48, 60
         rate, rcs, dt = oracle_rate(inp, n_s, steps_s)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -338,7 +423,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16+f32", "data": "synthetic",
-        "config": dict(WORKLOAD, autotuned=({"threads_per_cta": tuned[0], "window_cells": tuned[1]}
+        "config": dict(workload, autotuned=({"threads_per_cta": tuned[0], "window_cells": tuned[1]}
                                             if tuned else None)),
         "ray_cells_per_s": world * ray_cells / (total_ms_max / 1e3),
         "ray_cells_per_step": ray_cells / K,
