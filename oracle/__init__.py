@@ -21,7 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["aslam_oracle.c", "soft_range_oracle.c"]
+_SOURCES = ["aslam_oracle.c", "soft_range_oracle.c", "raycast3d_oracle.c"]
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -87,6 +87,26 @@ class OrcOut(C.Structure):
                 ("ray_cells", P), ("gt_cells", P)]
 
 
+class OrcCfg3D(C.Structure):
+    _fields_ = [
+        ("n_envs", C.c_int32), ("n_rings", C.c_int32), ("n_az", C.c_int32), ("n_spawn", C.c_int32),
+        ("hit_q", C.c_int32), ("miss_q", C.c_int32), ("clamp_q", C.c_int32), ("t_episode", C.c_int32),
+        ("seed", C.c_uint64),
+        ("res", C.c_float), ("r_max", C.c_float), ("sigma", C.c_float), ("dt", C.c_float),
+        ("v_max", C.c_float), ("w_max", C.c_float), ("d_crash", C.c_float), ("d_full", C.c_float),
+        ("visit_cell", C.c_float), ("sensor_z", C.c_float),
+        ("el_min", C.c_double), ("el_max", C.c_double), ("logodds_scale", C.c_double),
+        ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
+        ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
+        ("map_w", P), ("map_h", P), ("map_d", P), ("map_off", P), ("visit_off", P),
+    ]
+
+
+class OrcOut3D(C.Structure):
+    _fields_ = [("z", P), ("z_true", P), ("hit", P), ("cnt_h", P), ("cnt_m", P), ("terms", P),
+                ("obs", P), ("ray_cells", P), ("gt_cells", P)]
+
+
 class OrcSoftCfg(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("B", C.c_int32), ("K", C.c_int32),
                 ("res", C.c_double), ("ds", C.c_double), ("fov", C.c_double)]
@@ -120,6 +140,12 @@ def _declare(L):
     L.orc_step2d.argtypes = [C.POINTER(OrcCfg), C.POINTER(OrcState), P, P, C.POINTER(OrcOut)]
     L.orc_step2d.restype = C.c_int
     L.orc_soft_ranges.argtypes = [C.POINTER(OrcSoftCfg), P, P, C.c_int, P, P, P, P]
+    L.orc_walk3d.argtypes = [C.c_int32] * 6 + [C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                               P, P, P, C.c_int, C.POINTER(C.c_int)]
+    L.orc_walk3d.restype = C.c_int
+    L.orc_beams3d.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, P]
+    L.orc_step3d.argtypes = [C.POINTER(OrcCfg3D), C.POINTER(OrcState), P, P, C.POINTER(OrcOut3D)]
+    L.orc_step3d.restype = C.c_int
     L.orc_soft_jacobian.argtypes = [C.POINTER(OrcSoftCfg), P, P, C.c_int, P, P]
     L.orc_gn_batch.argtypes = [C.POINTER(OrcSoftCfg), P, P, P, C.c_int, C.c_int, C.c_double, P, P]
 
@@ -323,3 +349,90 @@ def soft_jacobian(cfg, L, pose):
     J = np.zeros((E, cfg.B, 3), np.float64)
     lib().orc_soft_jacobian(C.byref(cfg), _ptr(L), _ptr(pose), E, _ptr(r), _ptr(J))
     return r, J
+
+
+# ---------------------------------------------------------------- 3-D variant
+def walk3d(Px, Py, Pz, Dx, Dy, Dz, T, W, H, D):
+    cap = W + H + D + 8
+    cells = np.zeros(cap, dtype=np.int64)
+    en = np.zeros(cap, dtype=np.int64)
+    ea = np.zeros(cap, dtype=np.int64)
+    left = C.c_int()
+    n = lib().orc_walk3d(Px, Py, Pz, Dx, Dy, Dz, T, W, H, D, _ptr(cells), _ptr(en), _ptr(ea), cap,
+                         C.byref(left))
+    return cells[:n].copy(), en[:n].copy(), ea[:n].copy(), bool(left.value)
+
+
+DEFAULTS3D = dict(r_max=20.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0, hit_q=870, miss_q=-410,
+                  clamp_q=3584, logodds_scale=1.0 / 1024.0, t_episode=2048, d_crash=0.15,
+                  d_full=0.5, visit_cell=0.5, sensor_z=0.5, el_min=-15.0 * np.pi / 180,
+                  el_max=15.0 * np.pi / 180, lam_col=10.0, lam_explore=1.0, lam_abs=0.1,
+                  lam_delta=1.0, kappa=0.05, u_hi=1.0, seed=20260325)
+
+
+class OracleBatch3D:
+    """Numpy state of E voxel environments stepped by orc_step3d."""
+
+    def __init__(self, inputs, n_rings=16, **params):
+        p = dict(DEFAULTS3D)
+        p.update(params)
+        self.p = p
+        self.inp = inputs
+        E = inputs.n_envs
+        self.E = E
+        self.R, self.A = int(n_rings), int(inputs.n_beams[0])
+        assert np.all(inputs.n_beams == self.A)
+        self.B = self.R * self.A
+        self.map_w = np.ascontiguousarray(inputs.map_w, dtype=np.int32)
+        self.map_h = np.ascontiguousarray(inputs.map_h, dtype=np.int32)
+        self.map_d = np.ascontiguousarray(inputs.map_d, dtype=np.int32)
+        self.map_off = np.ascontiguousarray(inputs.map_off, dtype=np.int64)
+        dims = [visit_dims(int(w), int(h), inputs.res, p["visit_cell"])
+                for w, h in zip(self.map_w, self.map_h)]
+        self.visit_off = np.zeros(E + 1, dtype=np.int64)
+        self.visit_off[1:] = np.cumsum([a * b for a, b in dims])
+        self.gt = np.ascontiguousarray(inputs.gt, dtype=np.uint8)
+        self.spawn = np.ascontiguousarray(inputs.spawn, dtype=np.float32)
+        self.belief = np.zeros(int(self.map_off[-1]), dtype=np.int16)
+        self.x = self.spawn[:, 0, 0].copy()
+        self.y = self.spawn[:, 0, 1].copy()
+        self.th = self.spawn[:, 0, 2].copy()
+        self.u_prev = np.zeros(E, np.float32)
+        self.t = np.zeros(E, np.int32)
+        self.g = np.zeros(E, np.int32)
+        self.ep = np.zeros(E, np.int32)
+        self.done = np.zeros(E, np.uint8)
+        self.visit = np.full(int(self.visit_off[-1]), -1, np.int32)
+        self.cfg = OrcCfg3D(
+            n_envs=E, n_rings=self.R, n_az=self.A, n_spawn=self.spawn.shape[1],
+            hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"], t_episode=p["t_episode"],
+            seed=p["seed"], res=inputs.res, r_max=p["r_max"], sigma=p["sigma"], dt=p["dt"],
+            v_max=p["v_max"], w_max=p["w_max"], d_crash=p["d_crash"], d_full=p["d_full"],
+            visit_cell=p["visit_cell"], sensor_z=p["sensor_z"], el_min=p["el_min"],
+            el_max=p["el_max"], logodds_scale=p["logodds_scale"], lam_col=p["lam_col"],
+            lam_explore=p["lam_explore"], lam_abs=p["lam_abs"], lam_delta=p["lam_delta"],
+            kappa=p["kappa"], u_hi=p["u_hi"], map_w=_ptr(self.map_w), map_h=_ptr(self.map_h),
+            map_d=_ptr(self.map_d), map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off))
+
+    def step(self, actions, u=None, counts=False):
+        E, B = self.E, self.B
+        a = np.ascontiguousarray(actions, dtype=np.float32).reshape(E, 2)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float32).reshape(E)
+        n = int(self.map_off[-1])
+        o = dict(z=np.zeros((E, B), np.float32), z_true=np.zeros((E, B), np.float32),
+                 hit=np.zeros((E, B), np.uint8), terms=np.zeros((E, N_TERMS), np.float64),
+                 obs=np.zeros((E, B + 2), np.float32), ray_cells=np.zeros(E, np.int64),
+                 gt_cells=np.zeros(E, np.int64))
+        if counts:
+            o["cnt_h"] = np.zeros(n, np.int32)
+            o["cnt_m"] = np.zeros(n, np.int32)
+        out = OrcOut3D(z=_ptr(o["z"]), z_true=_ptr(o["z_true"]), hit=_ptr(o["hit"]),
+                       cnt_h=_ptr(o.get("cnt_h")), cnt_m=_ptr(o.get("cnt_m")), terms=_ptr(o["terms"]),
+                       obs=_ptr(o["obs"]), ray_cells=_ptr(o["ray_cells"]), gt_cells=_ptr(o["gt_cells"]))
+        st = OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x), y=_ptr(self.y),
+                      th=_ptr(self.th), u_prev=_ptr(self.u_prev), t=_ptr(self.t), g=_ptr(self.g),
+                      ep=_ptr(self.ep), done=_ptr(self.done), visit=_ptr(self.visit),
+                      spawn=_ptr(self.spawn))
+        if lib().orc_step3d(C.byref(self.cfg), C.byref(st), _ptr(a), _ptr(uu), C.byref(out)) != 0:
+            raise RuntimeError("orc_step3d failed")
+        return o

@@ -222,3 +222,57 @@ def perturb_poses(poses, seed, sigma=(0.05, 0.05, 0.02)):
     rng = np.random.default_rng(seed)
     p = np.asarray(poses, dtype=np.float64)
     return (p + rng.normal(0.0, 1.0, p.shape) * np.asarray(sigma)).astype(np.float32)
+
+
+@dataclasses.dataclass
+class Batch3DInputs:
+    """A batch of voxel worlds: env e is W x H x D at map_off[e], flat (k*H + j)*W + i."""
+    map_w: np.ndarray
+    map_h: np.ndarray
+    map_d: np.ndarray
+    n_beams: np.ndarray      # azimuths per ring
+    res: float
+    gt: np.ndarray
+    map_off: np.ndarray
+    spawn: np.ndarray        # [E, K, 3]
+
+    @property
+    def n_envs(self):
+        return int(self.map_w.shape[0])
+
+
+def make_world_3d(W, H, D, res, rng, n_box=(8, 16), box_side=(0.5, 3.0), box_h=(0.3, 3.2),
+                  n_pillar=(4, 10), pillar_r=(0.1, 0.4), floor=True):
+    """uint8 [D, H, W]: floor layer, boxes standing on it and full-height pillars."""
+    cx = (np.arange(W) + 0.5) * res
+    cy = (np.arange(H) + 0.5) * res
+    cz = (np.arange(D) + 0.5) * res
+    occ = np.zeros((D, H, W), np.uint8)
+    for _ in range(int(rng.integers(n_box[0], n_box[1] + 1))):
+        x0, y0 = rng.uniform(0, W * res), rng.uniform(0, H * res)
+        sx, sy, hz = rng.uniform(*box_side), rng.uniform(*box_side), rng.uniform(*box_h)
+        m2 = (np.abs(cx[None, :] - x0) <= sx / 2) & (np.abs(cy[:, None] - y0) <= sy / 2)
+        occ[cz <= hz] |= m2.astype(np.uint8)
+    for _ in range(int(rng.integers(n_pillar[0], n_pillar[1] + 1))):
+        x0, y0, r = rng.uniform(0, W * res), rng.uniform(0, H * res), rng.uniform(*pillar_r)
+        m2 = ((cx[None, :] - x0) ** 2 + (cy[:, None] - y0) ** 2) <= r * r
+        occ |= m2.astype(np.uint8)[None]
+    if floor:
+        occ[0] = 1
+    return occ
+
+
+def voxel_batch(E=512, W=128, H=128, D=32, res=0.1, n_az=512, seed=BASE_SEED, K=8, clearance=0.3):
+    """E voxel worlds with floor, boxes and pillars; spawns on free columns."""
+    grids, spawns = [], []
+    for e in range(E):
+        occ = make_world_3d(W, H, D, res, np.random.default_rng(seed + e))
+        grids.append(occ)
+        column = World2D(W, H, res, occ[1:].max(axis=0))
+        spawns.append(spawn_poses_2d(column, K, np.random.default_rng(seed + 10_000_000 + e),
+                                     clearance=clearance))
+    off = np.zeros(E + 1, np.int64)
+    off[1:] = np.cumsum([g.size for g in grids])
+    return Batch3DInputs(np.full(E, W, np.int32), np.full(E, H, np.int32), np.full(E, D, np.int32),
+                         np.full(E, n_az, np.int32), float(res),
+                         np.concatenate([g.reshape(-1) for g in grids]), off, np.stack(spawns))
