@@ -83,7 +83,7 @@ typedef struct {
     uint32_t struct_size;          /* sizeof(aslam_config) */
     uint32_t version;              /* ASLAM_CONFIG_VERSION */
     int32_t n_envs;                /* E >= 1 */
-    int32_t dims;                  /* 2 (3: see aslam3d_*) */
+    int32_t dims;                  /* 2: planar grids; 3: voxel volumes (fields at the end) */
     int32_t n_spawn;               /* spawn poses per env, >= 1 */
     int32_t reward_mode;           /* ASLAM_REWARD_* */
     const int32_t *h_map_w;        /* HOST [E]: grid width W (cells), >= 1 */
@@ -109,6 +109,14 @@ typedef struct {
     uint64_t seed;                 /* noise stream key (Philox4x32-10) */
     int32_t flags;                 /* ASLAM_FLAG_* */
     int32_t window_cells;          /* side of the shared-memory counter window; 0 = auto */
+    /* 3-D voxel variant (dims = 3): W x H x D voxels, a multi-ring LiDAR of
+     * n_rings elevations evenly spaced over [elev_min, elev_max] (both ends
+     * included) times h_n_beams[e] azimuths over a full turn, mounted at
+     * sensor_z_m; beam index b = ring * azimuths + azimuth.  W must be a
+     * multiple of 8.  Ignored for dims = 2. */
+    const int32_t *h_map_d;        /* HOST [E]: depth D (voxels) */
+    int32_t n_rings;
+    float sensor_z_m, elev_min_rad, elev_max_rad;
 } aslam_config;
 
 #define ASLAM_MAX_BEAMS 1024

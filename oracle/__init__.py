@@ -99,6 +99,7 @@ class OrcCfg3D(C.Structure):
         ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
         ("map_w", P), ("map_h", P), ("map_d", P), ("map_off", P), ("visit_off", P),
+        ("env_id", P),
     ]
 
 
@@ -373,9 +374,13 @@ DEFAULTS3D = dict(r_max=20.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0, hit_q=870
 class OracleBatch3D:
     """Numpy state of E voxel environments stepped by orc_step3d."""
 
-    def __init__(self, inputs, n_rings=16, **params):
+    def __init__(self, inputs, n_rings=16, env_ids=None, **params):
         p = dict(DEFAULTS3D)
         p.update(params)
+        # the elevation limits and sensor height are fp32 quantities of the
+        # sensor description: both implementations start from the same floats
+        for k in ("el_min", "el_max", "sensor_z"):
+            p[k] = float(np.float32(p[k]))
         self.p = p
         self.inp = inputs
         E = inputs.n_envs
@@ -403,6 +408,7 @@ class OracleBatch3D:
         self.ep = np.zeros(E, np.int32)
         self.done = np.zeros(E, np.uint8)
         self.visit = np.full(int(self.visit_off[-1]), -1, np.int32)
+        self.env_ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
         self.cfg = OrcCfg3D(
             n_envs=E, n_rings=self.R, n_az=self.A, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"], t_episode=p["t_episode"],
@@ -412,7 +418,8 @@ class OracleBatch3D:
             el_max=p["el_max"], logodds_scale=p["logodds_scale"], lam_col=p["lam_col"],
             lam_explore=p["lam_explore"], lam_abs=p["lam_abs"], lam_delta=p["lam_delta"],
             kappa=p["kappa"], u_hi=p["u_hi"], map_w=_ptr(self.map_w), map_h=_ptr(self.map_h),
-            map_d=_ptr(self.map_d), map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off))
+            map_d=_ptr(self.map_d), map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off),
+            env_id=_ptr(self.env_ids))
 
     def step(self, actions, u=None, counts=False):
         E, B = self.E, self.B

@@ -115,6 +115,7 @@ typedef struct {
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     const int32_t *map_w, *map_h, *map_d;
     const int64_t *map_off, *visit_off;
+    const int32_t *env_id;     /* [E] index of each env in the noise stream, or NULL */
 } orc_cfg3d;
 
 typedef struct {
@@ -229,7 +230,8 @@ int orc_step3d(const orc_cfg3d *cfg, orc_state3d *st, const float *actions, cons
                 if (!hit)
                     gt_cells += nc;
                 if (hit) {
-                    float g = orc_gauss(cfg->seed, (uint32_t)e, (uint32_t)st->g[e], (uint32_t)b);
+                    uint32_t eid = cfg->env_id ? (uint32_t)cfg->env_id[e] : (uint32_t)e;
+                    float g = orc_gauss(cfg->seed, eid, (uint32_t)st->g[e], (uint32_t)b);
                     z = fminf(fmaxf(z_true + cfg->sigma * g, 0.0f), cfg->r_max);
                 }
                 int32_t Tz = hit ? (int32_t)lrintf((z / cfg->res) * 65536.0f) : Tmax;

@@ -54,6 +54,8 @@ class AslamConfig(C.Structure):
         ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
         ("seed", C.c_uint64), ("flags", C.c_int32), ("window_cells", C.c_int32),
+        ("h_map_d", P), ("n_rings", C.c_int32), ("sensor_z_m", C.c_float),
+        ("elev_min_rad", C.c_float), ("elev_max_rad", C.c_float),
     ]
 
 
@@ -154,12 +156,15 @@ def config_defaults() -> AslamConfig:
 
 
 _FLOAT_KEYS = {"res_m", "r_max_m", "fov_rad", "noise_sigma_m", "dt_s", "v_max", "w_max",
+               "sensor_z_m", "elev_min_rad", "elev_max_rad",
                "d_crash", "d_full", "visit_cell_m", "logodds_scale", "lam_col", "lam_explore",
                "lam_abs", "lam_delta", "kappa", "u_hi"}
 
 
 class Batch2D:
-    """A batch of 2-D environments stepped by libaslam on the current CUDA device."""
+    """A batch of environments stepped by libaslam on the current CUDA device:
+    planar grids (synth.Batch2DInputs) or voxel volumes (synth.Batch3DInputs,
+    then `n_rings` and the elevation / sensor-height fields apply)."""
 
     def __init__(self, inputs, device="cuda", **cfg):
         if not torch.cuda.is_available():
@@ -181,6 +186,15 @@ class Batch2D:
         c.h_map_w = self._w.ctypes.data_as(P)
         c.h_map_h = self._h.ctypes.data_as(P)
         c.h_n_beams = self._b.ctypes.data_as(P)
+        self.dims = 3 if hasattr(inputs, "map_d") else 2
+        if self.dims == 3:
+            self._d = np.ascontiguousarray(inputs.map_d, dtype=np.int32)
+            c.dims = 3
+            c.h_map_d = self._d.ctypes.data_as(P)
+            c.n_rings = 16
+            c.sensor_z_m = 0.5
+            c.elev_min_rad = -15.0 * np.pi / 180
+            c.elev_max_rad = 15.0 * np.pi / 180
         for k, v in cfg.items():
             if not hasattr(c, k):
                 raise AslamError(1, "unknown config field %s" % k)
@@ -252,6 +266,9 @@ class Batch2D:
         st = self.state()["belief"]
         a = int(self.map_off[e])
         W, H = int(self._w[e]), int(self._h[e])
+        if self.dims == 3:
+            D = int(self._d[e])
+            return st[a:a + W * H * D].view(D, H, W)
         return st[a:a + W * H].view(H, W)
 
     # ------------------------------------------------------------------ calls

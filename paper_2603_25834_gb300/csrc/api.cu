@@ -24,14 +24,14 @@ constexpr size_t kAlign = 256;
 constexpr int kCellPad = 256;    // env grids start on 512-byte (int16) boundaries
 
 struct HostInfo {
-    int E = 0, b_max = 0, r8_max = 1;
-    std::vector<int> W, H, B, Vw, Vh, R8;
+    int E = 0, b_max = 0, r8_max = 1, dims = 2, n_rings = 1;
+    std::vector<int> W, H, B, Vw, Vh, R8, D;
     std::vector<long long> map_off, gtb_off, ray_off, visit_off;
     int gt_words_max = 0;
 };
 
 struct Offsets {
-    size_t W, H, B, Vw, Vh, R8, order, map_off, gtb_off, ray_off, visit_off, src_off;
+    size_t W, H, B, Vw, Vh, R8, Dd, elev, order, map_off, gtb_off, ray_off, visit_off, src_off;
     size_t beam_cs, lut, gt_bits;
     size_t x, y, th, u_prev, t, g, ep, done, Hq;
     size_t belief, visit, spawn;
@@ -76,7 +76,18 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (c->struct_size != sizeof(aslam_config)) return fail("config struct_size mismatch");
     if (c->version != ASLAM_CONFIG_VERSION) return fail("config version mismatch");
     if (c->n_envs < 1) return fail("n_envs must be >= 1");
-    if (c->dims != 2) return fail("dims must be 2 for aslam_create_batch");
+    if (c->dims != 2 && c->dims != 3) return fail("dims must be 2 or 3");
+    if (c->dims == 3) {
+        if (!c->h_map_d) return fail("h_map_d is NULL for a 3-D batch");
+        if (c->n_rings < 1 || c->n_rings > 256) return fail("n_rings out of [1, 256]");
+        if (!(c->elev_min_rad <= c->elev_max_rad)) return fail("elev_min_rad exceeds elev_max_rad");
+        for (int e = 0; e < c->n_envs; ++e) {
+            if (c->h_map_d[e] < 1 || c->h_map_d[e] > 4096) return fail("map depth out of [1, 4096]");
+            if (c->h_map_w[e] % 8) return fail("3-D maps need a width that is a multiple of 8");
+            if ((long long)c->h_map_w[e] * c->h_map_h[e] * c->h_map_d[e] > (1LL << 30))
+                return fail("3-D map larger than 2^30 voxels");
+        }
+    }
     if (c->n_spawn < 1) return fail("n_spawn must be >= 1");
     if (!c->h_map_w || !c->h_map_h || !c->h_n_beams) return fail("map dims / beams arrays are NULL");
     for (int e = 0; e < c->n_envs; ++e) {
@@ -85,6 +96,8 @@ bool validate(const aslam_config *c, std::string *msg) {
             return fail("map side out of [1, ASLAM_MAX_MAP_SIDE]");
         if (c->h_n_beams[e] < 0 || c->h_n_beams[e] > ASLAM_MAX_BEAMS)
             return fail("n_beams out of [0, ASLAM_MAX_BEAMS]");
+        if (c->dims == 2 && (long long)c->h_map_w[e] * c->h_map_h[e] > (1LL << 26))
+            return fail("2-D map larger than 2^26 cells");
     }
     if (!(c->res_m > 0.0f) || !(c->r_max_m > 0.0f)) return fail("res_m and r_max_m must be > 0");
     if ((double)c->r_max_m / c->res_m > 16384.0) return fail("r_max_m / res_m must be <= 16384 cells");
@@ -112,10 +125,16 @@ bool validate(const aslam_config *c, std::string *msg) {
 void host_info(const aslam_config *c, HostInfo *hi) {
     const int E = c->n_envs;
     hi->E = E;
+    hi->dims = c->dims;
+    hi->n_rings = c->dims == 3 ? c->n_rings : 1;
     hi->W.assign(c->h_map_w, c->h_map_w + E);
     hi->H.assign(c->h_map_h, c->h_map_h + E);
     hi->B.assign(c->h_n_beams, c->h_n_beams + E);
-    hi->b_max = *std::max_element(hi->B.begin(), hi->B.end());
+    hi->D.assign(E, 1);
+    if (c->dims == 3) {
+        hi->D.assign(c->h_map_d, c->h_map_d + E);
+        for (int e = 0; e < E; ++e) hi->B[e] *= c->n_rings;   // beams = rings x azimuths
+    }
     hi->Vw.resize(E);
     hi->Vh.resize(E);
     hi->R8.resize(E);
@@ -125,8 +144,9 @@ void host_info(const aslam_config *c, HostInfo *hi) {
     hi->ray_off.assign(E + 1, 0);
     hi->visit_off.assign(E + 1, 0);
     hi->gt_words_max = 0;
+    hi->b_max = *std::max_element(hi->B.begin(), hi->B.end());
     for (int e = 0; e < E; ++e) {
-        const long long n = (long long)hi->W[e] * hi->H[e];
+        const long long n = (long long)hi->W[e] * hi->H[e] * hi->D[e];
         const long long words = (long long)pad_to((size_t)((n + 31) / 32), 4);
         hi->map_off[e + 1] = hi->map_off[e] + (long long)pad_to((size_t)n, kCellPad);
         hi->gtb_off[e + 1] = hi->gtb_off[e] + words;
@@ -134,7 +154,7 @@ void host_info(const aslam_config *c, HostInfo *hi) {
         visit_dims(hi->W[e], hi->H[e], c->res_m, c->visit_cell_m, &hi->Vw[e], &hi->Vh[e]);
         hi->visit_off[e + 1] = hi->visit_off[e] + (long long)hi->Vw[e] * hi->Vh[e];
         hi->gt_words_max = std::max(hi->gt_words_max, (int)words);
-        hi->R8[e] = near_radius(hi->B[e], (double)c->fov_rad);
+        hi->R8[e] = c->dims == 3 ? 1 : near_radius(hi->B[e], (double)c->fov_rad);
         hi->r8_max = std::max(hi->r8_max, hi->R8[e]);
     }
 }
@@ -157,6 +177,8 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.Vw = add(4 * E);
     o.Vh = add(4 * E);
     o.R8 = add(4 * E);
+    o.Dd = add(4 * E);
+    o.elev = add(8 * (size_t)hi.n_rings);
     o.order = add(4 * E);
     o.map_off = add(8 * (E + 1));
     o.gtb_off = add(8 * (E + 1));
@@ -281,6 +303,22 @@ int auto_window(const HostInfo &hi, int smem_optin) {
 }
 
 aslam_status configure_launch(aslam_batch *b, int block, int S) {
+    if (b->hi.dims == 3) {
+        // voxel batches: ground-truth bits in shared memory, global counters
+        const size_t smem = 4 * (size_t)b->hi.gt_words_max;
+        if (smem + kStaticSmem > (size_t)b->smem_optin)
+            return fail_b(b, ASLAM_ERR_UNSUPPORTED, "voxel map too large for shared memory");
+        CK(step3d_set_smem(smem), "cudaFuncSetAttribute");
+        int per_sm = 0;
+        CK(step3d_occupancy(block, smem, &per_sm), "occupancy");
+        if (per_sm < 1) return fail_b(b, ASLAM_ERR_INVALID_ARG, "launch configuration does not fit an SM");
+        b->block = block;
+        b->window = 0;
+        b->smem = smem;
+        b->grid = std::min(b->hi.E, b->sm_count * per_sm);
+        b->p.gt_words_max = b->hi.gt_words_max;
+        return ASLAM_OK;
+    }
     int ww = 0;
     std::string msg;
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
@@ -303,6 +341,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
 }
 
 int default_block(const HostInfo &hi) {
+    if (hi.dims == 3) return 1024;
     int t = (std::min(hi.b_max, 512) + 31) / 32 * 32;
     return std::max(128, t);
 }
@@ -388,7 +427,8 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         host_info(cfg, &b->hi);
         b->off = build_layout(cfg, b->hi);
         for (int e = 0; e < cfg->n_envs; ++e) {
-            if (h_gt_off[e + 1] - h_gt_off[e] != (int64_t)cfg->h_map_w[e] * cfg->h_map_h[e]) {
+            if (h_gt_off[e + 1] - h_gt_off[e] !=
+                (int64_t)cfg->h_map_w[e] * cfg->h_map_h[e] * b->hi.D[e]) {
                 delete b;
                 return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "h_gt_off does not match W*H");
             }
@@ -449,6 +489,11 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.Vw = at<int>(b, o.Vw);
         p.Vh = at<int>(b, o.Vh);
         p.R8 = at<int>(b, o.R8);
+        p.Dd = at<int>(b, o.Dd);
+        p.elev_cs = at<float2>(b, o.elev);
+        p.dims = hi.dims;
+        p.n_rings = hi.n_rings;
+        p.Pz = cfg->dims == 3 ? (int)lrintf((cfg->sensor_z_m / cfg->res_m) * 65536.0f) : 0;
         p.order = at<int>(b, o.order);
         p.map_off = at<long long>(b, o.map_off);
         p.gtb_off = at<long long>(b, o.gtb_off);
@@ -489,14 +534,23 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         const double fov = (double)cfg->fov_rad;
         const bool full_turn = fov <= 0.0 || fov >= two_pi - 1e-9;
         for (int e = 0; e < E; ++e) {
-            const int B = hi.B[e];
-            for (int k = 0; k < B; ++k) {
+            // 2-D: B beams over the field of view; 3-D: rings x azimuths over a
+            // full turn, beam b = ring * A + azimuth
+            const int A = hi.B[e] / hi.n_rings;
+            for (int k = 0; k < hi.B[e]; ++k) {
                 double a;
-                if (full_turn) a = (two_pi * (double)k) / (double)B;
-                else if (B == 1) a = 0.0;
-                else a = -0.5 * fov + ((double)k * fov) / (double)(B - 1);
+                if (hi.dims == 3) a = (two_pi * (double)(k % A)) / (double)A;
+                else if (full_turn) a = (two_pi * (double)k) / (double)A;
+                else if (A == 1) a = 0.0;
+                else a = -0.5 * fov + ((double)k * fov) / (double)(A - 1);
                 cs[(size_t)hi.ray_off[e] + k] = make_float2((float)std::cos(a), (float)std::sin(a));
             }
+        }
+        std::vector<float2> elev((size_t)hi.n_rings);
+        for (int r = 0; r < hi.n_rings; ++r) {
+            const double lo = (double)cfg->elev_min_rad, hi_el = (double)cfg->elev_max_rad;
+            const double el = hi.n_rings == 1 ? lo : lo + ((double)r * (hi_el - lo)) / (double)(hi.n_rings - 1);
+            elev[(size_t)r] = make_float2((float)std::cos(el), (float)std::sin(el));
         }
         // Entropy of a cell with log-odds l = L * scale, in 2^-40 nats, by
         // the stable form h = l * q + log1p(e^-l), q = e^-l / (1 + e^-l).
@@ -515,7 +569,8 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         const double rcell = (double)cfg->r_max_m / cfg->res_m;
         for (int e = 0; e < E; ++e)
             cost[e] = (double)std::max(hi.B[e], 1) *
-                      std::min(rcell, std::sqrt((double)hi.W[e] * hi.W[e] + (double)hi.H[e] * hi.H[e]));
+                      std::min(rcell, std::sqrt((double)hi.W[e] * hi.W[e] + (double)hi.H[e] * hi.H[e] +
+                                                (double)hi.D[e] * hi.D[e]));
         std::stable_sort(b->order.begin(), b->order.end(),
                          [&](int a, int c2) { return cost[a] > cost[c2]; });
 
@@ -530,6 +585,8 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 == cudaSuccess) e1 = h2d((void *)p.Vw, hi.Vw.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.Vh, hi.Vh.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.R8, hi.R8.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.Dd, hi.D.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess) e1 = h2d((void *)p.elev_cs, elev.data(), 8 * elev.size());
         if (e1 == cudaSuccess) e1 = h2d((void *)p.order, b->order.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.map_off, hi.map_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d((void *)p.gtb_off, hi.gtb_off.data(), 8 * (size_t)(E + 1));
@@ -545,7 +602,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.queue, 0, 8, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(at<void>(b, o.tune_actions), 0, 8 * (size_t)E, s);
         if (e1 == cudaSuccess)
-            e1 = launch_pack_gt(d_gt, at<long long>(b, o.src_off), p.W, p.H, p.gtb_off,
+            e1 = launch_pack_gt(d_gt, at<long long>(b, o.src_off), p.W, p.H, p.Dd, p.gtb_off,
                                 (unsigned *)p.gt_bits, E, s);
         if (e1 != cudaSuccess) { st = cuda_fail(b, e1, "create: upload"); break; }
         st = reset_all(b, s);
@@ -575,7 +632,10 @@ aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const floa
     p.u_in = d_u;
     p.out_reward = d_reward;
     p.out_obs = d_obs;
-    CK(launch_step2d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
+    if (b->hi.dims == 3)
+        CK(launch_step3d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
+    else
+        CK(launch_step2d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
     return ASLAM_OK;
 }
 
@@ -656,7 +716,8 @@ aslam_status aslam_capture_graph(aslam_batch *b, const float *d_actions, const f
     p.out_reward = d_reward;
     p.out_obs = d_obs;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t le = launch_step2d(p, b->grid, b->block, b->smem, s);
+    cudaError_t le = b->hi.dims == 3 ? launch_step3d(p, b->grid, b->block, b->smem, s)
+                                     : launch_step2d(p, b->grid, b->block, b->smem, s);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(s, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(b, le, "capture launch"); }
@@ -683,6 +744,10 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
     const int Sa = auto_window(b->hi, b->smem_optin);
     for (int S : {Sa, 320, 256, 224, 192, 160, 128})
         if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
+    if (b->hi.dims == 3) {
+        windows.assign(1, 0);
+        blocks.assign({256, 512, 1024});
+    }
     (void)b_max;
     const int keep_block = b->block, keep_window = b->window;
     float best_ms = 1e30f;
@@ -699,10 +764,13 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
             if (st != ASLAM_OK) break;
             Step2DParams p = b->p;
             p.actions = acts;
-            cudaError_t ce = launch_step2d(p, b->grid, b->block, b->smem, s);
+            auto launch = [&]() {
+                return b->hi.dims == 3 ? launch_step3d(p, b->grid, b->block, b->smem, s)
+                                       : launch_step2d(p, b->grid, b->block, b->smem, s);
+            };
+            cudaError_t ce = launch();
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && ce == cudaSuccess; ++r)
-                ce = launch_step2d(p, b->grid, b->block, b->smem, s);
+            for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch();
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.0f;

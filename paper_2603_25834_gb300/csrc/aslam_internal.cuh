@@ -143,11 +143,13 @@ struct Step2DParams {
     int gt_words_max;            // shared words reserved for ground-truth bits
     int win_words_max;           // shared words reserved for 8-bit counters (4 cells/word)
     int near_words_max;          // shared words reserved for the 32-bit near block
+    int dims, n_rings, Pz;       // 3-D: ring count and sensor height (Q16 voxels)
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     uint2 key;
     // per-env static description
-    const int *W, *H, *B, *Vw, *Vh, *order, *R8;
+    const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
+    const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
     const long long *map_off, *gtb_off, *ray_off, *visit_off;
     const float2 *beam_cs;
     const long long *lut;        // [2*clamp_q + 1], entropy of L in 2^-40 nats
@@ -187,10 +189,14 @@ void set_thread_error(const char *msg);
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 cudaError_t step2d_set_smem(size_t smem);
+cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
+                          cudaStream_t s);
+cudaError_t step3d_set_smem(size_t smem);
+cudaError_t step3d_occupancy(int block, size_t smem, int *ctas_per_sm);
 cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm);
 cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,
-                           const int *H, const long long *dst_words, unsigned *bits, int E,
-                           cudaStream_t s);
+                           const int *H, const int *D, const long long *dst_words, unsigned *bits,
+                           int E, cudaStream_t s);
 cudaError_t launch_init_state(const Step2DParams &p, cudaStream_t s);
 cudaError_t launch_gather_obs(const Step2DParams &p, float *obs, cudaStream_t s);
 cudaError_t launch_gather_reward(const Step2DParams &p, float *out, cudaStream_t s);

@@ -1,0 +1,129 @@
+// env_common.cuh -- per-environment parts shared by the 2-D and 3-D step
+// kernels: episode reset + action integration at the start of a step, and
+// the reward / termination / bookkeeping at its end (run by one thread).
+#pragma once
+
+#include "aslam_internal.cuh"
+
+namespace aslam {
+
+struct EnvStart {
+    float x, y, th, u_prev;
+    int t, gstep, reset;
+    long long Hq;
+};
+
+// Reset a done env to its next spawn pose, then integrate the action with
+// the Euler unicycle (pre-step heading, heading wrapped to [-pi, pi)).
+__device__ __forceinline__ EnvStart begin_env(const Step2DParams &p, int e, long long ncell) {
+    EnvStart s;
+    s.reset = p.done[e] != 0;
+    if (s.reset) {
+        const int ep = p.ep[e] + 1;
+        p.ep[e] = ep;
+        const float *sp = p.spawn + ((long long)e * p.n_spawn + (ep % p.n_spawn)) * 3;
+        s.x = sp[0];
+        s.y = sp[1];
+        s.th = sp[2];
+        s.t = 0;
+        s.u_prev = 0.0f;
+        s.Hq = ncell * p.lut[p.clamp_q];
+    } else {
+        s.x = p.x[e];
+        s.y = p.y[e];
+        s.th = p.th[e];
+        s.t = p.t[e];
+        s.u_prev = p.u_prev[e];
+        s.Hq = p.Hq[e];
+    }
+    s.t += 1;
+    const float pi_f = (float)3.14159265358979323846;
+    const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
+    const float v = fminf(fmaxf(p.actions[2 * e], 0.0f), p.v_max);
+    const float w = fminf(fmaxf(p.actions[2 * e + 1], -p.w_max), p.w_max);
+    float s0, c0;
+    det_sincos(s.th, s0, c0);
+    s.x = fadd(s.x, fmul(fmul(v, c0), p.dt));
+    s.y = fadd(s.y, fmul(fmul(v, s0), p.dt));
+    float th = fadd(s.th, fmul(w, p.dt));
+    if (th >= pi_f) th = fsub(th, two_pi_f);
+    if (th < -pi_f) th = fadd(th, two_pi_f);
+    s.th = th;
+    p.x[e] = s.x;
+    p.y[e] = s.y;
+    p.th[e] = s.th;
+    p.t[e] = s.t;
+    s.gstep = p.g[e];
+    return s;
+}
+
+// Reductions of one env's step.
+struct EnvTotals {
+    long long dHq, ray_cells, gt_cells;
+    float dmin_meas, dmin_true;
+};
+
+// Entropy gain, visit grid (Eq. 8-9), reward terms (Eq. 7-17), termination
+// and the per-env outputs.  One thread.
+__device__ __forceinline__ void finish_env(const Step2DParams &p, int e, int W, int H,
+                                           const EnvStart &s, int col_cell, const EnvTotals &r) {
+    const long long Hq = s.Hq + r.dHq;
+    p.Hq[e] = Hq;
+    const double dH = -(double)r.dHq / kLutScale;    // H_{t-1} - H_t (nats)
+    const int col = col_cell || (r.dmin_true < p.d_crash);
+    const int Vw = p.Vw[e], Vh = p.Vh[e];
+    const float vx0 = fmul(-0.5f, fmul((float)W, p.res));
+    const float vy0 = fmul(-0.5f, fmul((float)H, p.res));
+    int vi = (int)floorf(fdiv(fsub(s.x, vx0), p.visit_cell));
+    int vj = (int)floorf(fdiv(fsub(s.y, vy0), p.visit_cell));
+    vi = min(max(vi, 0), Vw - 1);
+    vj = min(max(vj, 0), Vh - 1);
+    int *vc = p.visit + p.visit_off[e] + (long long)vj * Vw + vi;
+    const int last = *vc;
+    double dcells = 1.0;
+    if (last >= 0) dcells = fmin(fmax(0.5 * (double)(s.t - last) / (double)p.t_episode, 0.0), 1.0);
+    *vc = s.t;
+    const double Up = (double)s.u_prev;
+    const double U = p.u_in ? (double)p.u_in[e] : 0.0;
+    double cg = fmin(fmax((p.u_hi - Up) / p.u_hi, 0.0), 1.0);
+    cg = cg * cg;
+    const double iota = fmin(fmax(fmax(Up - U, 0.0) / p.kappa, 0.0), 1.0);
+    const double I = cg + (1.0 - cg) * iota;
+    const double r_explore = p.lam_explore * dcells * I;
+    const double eU = exp(Up);
+    const double r_abs = p.lam_abs * eU * Up;
+    const double r_delta = p.lam_delta * eU * (Up - U);
+    const double alpha = fmin(fmax(((double)r.dmin_meas - (double)p.d_crash) /
+                                       ((double)p.d_full - (double)p.d_crash), 0.0), 1.0);
+    const double r_explore_s = r_explore * alpha;
+    const double r_delta_s = (Up - U > 0.0) ? r_delta * alpha : r_delta;
+    const double R = col ? -p.lam_col : (r_explore_s - r_abs + r_delta_s);
+    float *tm = p.terms + (long long)e * kTerms;
+    tm[0] = (float)dH;
+    tm[1] = (float)dcells;
+    tm[2] = (float)I;
+    tm[3] = (float)alpha;
+    tm[4] = (float)r_explore_s;
+    tm[5] = (float)r_abs;
+    tm[6] = (float)r_delta_s;
+    tm[7] = (float)R;
+    tm[8] = (float)col;
+    tm[9] = r.dmin_meas;
+    tm[10] = r.dmin_true;
+    tm[11] = (float)((double)Hq / kLutScale);
+    const float rew = p.reward_mode == ASLAM_REWARD_COMPOSITE ? (float)R : (float)dH;
+    p.reward[e] = rew;
+    if (p.out_reward) p.out_reward[e] = rew;
+    p.done[e] = (col || s.t >= p.t_episode) ? 1 : 0;
+    p.u_prev[e] = (float)U;
+    p.g[e] = s.gstep + 1;
+    p.ray_cells[e] = r.ray_cells;
+    p.gt_cells[e] = r.gt_cells;
+    if (p.out_obs) {
+        float *o = p.out_obs + (long long)e * (p.b_max + 2);
+        o[p.b_max] = s.th;
+        o[p.b_max + 1] = (float)U;
+    }
+}
+
+}  // namespace aslam

@@ -31,6 +31,7 @@
 // the robot there and counts the rest with fire-and-forget global atomics
 // (32-bit counters plus a bitmap of touched 8-cell chunks).
 #include "aslam_internal.cuh"
+#include "env_common.cuh"
 
 namespace aslam {
 namespace {
@@ -39,9 +40,9 @@ struct EnvShared {
     int e, W, H, B, reset, partial, R8, NB;
     int Px, Py, ri, rj, col_cell;
     int wx0, wy0, SW, SH;
-    int t, gstep;
-    float x, y, th, c, s, u_prev;
-    long long map_off, gtb_off, ray_off, Hq;
+    float c, s;
+    long long map_off, gtb_off, ray_off;
+    EnvStart start;
 };
 
 __device__ __forceinline__ unsigned gt_bit(const unsigned *bits, int k) {
@@ -78,53 +79,10 @@ __device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvSh
     sh.map_off = p.map_off[e];
     sh.gtb_off = p.gtb_off[e];
     sh.ray_off = p.ray_off[e];
-    float x, y, th, up;
-    int t;
-    long long Hq;
-    int reset = p.done[e] != 0;
-    if (reset) {
-        int ep = p.ep[e] + 1;
-        p.ep[e] = ep;
-        const float *sp = p.spawn + ((long long)e * p.n_spawn + (ep % p.n_spawn)) * 3;
-        x = sp[0];
-        y = sp[1];
-        th = sp[2];
-        t = 0;
-        up = 0.0f;
-        Hq = (long long)W * H * p.lut[p.clamp_q];
-    } else {
-        x = p.x[e];
-        y = p.y[e];
-        th = p.th[e];
-        t = p.t[e];
-        up = p.u_prev[e];
-        Hq = p.Hq[e];
-    }
-    sh.reset = reset;
-    t += 1;
-    // Euler unicycle with the pre-step heading; heading wrapped to [-pi, pi).
-    const float pi_f = (float)3.14159265358979323846;
-    const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
-    float v = fminf(fmaxf(p.actions[2 * e], 0.0f), p.v_max);
-    float w = fminf(fmaxf(p.actions[2 * e + 1], -p.w_max), p.w_max);
-    float s0, c0;
-    det_sincos(th, s0, c0);
-    x = fadd(x, fmul(fmul(v, c0), p.dt));
-    y = fadd(y, fmul(fmul(v, s0), p.dt));
-    th = fadd(th, fmul(w, p.dt));
-    if (th >= pi_f) th = fsub(th, two_pi_f);
-    if (th < -pi_f) th = fadd(th, two_pi_f);
-    p.x[e] = x;
-    p.y[e] = y;
-    p.th[e] = th;
-    p.t[e] = t;
-    sh.x = x;
-    sh.y = y;
-    sh.th = th;
-    sh.t = t;
-    sh.u_prev = up;
-    sh.Hq = Hq;
-    sh.gstep = p.g[e];
+    const EnvStart st = begin_env(p, e, (long long)W * H);
+    sh.start = st;
+    sh.reset = st.reset;
+    const float x = st.x, y = st.y, th = st.th;
     int Px = q16_of(x, p.res), Py = q16_of(y, p.res);
     sh.Px = Px;
     sh.Py = Py;
@@ -251,7 +209,7 @@ __device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShare
     }
     float z = z_true;
     if (hit) {
-        const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.gstep, (unsigned)b);
+        const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.start.gstep, (unsigned)b);
         z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, gz)), 0.0f), p.r_max);
     }
     const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
@@ -505,75 +463,20 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
         }
         __syncthreads();
         if (tid == 0) {
-            long long dHq = 0;
-            long long RC = 0, GC = 0;
-            float dm = p.r_max, dtr = p.r_max;
+            EnvTotals r;
+            r.dHq = 0;
+            r.ray_cells = 0;
+            r.gt_cells = 0;
+            r.dmin_meas = p.r_max;
+            r.dmin_true = p.r_max;
             for (int w = 0; w < nwarps; ++w) {
-                dHq += r_dh[w];
-                RC += r_rc[w];
-                GC += r_gc[w];
-                dm = fminf(dm, r_dm[w]);
-                dtr = fminf(dtr, r_dt[w]);
+                r.dHq += r_dh[w];
+                r.ray_cells += r_rc[w];
+                r.gt_cells += r_gc[w];
+                r.dmin_meas = fminf(r.dmin_meas, r_dm[w]);
+                r.dmin_true = fminf(r.dmin_true, r_dt[w]);
             }
-            const long long Hq = sh.Hq + dHq;
-            p.Hq[e] = Hq;
-            const double dH = -(double)dHq / kLutScale;    // H_{t-1} - H_t (nats)
-            const int col = sh.col_cell || (dtr < p.d_crash);
-            // Visit grid at the ground-truth position (Eq. 8-9).
-            const int Vw = p.Vw[e], Vh = p.Vh[e];
-            const float vx0 = fmul(-0.5f, fmul((float)W, p.res));
-            const float vy0 = fmul(-0.5f, fmul((float)H, p.res));
-            int vi = (int)floorf(fdiv(fsub(sh.x, vx0), p.visit_cell));
-            int vj = (int)floorf(fdiv(fsub(sh.y, vy0), p.visit_cell));
-            vi = min(max(vi, 0), Vw - 1);
-            vj = min(max(vj, 0), Vh - 1);
-            int *vc = p.visit + p.visit_off[e] + (long long)vj * Vw + vi;
-            const int last = *vc;
-            double dcells = 1.0;
-            if (last >= 0) dcells = fmin(fmax(0.5 * (double)(sh.t - last) / (double)p.t_episode, 0.0), 1.0);
-            *vc = sh.t;
-            // Reward terms, Eq. 7-17.
-            const double Up = (double)sh.u_prev;
-            const double U = p.u_in ? (double)p.u_in[e] : 0.0;
-            double cg = fmin(fmax((p.u_hi - Up) / p.u_hi, 0.0), 1.0);
-            cg = cg * cg;
-            const double iota = fmin(fmax(fmax(Up - U, 0.0) / p.kappa, 0.0), 1.0);
-            const double I = cg + (1.0 - cg) * iota;
-            const double r_explore = p.lam_explore * dcells * I;
-            const double eU = exp(Up);
-            const double r_abs = p.lam_abs * eU * Up;
-            const double r_delta = p.lam_delta * eU * (Up - U);
-            const double alpha = fmin(fmax(((double)dm - (double)p.d_crash) /
-                                               ((double)p.d_full - (double)p.d_crash), 0.0), 1.0);
-            const double r_explore_s = r_explore * alpha;
-            const double r_delta_s = (Up - U > 0.0) ? r_delta * alpha : r_delta;
-            const double R = col ? -p.lam_col : (r_explore_s - r_abs + r_delta_s);
-            float *tm = p.terms + (long long)e * kTerms;
-            tm[0] = (float)dH;
-            tm[1] = (float)dcells;
-            tm[2] = (float)I;
-            tm[3] = (float)alpha;
-            tm[4] = (float)r_explore_s;
-            tm[5] = (float)r_abs;
-            tm[6] = (float)r_delta_s;
-            tm[7] = (float)R;
-            tm[8] = (float)col;
-            tm[9] = dm;
-            tm[10] = dtr;
-            tm[11] = (float)((double)Hq / kLutScale);
-            const float rew = p.reward_mode == ASLAM_REWARD_COMPOSITE ? (float)R : (float)dH;
-            p.reward[e] = rew;
-            if (p.out_reward) p.out_reward[e] = rew;
-            p.done[e] = (col || sh.t >= p.t_episode) ? 1 : 0;
-            p.u_prev[e] = (float)U;
-            p.g[e] = sh.gstep + 1;
-            p.ray_cells[e] = RC;
-            p.gt_cells[e] = GC;
-            if (p.out_obs) {
-                float *o = p.out_obs + (long long)e * (p.b_max + 2);
-                o[p.b_max] = sh.th;
-                o[p.b_max + 1] = (float)U;
-            }
+            finish_env(p, e, W, H, sh.start, sh.col_cell, r);
         }
         if (p.out_obs) {
             float *o = p.out_obs + (long long)e * (p.b_max + 2);
@@ -583,9 +486,10 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
 }
 
 __global__ void pack_gt_kernel(const uint8_t *gt, const long long *src_off, const int *W,
-                               const int *H, const long long *dst_words, unsigned *bits) {
+                               const int *H, const int *D, const long long *dst_words,
+                               unsigned *bits) {
     const int e = blockIdx.x;
-    const long long n = (long long)W[e] * H[e];
+    const long long n = (long long)W[e] * H[e] * D[e];
     const long long words = (n + 31) >> 5;
     const long long padded = (words + 3) & ~3LL;
     const uint8_t *g = gt + src_off[e];
@@ -611,7 +515,7 @@ __global__ void init_state_kernel(const Step2DParams p) {
         p.g[e] = 0;
         p.ep[e] = 0;
         p.done[e] = 0;
-        p.Hq[e] = (long long)p.W[e] * p.H[e] * p.lut[p.clamp_q];
+        p.Hq[e] = (long long)p.W[e] * p.H[e] * p.Dd[e] * p.lut[p.clamp_q];
         p.reward[e] = 0.0f;
     }
 }
@@ -669,9 +573,9 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
 }
 
 cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,
-                           const int *H, const long long *dst_words, unsigned *bits, int E,
-                           cudaStream_t s) {
-    pack_gt_kernel<<<E, 256, 0, s>>>(gt, src_off, W, H, dst_words, bits);
+                           const int *H, const int *D, const long long *dst_words, unsigned *bits,
+                           int E, cudaStream_t s) {
+    pack_gt_kernel<<<E, 256, 0, s>>>(gt, src_off, W, H, D, dst_words, bits);
     return cudaGetLastError();
 }
 

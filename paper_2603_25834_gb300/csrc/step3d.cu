@@ -1,0 +1,380 @@
+// step3d.cu -- the batched 3-D (voxel) environment step on sm_103a.
+//
+// Same step as the 2-D kernel (action integration, sensing, noise, per-scan
+// sum-then-clamp log-odds update, entropy gain, Eq. 7-17 reward, Eq. 3
+// observation), for a multi-ring LiDAR at sensor height z_s in a W x H x D
+// voxel world.  One persistent CTA per environment:
+//   * the env's ground truth (1 bit per voxel, 64 KiB for 128x128x32) is
+//     staged in shared memory;
+//   * one thread per beam walks the voxels with an exact fixed-point 3-D
+//     traversal: three 64-bit error terms e_xy, e_xz, e_yz compare the next
+//     face crossings of each axis pair; ties go Z first, then Y, then X;
+//   * counts go to global 32-bit (hits << 16 | misses) counters plus a
+//     bitmap of touched 8-voxel chunks.  The belief walk runs warp-
+//     synchronously: the 32 lanes of a warp are 32 adjacent azimuths of one
+//     ring, which cross the same voxels near the sensor, so lanes in the same
+//     voxel are merged (__match_any_sync) into one atomic;
+//   * the CTA then applies the touched chunks and sums the entropy change.
+#include "aslam_internal.cuh"
+#include "env_common.cuh"
+
+namespace aslam {
+namespace {
+
+struct Env3 {
+    int e, W, H, Dd, B, A;
+    int Px, Py, ri, rj, rk, col_cell;
+    float c, s;
+    long long map_off, gtb_off, ray_off, ncell;
+    EnvStart start;
+};
+
+__device__ __forceinline__ unsigned gt_bit3(const unsigned *bits, long long k) {
+    return (bits[k >> 5] >> (k & 31)) & 1u;
+}
+
+struct Walk3 {
+    int i, j, k;             // voxel
+    long long flat;
+    long long exy, exz, eyz; // next-crossing comparisons of axis pairs
+    int last;                // axis of the last step (0 x, 1 y, 2 z)
+};
+
+struct Ray3 {
+    int sx, sy, sz;
+    long long ax, ay, az;    // |D| per axis (Q30)
+    long long Ax, Ay, Az;    // |D| * 2^16
+    long long nx0, ny0, nz0;
+    long long stride_y, stride_z;
+};
+
+// One traversal step; returns false when it leaves the volume.
+__device__ __forceinline__ bool step3(const Ray3 &r, const Env3 &sh, Walk3 &w) {
+    int a;
+    if (w.exy < 0) a = (w.exz < 0) ? 0 : 2;
+    else a = (w.eyz < 0) ? 1 : 2;
+    w.last = a;
+    if (a == 0) {
+        w.i += r.sx;
+        w.flat += r.sx;
+        w.exy += r.Ay;
+        w.exz += r.Az;
+        return (unsigned)w.i < (unsigned)sh.W;
+    }
+    if (a == 1) {
+        w.j += r.sy;
+        w.flat += r.sy * r.stride_y;
+        w.exy -= r.Ax;
+        w.eyz += r.Az;
+        return (unsigned)w.j < (unsigned)sh.H;
+    }
+    w.k += r.sz;
+    w.flat += r.sz * r.stride_z;
+    w.exz -= r.Ax;
+    w.eyz -= r.Ay;
+    return (unsigned)w.k < (unsigned)sh.Dd;
+}
+
+__device__ __forceinline__ void count_plain(const Step2DParams &p, const Env3 &sh, long long k,
+                                            unsigned inc) {
+    atomicAdd(&p.far_cnt[sh.map_off + k], inc);
+    atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
+}
+
+__device__ __forceinline__ long long apply_cell3(const Step2DParams &p, short &L, unsigned h,
+                                                 unsigned m) {
+    const int l0 = L;
+    int l1 = l0 + (int)h * p.hit_q + (int)m * p.miss_q;
+    l1 = min(max(l1, -p.clamp_q), p.clamp_q);
+    L = (short)l1;
+    return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
+}
+
+__global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *s_gt = smem;
+    __shared__ Env3 sh;
+    __shared__ long long r_dh[32], r_rc[32], r_gc[32];
+    __shared__ float r_dm[32], r_dt[32];
+    __shared__ int s_next;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
+
+    if (tid == 0) s_next = (int)atomicAdd(p.queue, 1u);
+    for (;;) {
+        __syncthreads();
+        const int item = s_next;
+        __syncthreads();
+        if (item >= p.E) {
+            if (tid == 0) {
+                __threadfence();
+                if (atomicAdd(p.queue + 1, 1u) == gridDim.x - 1) {
+                    p.queue[0] = 0u;
+                    p.queue[1] = 0u;
+                    __threadfence();
+                }
+            }
+            break;
+        }
+        if (tid == 0) {
+            const int e = p.order[item];
+            const int W = p.W[e], H = p.H[e], Dd = p.Dd[e];
+            sh.e = e;
+            sh.W = W;
+            sh.H = H;
+            sh.Dd = Dd;
+            sh.B = p.B[e];
+            sh.A = sh.B / p.n_rings;
+            sh.map_off = p.map_off[e];
+            sh.gtb_off = p.gtb_off[e];
+            sh.ray_off = p.ray_off[e];
+            sh.ncell = (long long)W * H * Dd;
+            sh.start = begin_env(p, e, sh.ncell);
+            sh.Px = q16_of(sh.start.x, p.res);
+            sh.Py = q16_of(sh.start.y, p.res);
+            sh.ri = sh.Px >> 16;
+            sh.rj = sh.Py >> 16;
+            sh.rk = p.Pz >> 16;
+            const bool inside = (unsigned)sh.ri < (unsigned)W && (unsigned)sh.rj < (unsigned)H &&
+                                (unsigned)sh.rk < (unsigned)Dd;
+            sh.col_cell = !inside ||
+                          gt_bit3(p.gt_bits + sh.gtb_off, ((long long)sh.rk * H + sh.rj) * W + sh.ri);
+            det_sincos(sh.start.th, sh.s, sh.c);
+            s_next = (int)atomicAdd(p.queue, 1u);
+        }
+        __syncthreads();
+        const int e = sh.e;
+        const long long ncell = sh.ncell;
+        // ---- reset, stage ground truth ----------------------------------------
+        if (sh.start.reset) {
+            int4 *bz = reinterpret_cast<int4 *>(p.belief + sh.map_off);
+            for (long long q = tid; q < (ncell + 7) >> 3; q += nt) bz[q] = make_int4(0, 0, 0, 0);
+            const long long vo = p.visit_off[e], vn = p.visit_off[e + 1] - vo;
+            for (long long q = tid; q < vn; q += nt) p.visit[vo + q] = -1;
+        }
+        {
+            const long long words = (ncell + 31) >> 5;
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + sh.gtb_off);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
+            for (long long q = tid; q < (words + 3) >> 2; q += nt) dst[q] = __ldg(&src[q]);
+            if (debug)
+                for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
+        }
+        __syncthreads();
+
+        // ---- beams -------------------------------------------------------------
+        long long rc = 0, gc = 0;
+        float dmin_m = p.r_max, dmin_t = p.r_max;
+        const int W = sh.W, H = sh.H;
+        const int rounds = (sh.B + nt - 1) / nt;
+        for (int q = 0; q < rounds; ++q) {
+            // every lane runs the same number of rounds: the warp-synchronous
+            // belief walk below needs whole warps
+            const int b = tid + q * nt;
+            const bool valid = b < sh.B;
+            Ray3 r;
+            Walk3 w0;
+            bool hit = false, in0 = false;
+            float z_true = p.r_max, z = p.r_max;
+            int Ku = -1;
+            if (valid) {
+                const int ring = b / sh.A;
+                const float2 cs = p.beam_cs[sh.ray_off + b];
+                const float2 el = p.elev_cs[ring];
+                const float hx = fsub(fmul(sh.c, cs.x), fmul(sh.s, cs.y));
+                const float hy = fadd(fmul(sh.s, cs.x), fmul(sh.c, cs.y));
+                const int Dx = __float2int_rn(fmul(fmul(el.x, hx), 1073741824.0f));
+                const int Dy = __float2int_rn(fmul(fmul(el.x, hy), 1073741824.0f));
+                const int Dz = __float2int_rn(fmul(el.y, 1073741824.0f));
+                const int i0 = sh.ri, j0 = sh.rj, k0 = sh.rk;
+                in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H &&
+                      (unsigned)k0 < (unsigned)sh.Dd;
+                r.sx = (Dx > 0) - (Dx < 0);
+                r.sy = (Dy > 0) - (Dy < 0);
+                r.sz = (Dz > 0) - (Dz < 0);
+                r.ax = Dx < 0 ? -(long long)Dx : Dx;
+                r.ay = Dy < 0 ? -(long long)Dy : Dy;
+                r.az = Dz < 0 ? -(long long)Dz : Dz;
+                r.Ax = r.ax << 16;
+                r.Ay = r.ay << 16;
+                r.Az = r.az << 16;
+                r.nx0 = Dx > 0 ? ((long long)(i0 + 1) << 16) - sh.Px
+                               : (Dx < 0 ? (long long)sh.Px - ((long long)i0 << 16) : 65536);
+                r.ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - sh.Py
+                               : (Dy < 0 ? (long long)sh.Py - ((long long)j0 << 16) : 65536);
+                r.nz0 = Dz > 0 ? ((long long)(k0 + 1) << 16) - p.Pz
+                               : (Dz < 0 ? (long long)p.Pz - ((long long)k0 << 16) : 65536);
+                r.stride_y = W;
+                r.stride_z = (long long)W * H;
+                w0.i = i0;
+                w0.j = j0;
+                w0.k = k0;
+                w0.flat = ((long long)k0 * H + j0) * W + i0;
+                w0.exy = r.nx0 * r.ay - r.ny0 * r.ax;
+                w0.exz = r.nx0 * r.az - r.nz0 * r.ax;
+                w0.eyz = r.ny0 * r.az - r.nz0 * r.ay;
+                w0.last = -1;
+                if (in0) {
+                    // ground truth up to the first occupied voxel
+                    Walk3 w = w0;
+                    int cells = 1;
+                    if (gt_bit3(s_gt, w.flat)) {
+                        hit = true;
+                        z_true = 0.0f;
+                    } else {
+                        const int Ks = crossings_le(r.nx0, r.ax, p.Tmax) +
+                                       crossings_le(r.ny0, r.ay, p.Tmax) +
+                                       crossings_le(r.nz0, r.az, p.Tmax);
+                        for (int s = 0; s < Ks; ++s) {
+                            if (!step3(r, sh, w)) break;
+                            ++cells;
+                            if (gt_bit3(s_gt, w.flat)) {
+                                hit = true;
+                                break;
+                            }
+                        }
+                        if (hit) {
+                            long long n, ad;
+                            if (w.last == 0) { n = r.nx0 + ((long long)(abs(w.i - i0) - 1) << 16); ad = r.ax; }
+                            else if (w.last == 1) { n = r.ny0 + ((long long)(abs(w.j - j0) - 1) << 16); ad = r.ay; }
+                            else { n = r.nz0 + ((long long)(abs(w.k - k0) - 1) << 16); ad = r.az; }
+                            z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+                        }
+                    }
+                    gc += cells;
+                    z = z_true;
+                    if (hit) {
+                        const float g = det_gauss(p.key, (unsigned)e, (unsigned)sh.start.gstep, (unsigned)b);
+                        z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
+                    }
+                    const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
+                    Ku = crossings_le(r.nx0, r.ax, Tz) + crossings_le(r.ny0, r.ay, Tz) +
+                         crossings_le(r.nz0, r.az, Tz);
+                }
+                const long long ro = sh.ray_off + b;
+                p.z[ro] = z;
+                if (debug) {
+                    p.z_true[ro] = z_true;
+                    p.hit[ro] = hit ? 1 : 0;
+                }
+                if (p.out_obs) p.out_obs[(long long)e * (p.b_max + 2) + b] = z;
+                dmin_m = fminf(dmin_m, z);
+                dmin_t = fminf(dmin_t, z_true);
+            }
+            // belief walk, warp-synchronous: lanes in the same voxel share one atomic
+            bool active = valid && in0;
+            Walk3 w = w0;
+            int s = 0;
+            for (;;) {
+                const unsigned act = __ballot_sync(0xffffffffu, active);
+                if (!act) break;
+                if (active) {
+                    const bool last = s == Ku;
+                    const bool is_hit = last && hit;
+                    const unsigned peers = __match_any_sync(act, w.flat);
+                    const unsigned hits = __ballot_sync(act, is_hit) & peers;
+                    if (lane == __ffs(peers) - 1) {
+                        const unsigned nh = __popc(hits), nm = __popc(peers) - nh;
+                        count_plain(p, sh, w.flat, (nh << 16) | nm);
+                    }
+                    ++rc;
+                    ++s;
+                    if (last) active = false;
+                    else if (!step3(r, sh, w)) active = false;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- apply the touched chunks ------------------------------------------
+        long long dh = 0;
+        {
+            short *Lenv = p.belief + sh.map_off;
+            unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
+            const long long nbw = (ncell + 255) >> 8;
+            unsigned *bits = p.far_bits + (sh.map_off >> 8);
+            for (long long wq = tid; wq < nbw; wq += nt) {
+                unsigned m = __ldcg(&bits[wq]);
+                if (!m) continue;
+                bits[wq] = 0u;
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    const long long k = wq * 256 + bit * 8;
+                    uint4 *cp = reinterpret_cast<uint4 *>(p.far_cnt + sh.map_off + k);
+                    const uint4 c0 = __ldcg(cp), c1 = __ldcg(cp + 1);
+                    cp[0] = make_uint4(0u, 0u, 0u, 0u);
+                    cp[1] = make_uint4(0u, 0u, 0u, 0u);
+                    int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
+                    short *L = reinterpret_cast<short *>(&lv);
+                    const unsigned c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (c[q]) dh += apply_cell3(p, L[q], c[q] >> 16, c[q] & 0xffffu);
+                        if (dbg) dbg[k + q] = c[q];
+                    }
+                    *reinterpret_cast<int4 *>(Lenv + k) = lv;
+                }
+            }
+        }
+
+        // ---- reductions, reward, observation ----------------------------------
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            dh += __shfl_down_sync(0xffffffffu, dh, o);
+            rc += __shfl_down_sync(0xffffffffu, rc, o);
+            gc += __shfl_down_sync(0xffffffffu, gc, o);
+            dmin_m = fminf(dmin_m, __shfl_down_sync(0xffffffffu, dmin_m, o));
+            dmin_t = fminf(dmin_t, __shfl_down_sync(0xffffffffu, dmin_t, o));
+        }
+        if (lane == 0) {
+            r_dh[warp] = dh;
+            r_rc[warp] = rc;
+            r_gc[warp] = gc;
+            r_dm[warp] = dmin_m;
+            r_dt[warp] = dmin_t;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            EnvTotals t;
+            t.dHq = 0;
+            t.ray_cells = 0;
+            t.gt_cells = 0;
+            t.dmin_meas = p.r_max;
+            t.dmin_true = p.r_max;
+            for (int q = 0; q < nwarps; ++q) {
+                t.dHq += r_dh[q];
+                t.ray_cells += r_rc[q];
+                t.gt_cells += r_gc[q];
+                t.dmin_meas = fminf(t.dmin_meas, r_dm[q]);
+                t.dmin_true = fminf(t.dmin_true, r_dt[q]);
+            }
+            finish_env(p, e, W, H, sh.start, sh.col_cell, t);
+        }
+        if (p.out_obs) {
+            float *o = p.out_obs + (long long)e * (p.b_max + 2);
+            for (int b = sh.B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t step3d_set_smem(size_t smem) {
+    return cudaFuncSetAttribute(step3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t step3d_occupancy(int block, size_t smem, int *ctas_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step3d_kernel, block, smem);
+}
+
+cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
+                          cudaStream_t s) {
+    step3d_kernel<<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace aslam

@@ -263,10 +263,16 @@ def make_world_3d(W, H, D, res, rng, n_box=(8, 16), box_side=(0.5, 3.0), box_h=(
 
 
 def voxel_batch(E=512, W=128, H=128, D=32, res=0.1, n_az=512, seed=BASE_SEED, K=8, clearance=0.3):
-    """E voxel worlds with floor, boxes and pillars; spawns on free columns."""
+    """E voxel worlds with floor, boxes and pillars (counts scaled to the floor
+    area of a 128 x 128 x 0.1 m world); spawns on free columns."""
     grids, spawns = [], []
+    scale = (W * H * res * res) / (128 * 128 * 0.01)
+    n_box = (int(round(8 * scale)), max(int(round(16 * scale)), 1))
+    n_pillar = (int(round(4 * scale)), max(int(round(10 * scale)), 1))
+    side = (0.5, max(0.6, min(3.0, 0.4 * min(W, H) * res)))
     for e in range(E):
-        occ = make_world_3d(W, H, D, res, np.random.default_rng(seed + e))
+        occ = make_world_3d(W, H, D, res, np.random.default_rng(seed + e), n_box=n_box,
+                            box_side=side, n_pillar=n_pillar)
         grids.append(occ)
         column = World2D(W, H, res, occ[1:].max(axis=0))
         spawns.append(spawn_poses_2d(column, K, np.random.default_rng(seed + 10_000_000 + e),
