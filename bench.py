@@ -250,7 +250,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "uneven", "diff"])
+    ap.add_argument("--workload", default="paper_scale",
+                    choices=["paper_scale", "uneven", "diff", "3d"])
     ap.add_argument("--envs", type=int, default=750)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,7 +279,17 @@ def main():
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
 
-    if args.workload == "uneven":
+    cfg_kw = dict(r_max_m=12.0, noise_sigma_m=0.01)
+    if args.workload == "3d":
+        E = args.envs if args.envs != 750 else 512
+        inp = synth.voxel_batch(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+        cfg_kw = dict(r_max_m=20.0, noise_sigma_m=0.01, n_rings=16)
+        workload = dict(workload="3d: %d envs x 128x128x32 voxels @0.1 m (floor, boxes, pillars), "
+                                 "16 rings x 512 azimuths over +-15 deg at 0.5 m, 20 m, "
+                                 "sigma 0.01 m, CUDA graph" % E,
+                        envs=E, res_m=0.1, r_max_m=20.0, noise_sigma_m=0.01,
+                        reward="composite Eq. 7-17", l2="flushed (256 MiB write) between timed steps")
+    elif args.workload == "uneven":
         E = args.envs if args.envs != 750 else 4096
         inp = synth.uneven(E=E, seed=synth.BASE_SEED + 100_000 * rank)
         workload = dict(workload="uneven: %d envs, sides {128,256,384,512} @0.05 m, beams "
@@ -291,9 +302,8 @@ def main():
         E = args.envs
         inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
         workload = dict(WORKLOAD, envs=E)
-    batch = aslam.Batch2D(inp, device=dev, r_max_m=12.0, noise_sigma_m=0.01,
-                          reward_mode=aslam.REWARD_COMPOSITE, threads_per_cta=args.threads,
-                          window_cells=args.window)
+    batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE,
+                          threads_per_cta=args.threads, window_cells=args.window, **cfg_kw)
     tuned = None
     if not args.no_autotune and not args.threads and not args.window:
         tuned = batch.autotune()
@@ -402,7 +412,7 @@ def main():
     # Algorithmic bytes of one launch: every updated cell read+written as
     # int16 (4 B), every ground-truth cell read (1 B), ranges and observation
     # written, pose/action/reward (24 B per env).
-    Bsum = int(inp.n_beams.sum())
+    Bsum = int(batch.ray_off[-1])
     alg_bytes = (ray_cells * 4 + gt_cells * 1) / K + Bsum * 4 + E * (batch.b_max + 2) * 4 + E * 24
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
@@ -430,7 +440,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)",
-                     "bytes_per_launch": alg_bytes, "kernel": "step2d_kernel"},
+                     "bytes_per_launch": alg_bytes,
+                     "kernel": "step3d_kernel" if args.workload == "3d" else "step2d_kernel"},
         "cpu_baseline": cpu,
         "e2e": {"value": world * E * K2 / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
