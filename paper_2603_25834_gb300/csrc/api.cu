@@ -36,7 +36,7 @@ struct Offsets {
     size_t x, y, th, u_prev, t, g, ep, done, Hq;
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
-    size_t far_cnt, far_bits, queue, err, tune_actions;
+    size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, err, tune_actions;
     size_t total;
 };
 
@@ -96,15 +96,15 @@ bool validate(const aslam_config *c, std::string *msg) {
             return fail("map side out of [1, ASLAM_MAX_MAP_SIDE]");
         if (c->h_n_beams[e] < 0 || c->h_n_beams[e] > ASLAM_MAX_BEAMS)
             return fail("n_beams out of [0, ASLAM_MAX_BEAMS]");
-        if (c->dims == 2 && (long long)c->h_map_w[e] * c->h_map_h[e] > (1LL << 26))
-            return fail("2-D map larger than 2^26 cells");
+        if (c->dims == 2 && (long long)c->h_map_w[e] * c->h_map_h[e] > 1600LL * 1024)
+            return fail("2-D map larger than 1638400 cells");
     }
     if (!(c->res_m > 0.0f) || !(c->r_max_m > 0.0f)) return fail("res_m and r_max_m must be > 0");
     if ((double)c->r_max_m / c->res_m > 16384.0) return fail("r_max_m / res_m must be <= 16384 cells");
     if (!(c->dt_s >= 0.0f) || !(c->v_max >= 0.0f) || !(c->w_max >= 0.0f))
         return fail("dt_s, v_max, w_max must be >= 0");
     if (!(c->noise_sigma_m >= 0.0f)) return fail("noise_sigma_m must be >= 0");
-    if (c->l_clamp_q < 1 || c->l_clamp_q > 32767) return fail("l_clamp_q out of [1, 32767]");
+    if (c->l_clamp_q < 1 || c->l_clamp_q > 8192) return fail("l_clamp_q out of [1, 8192]");
     if (std::abs(c->l_hit_q) > 32767 || std::abs(c->l_miss_q) > 32767)
         return fail("|l_hit_q|, |l_miss_q| must be <= 32767");
     if (c->t_episode < 1) return fail("t_episode must be >= 1");
@@ -115,8 +115,8 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (c->reward_mode != ASLAM_REWARD_ENTROPY && c->reward_mode != ASLAM_REWARD_COMPOSITE)
         return fail("unknown reward_mode");
     if (c->threads_per_cta != 0 &&
-        (c->threads_per_cta < 32 || c->threads_per_cta > 1024 || c->threads_per_cta % 32))
-        return fail("threads_per_cta must be 0 or a multiple of 32 in [32, 1024]");
+        (c->threads_per_cta < 128 || c->threads_per_cta > 1024 || c->threads_per_cta % 32))
+        return fail("threads_per_cta must be 0 or a multiple of 32 in [128, 1024]");
     if (c->window_cells != 0 && (c->window_cells < 64 || c->window_cells % 8))
         return fail("window_cells must be 0 or a multiple of 8 >= 64");
     return true;
@@ -210,6 +210,14 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.reward = add(4 * E);
     o.far_cnt = add(4 * cells);
     o.far_bits = add(cells / 64);
+    o.ray_code = add(4 * rays);
+    o.env_sense = add(env_sense_bytes() * E);
+    {
+        size_t nb = 0;
+        const int sb = sense_block(hi.gt_words_max);
+        for (int e = 0; e < hi.E; ++e) nb += (size_t)(hi.B[e] + sb - 1) / sb;
+        o.bundles = add(8 * std::max<size_t>(nb, 1));
+    }
     o.queue = add(8);          // {next item, CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
@@ -293,10 +301,16 @@ int near_words(const HostInfo &hi) {
     return (int)pad_to((size_t)nb * nb, 4);
 }
 
+// Shared words of the update kernel's per-beam chunk table and of the
+// entropy half table (int64 per |L| = 0..clamp).
+int pref_words(const HostInfo &hi) { return 3 * (int)pad_to((size_t)hi.b_max + 1, 4); }
+int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }
+
 constexpr int kStaticSmem = 2048;
 
-int auto_window(const HostInfo &hi, int smem_optin) {
-    long long budget_words = (smem_optin - kStaticSmem) / 4 - hi.gt_words_max - near_words(hi);
+int auto_window(const HostInfo &hi, int smem_optin, int clamp_q) {
+    long long budget_words = (smem_optin - kStaticSmem) / 4 - pref_words(hi) - near_words(hi) -
+                             lut_words(clamp_q);
     int S = (int)std::floor(std::sqrt(4.0 * (double)budget_words));
     S &= ~7;
     return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
@@ -322,7 +336,8 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     int ww = 0;
     std::string msg;
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
-    const size_t smem = 4 * ((size_t)b->hi.gt_words_max + ww + near_words(b->hi));
+    const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) + pref_words(b->hi) + ww +
+                             near_words(b->hi));
     if (smem + kStaticSmem > (size_t)b->smem_optin)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
     CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
@@ -337,6 +352,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     b->p.gt_words_max = b->hi.gt_words_max;
     b->p.win_words_max = ww;
     b->p.near_words_max = near_words(b->hi);
+    b->p.lut_words = lut_words(b->p.clamp_q);
     return ASLAM_OK;
 }
 
@@ -525,6 +541,10 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.reward = at<float>(b, o.reward);
         p.far_cnt = at<unsigned>(b, o.far_cnt);
         p.far_bits = at<unsigned>(b, o.far_bits);
+        p.ray_code = at<int>(b, o.ray_code);
+        p.env_sense = at<void>(b, o.env_sense);
+        // later chunks must start outside the near block: chunk >= 2*R8
+        p.chunk = std::max(32, 2 * hi.r8_max);
         p.queue = at<unsigned>(b, o.queue);
         p.err = at<unsigned>(b, o.err);
 
@@ -573,6 +593,15 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                                                 (double)hi.D[e] * hi.D[e]));
         std::stable_sort(b->order.begin(), b->order.end(),
                          [&](int a, int c2) { return cost[a] > cost[c2]; });
+        // sensing bundles of sense_block() beams, costliest envs first
+        std::vector<int2> bundles;
+        p.sense_block = sense_block(hi.gt_words_max);
+        for (int q = 0; q < E; ++q) {
+            const int e = b->order[q];
+            for (int b0 = 0; b0 < hi.B[e]; b0 += p.sense_block) bundles.push_back(make_int2(e, b0));
+        }
+        p.n_bundles = (int)bundles.size();
+        p.bundles = at<int2>(b, o.bundles);
 
         auto h2d = [&](void *dst, const void *src, size_t n) {
             return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
@@ -588,6 +617,8 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 == cudaSuccess) e1 = h2d((void *)p.Dd, hi.D.data(), 4 * (size_t)E);
         if (e1 == cudaSuccess) e1 = h2d((void *)p.elev_cs, elev.data(), 8 * elev.size());
         if (e1 == cudaSuccess) e1 = h2d((void *)p.order, b->order.data(), 4 * (size_t)E);
+        if (e1 == cudaSuccess && !bundles.empty())
+            e1 = h2d((void *)p.bundles, bundles.data(), 8 * bundles.size());
         if (e1 == cudaSuccess) e1 = h2d((void *)p.map_off, hi.map_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d((void *)p.gtb_off, hi.gtb_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d((void *)p.ray_off, hi.ray_off.data(), 8 * (size_t)(E + 1));
@@ -607,7 +638,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 != cudaSuccess) { st = cuda_fail(b, e1, "create: upload"); break; }
         st = reset_all(b, s);
         if (st != ASLAM_OK) break;
-        const int S = cfg->window_cells ? cfg->window_cells : auto_window(hi, b->smem_optin);
+        const int S = cfg->window_cells ? cfg->window_cells : auto_window(hi, b->smem_optin, cfg->l_clamp_q);
         const int block = cfg->threads_per_cta ? cfg->threads_per_cta : default_block(hi);
         st = configure_launch(b, block, S);
         if (st != ASLAM_OK) break;
@@ -741,7 +772,7 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
     std::vector<int> blocks, windows;
     for (int t : {128, 256, 384, 512, 768, 1024})
         if (t >= 64 && (t <= 1024)) blocks.push_back(t);
-    const int Sa = auto_window(b->hi, b->smem_optin);
+    const int Sa = auto_window(b->hi, b->smem_optin, b->p.clamp_q);
     for (int S : {Sa, 320, 256, 224, 192, 160, 128})
         if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
     if (b->hi.dims == 3) {

@@ -169,6 +169,12 @@ struct Step2DParams {
     float *terms, *reward;
     unsigned *far_cnt;           // [sum cells] (hits << 16 | misses) outside the window
     unsigned *far_bits;          // [sum cells / 256] touched 8-cell chunks outside the window
+    int *ray_code;               // [sum B] sensing result per beam: Ku | hit << 30, -1: no cells
+    void *env_sense;             // [E] EnvSense: what the sensing kernel hands to the update kernel
+    int chunk;                   // cells per update-walk chunk
+    int lut_words;               // shared words of the entropy half table
+    const int2 *bundles;         // [n_bundles] (env, first beam) of each sensing CTA
+    int n_bundles, sense_block;
     // this launch
     const float *actions, *u_in;
     float *out_reward, *out_obs;
@@ -189,6 +195,8 @@ void set_thread_error(const char *msg);
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 cudaError_t step2d_set_smem(size_t smem);
+size_t env_sense_bytes();
+int sense_block(int gt_words_max);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 cudaError_t step3d_set_smem(size_t smem);

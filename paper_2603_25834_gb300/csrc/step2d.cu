@@ -1,22 +1,26 @@
-// step2d.cu -- the batched 2-D environment step on sm_103a.
+// step2d.cu -- the batched 2-D environment step on sm_103a, in two kernels.
 //
-// One persistent CTA takes one environment at a time from a cost-ordered
-// work queue and runs the whole step for it:
-//   A. thread 0: reset if the env was done, action integration (Euler
-//      unicycle, Sec. III-C Eq. 4 / Sec. IV-A robot), ray origin in Q16;
-//   B. all threads: stage the env's ground-truth grid (1 bit per cell) in
-//      shared memory and clear the shared hit/miss counters;
-//   C. one thread per beam: exact fixed-point grid traversal (Amanatides-Woo
-//      order with exact 64-bit comparisons) of the ground truth until the
-//      first occupied cell (Sec. IV-A LiDAR), Gaussian range noise, then a
-//      second traversal of the belief grid to the measured endpoint that
-//      adds one miss to every crossed cell and a hit to the endpoint of a
-//      returned beam (Sec. III-D log-odds grid);
-//   D. all threads: per cell, L' = clamp(L + h*HIT + m*MISS) (one clamp per
-//      scan, so the result does not depend on beam order) and the change of
-//      the cell's entropy from a fixed-point table;
-//   E. thread 0: segmented reductions -> entropy gain, Eq. 7-17 reward,
-//      visit grid (Eq. 8-9), termination; all threads: observation (Eq. 3).
+// sense2d_kernel: one CTA per environment, one thread per beam.  Thread 0
+//   resets a done env and integrates the action (Euler unicycle, Sec. III-C
+//   Eq. 4 / Sec. IV-A robot); the env's ground truth is staged in shared
+//   memory as one bit per cell; every thread walks its beam's cells with an
+//   exact fixed-point traversal (Amanatides-Woo order, exact 64-bit
+//   comparisons, ties Y first) to the first occupied cell (Sec. IV-A LiDAR),
+//   draws the range noise, and records how many crossings the belief walk to
+//   the measured endpoint takes (Ku) and whether the beam returned.  It needs
+//   no counters, so every env of a batch can be in flight at once.
+//
+// update2d_kernel: one persistent CTA per environment, pulled from a
+//   longest-first queue.  The belief walks of all beams (one miss per crossed
+//   cell, a hit at the endpoint of a returned beam; Sec. III-D log-odds grid)
+//   are cut into chunks of `chunk` cells; a chunk starts by jumping the walk
+//   straight to its first step (the number of x-crossings among the first s
+//   crossings follows from the same exact comparisons), so the CTA's lanes
+//   share the work evenly instead of waiting for the longest beam.  Counts go
+//   to shared-memory counters; then every touched cell gets
+//   L' = clamp(L + h*HIT + m*MISS) once per scan (beam order does not
+//   matter), the entropy change comes from a fixed-point table, and thread 0
+//   finishes the reward (Eq. 7-17), visit grid (Eq. 8-9) and termination.
 //
 // Counters.  A cell at Chebyshev distance d >= 2 from the robot's cell has
 // its centre at least d - 1/2 cells from the robot and lies in a disc of
@@ -34,93 +38,244 @@
 #include "env_common.cuh"
 
 namespace aslam {
+
+// Handed from the sensing kernel to the update kernel, one per env.
+struct EnvSense {
+    EnvStart start;
+    int Px, Py, col_cell, gt_cells;
+    float c, s, dmin_meas, dmin_true;
+};
+
+size_t env_sense_bytes() { return sizeof(EnvSense); }
+
 namespace {
 
-struct EnvShared {
-    int e, W, H, B, reset, partial, R8, NB;
-    int Px, Py, ri, rj, col_cell;
-    int wx0, wy0, SW, SH;
-    float c, s;
-    long long map_off, gtb_off, ray_off;
-    EnvStart start;
-};
+constexpr int kSenseSmemMax = 200 * 1024;   // ground truth of up to 1.6 M cells
 
 __device__ __forceinline__ unsigned gt_bit(const unsigned *bits, int k) {
     return (bits[k >> 5] >> (k & 31)) & 1u;
 }
 
-// L2 prefetch of a byte range (bulk-copy engine, no completion to wait for).
+// L2 prefetch of a byte range (bulk-copy engine, nothing to wait for).
 __device__ __forceinline__ void prefetch_l2(const void *ptr, unsigned bytes) {
     bytes &= ~15u;
     if (bytes == 0u) return;
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
 }
 
-// Grab the next queue item; for an in-range item prefetch what its step reads.
-__device__ __forceinline__ int grab_item(const Step2DParams &p) {
-    const int item = (int)atomicAdd(p.queue, 1u);
-    if (item < p.E) {
-        const int e = p.order[item];
-        const long long n = (long long)p.W[e] * p.H[e];
-        prefetch_l2(p.gt_bits + p.gtb_off[e], (unsigned)(((n + 127) >> 7) << 4));
-        prefetch_l2(p.belief + p.map_off[e], (unsigned)min(2 * n, (long long)(1 << 30)));
-    }
-    return item;
+// Fixed-point beam geometry shared by both kernels.
+struct Beam {
+    int sx, sy;
+    long long adx, ady, nx0, ny0;
+};
+
+__device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray, int Px, int Py,
+                                           int i0, int j0, float c, float s) {
+    const float2 cs = p.beam_cs[ray];
+    const float dx = fsub(fmul(c, cs.x), fmul(s, cs.y));
+    const float dy = fadd(fmul(s, cs.x), fmul(c, cs.y));
+    const int Dx = __float2int_rn(fmul(dx, 1073741824.0f));
+    const int Dy = __float2int_rn(fmul(dy, 1073741824.0f));
+    Beam b;
+    b.sx = (Dx > 0) - (Dx < 0);
+    b.sy = (Dy > 0) - (Dy < 0);
+    b.adx = Dx < 0 ? -(long long)Dx : (long long)Dx;
+    b.ady = Dy < 0 ? -(long long)Dy : (long long)Dy;
+    // Q16 distance from the origin to the first grid line along each axis
+    b.nx0 = Dx > 0 ? ((long long)(i0 + 1) << 16) - Px
+                   : (Dx < 0 ? (long long)Px - ((long long)i0 << 16) : 65536);
+    b.ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - Py
+                   : (Dy < 0 ? (long long)Py - ((long long)j0 << 16) : 65536);
+    return b;
 }
 
-__device__ __forceinline__ void env_prologue(const Step2DParams &p, int e, EnvShared &sh) {
+// Number of cells of the beam's walk that lie in the W x H map (the walk
+// leaves at the first crossing past the last column or row in its way).
+__device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W, int H) {
+    const long long big = 1LL << 40;
+    const int rx = b.sx > 0 ? W - 1 - i0 : i0;       // x-crossings that stay inside
+    const int ry = b.sy > 0 ? H - 1 - j0 : j0;
+    if (b.adx == 0) return b.ady == 0 ? (int)big : ry + 1;
+    if (b.ady == 0) return rx + 1;
+    const long long NX = b.nx0 + ((long long)rx << 16);    // the crossing that leaves along x
+    const long long NY = b.ny0 + ((long long)ry << 16);    // ... along y
+    if (NX * b.ady < NY * b.adx) {
+        // leaves along x: y-crossings before it (ties go Y first, so <=)
+        const long long D = NX * b.ady - b.ny0 * b.adx;
+        const long long cy = D < 0 ? 0 : D / (b.adx << 16) + 1;
+        return rx + (int)cy + 1;
+    }
+    // leaves along y: x-crossings strictly before it
+    const long long D = NY * b.adx - b.nx0 * b.ady;
+    const long long cx = D <= 0 ? 0 : (D - 1) / (b.ady << 16) + 1;
+    return ry + (int)cx + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Integration kernel: one thread per env
+// ---------------------------------------------------------------------------
+__global__ void integrate2d_kernel(const Step2DParams p) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += gridDim.x * blockDim.x) {
+        const int W = p.W[e], H = p.H[e];
+        EnvSense es;
+        es.start = begin_env(p, e, (long long)W * H);
+        es.Px = q16_of(es.start.x, p.res);
+        es.Py = q16_of(es.start.y, p.res);
+        const int ri = es.Px >> 16, rj = es.Py >> 16;
+        const bool inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
+        es.col_cell = !inside || gt_bit(p.gt_bits + p.gtb_off[e], rj * W + ri);
+        det_sincos(es.start.th, es.s, es.c);
+        es.gt_cells = 0;
+        es.dmin_meas = p.r_max;      // reduced with atomicMin on the (positive) float bits
+        es.dmin_true = p.r_max;
+        reinterpret_cast<EnvSense *>(p.env_sense)[e] = es;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sensing kernel: one small CTA per bundle of beams of one env
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
+    extern __shared__ __align__(16) unsigned s_gt[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
+    const int2 bundle = p.bundles[blockIdx.x];          // (env, first beam)
+    const int e = bundle.x;
+    const int b = bundle.y + tid;
+    EnvSense *esp = reinterpret_cast<EnvSense *>(p.env_sense) + e;
     const int W = p.W[e], H = p.H[e];
-    sh.e = e;
-    sh.W = W;
-    sh.H = H;
-    sh.B = p.B[e];
-    sh.R8 = p.R8[e];
-    sh.NB = 2 * sh.R8 - 1;
-    sh.map_off = p.map_off[e];
-    sh.gtb_off = p.gtb_off[e];
-    sh.ray_off = p.ray_off[e];
-    const EnvStart st = begin_env(p, e, (long long)W * H);
-    sh.start = st;
-    sh.reset = st.reset;
-    const float x = st.x, y = st.y, th = st.th;
-    int Px = q16_of(x, p.res), Py = q16_of(y, p.res);
-    sh.Px = Px;
-    sh.Py = Py;
-    int ri = Px >> 16, rj = Py >> 16;
-    sh.ri = ri;
-    sh.rj = rj;
-    int inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
-    sh.col_cell = !inside || gt_bit(p.gt_bits + sh.gtb_off, rj * W + ri);
-    float s1, c1;
-    det_sincos(th, s1, c1);
-    sh.c = c1;
-    sh.s = s1;
-    const int S = p.window;
-    int partial = (long long)W * H > (long long)S * S;
-    sh.partial = partial;
-    if (partial) {
-        int SW = min(S, W), SH = min(S, H);
-        sh.SW = SW;
-        sh.SH = SH;
-        sh.wx0 = min(max(ri - SW / 2, 0), W - SW) & ~7;
-        sh.wy0 = min(max(rj - SH / 2, 0), H - SH);
-    } else {
-        sh.SW = W;
-        sh.SH = H;
-        sh.wx0 = 0;
-        sh.wy0 = 0;
+    const int B = p.B[e];
+    if (bundle.y == 0 && tid == 0) {
+        // the update kernel will read this env's belief: stream it into L2
+        // while the beams are traced
+        prefetch_l2(p.belief + p.map_off[e], (unsigned)min(2LL * W * H, 1LL << 30));
+    }
+    {
+        // the env's ground truth, one bit per cell, into shared memory
+        const int words = (int)(((long long)W * H + 31) >> 5);
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + p.gtb_off[e]);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
+        for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
+    }
+    __syncthreads();
+    int gc = 0;
+    float dmin_m = p.r_max, dmin_t = p.r_max;
+    if (b < B) {
+        const unsigned *gt = s_gt;
+        const int Px = esp->Px, Py = esp->Py;
+        const int i0 = Px >> 16, j0 = Py >> 16;
+        const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
+        const long long ray = p.ray_off[e] + b;
+        const Beam bm = beam_setup(p, ray, Px, Py, i0, j0, esp->c, esp->s);
+        bool hit = false;
+        float z_true = p.r_max, z = p.r_max;
+        int code = -1;
+        if (in0) {
+            int k = j0 * W + i0, cells = 1;
+            if (gt_bit(gt, k)) {
+                hit = true;
+                z_true = 0.0f;
+            } else {
+                // next X crossing strictly earlier than next Y crossing iff
+                // nx/adx < ny/ady, i.e. e = nx*ady - ny*adx < 0 (ties step Y)
+                const int Ks = crossings_le(bm.nx0, bm.adx, p.Tmax) +
+                               crossings_le(bm.ny0, bm.ady, p.Tmax);
+                const long long dA = bm.ady << 16, dB = bm.adx << 16;
+                const int syW = bm.sy * W;
+                long long ee = bm.nx0 * bm.ady - bm.ny0 * bm.adx;
+                int i = i0, j = j0;
+                bool lastx = false;
+                for (int s = 0; s < Ks; ++s) {
+                    lastx = ee < 0;
+                    if (lastx) {
+                        i += bm.sx;
+                        k += bm.sx;
+                        ee += dA;
+                    } else {
+                        j += bm.sy;
+                        k += syW;
+                        ee -= dB;
+                    }
+                    if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
+                    ++cells;
+                    if (gt_bit(gt, k)) {
+                        hit = true;
+                        break;
+                    }
+                }
+                if (hit) {
+                    // entry parameter of the hit cell: the crossing that entered it
+                    const long long n = lastx ? bm.nx0 + ((long long)(abs(i - i0) - 1) << 16)
+                                              : bm.ny0 + ((long long)(abs(j - j0) - 1) << 16);
+                    const long long ad = lastx ? bm.adx : bm.ady;
+                    z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+                }
+            }
+            gc = cells;
+            z = z_true;
+            if (hit) {
+                const float g = det_gauss(p.key, (unsigned)e, (unsigned)esp->start.gstep, (unsigned)b);
+                z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
+            }
+            const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
+            const int Ku = crossings_le(bm.nx0, bm.adx, Tz) + crossings_le(bm.ny0, bm.ady, Tz);
+            // belief walk: cells 0..Ku, cut at the map border; the endpoint
+            // gets the hit only when it is in the map
+            const int nm = cells_in_map(bm, i0, j0, W, H);
+            const int ncells = min(Ku + 1, nm);
+            code = (ncells - 1) | ((hit && Ku < nm) ? (1 << 30) : 0);
+        }
+        p.ray_code[ray] = code;
+        p.z[ray] = z;
+        if (debug) {
+            p.z_true[ray] = z_true;
+            p.hit[ray] = hit ? 1 : 0;
+        }
+        if (p.out_obs) p.out_obs[(long long)e * (p.b_max + 2) + b] = z;
+        dmin_m = z;
+        dmin_t = z_true;
+    }
+    // per-env reductions: a warp sum / min, then one atomic per warp
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        gc += __shfl_down_sync(0xffffffffu, gc, o);
+        dmin_m = fminf(dmin_m, __shfl_down_sync(0xffffffffu, dmin_m, o));
+        dmin_t = fminf(dmin_t, __shfl_down_sync(0xffffffffu, dmin_t, o));
+    }
+    if (lane == 0) {
+        atomicAdd(&esp->gt_cells, gc);
+        // ranges are >= 0, so their float bits order like the values
+        atomicMin(reinterpret_cast<int *>(&esp->dmin_meas), __float_as_int(dmin_m));
+        atomicMin(reinterpret_cast<int *>(&esp->dmin_true), __float_as_int(dmin_t));
     }
 }
 
-// Adds (or, with sign < 0, removes) one hit or miss of cell (i, j) (flat k).
-template <bool kPartial>
+// ---------------------------------------------------------------------------
+// Update kernel
+// ---------------------------------------------------------------------------
+struct EnvShared {
+    int e, W, H, B, reset, partial, R8, NB;
+    int Px, Py, ri, rj, col_cell;
+    int wx0, wy0, SW, SH;
+    float c, s;
+    long long map_off, ray_off;
+    EnvStart start;
+    int gt_cells;
+    float dmin_meas, dmin_true;
+};
+
+// Adds one hit or miss of cell (i, j) (flat k) to its counter.  kNear:
+// the cell may lie in the 32-bit block around the robot.
+template <bool kPartial, bool kNear>
 __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared &sh, int i,
                                           int j, int k, bool is_hit, unsigned *s_win,
                                           unsigned *s_near) {
-    const int ni = i - sh.ri + sh.R8 - 1, nj = j - sh.rj + sh.R8 - 1;
-    if ((unsigned)ni < (unsigned)sh.NB && (unsigned)nj < (unsigned)sh.NB) {
-        atomicAdd(&s_near[nj * sh.NB + ni], is_hit ? 0x10000u : 1u);
-        return;
+    if (kNear) {
+        const int ni = i - sh.ri + sh.R8 - 1, nj = j - sh.rj + sh.R8 - 1;
+        if ((unsigned)ni < (unsigned)sh.NB && (unsigned)nj < (unsigned)sh.NB) {
+            atomicAdd(&s_near[nj * sh.NB + ni], is_hit ? 0x10000u : 1u);
+            return;
+        }
     }
     const unsigned inc = is_hit ? 0x10u : 0x01u;
     if (!kPartial) {
@@ -137,152 +292,98 @@ __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared
     atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
 }
 
-// One beam: ground-truth traversal, noise, belief traversal with counting.
-template <bool kPartial>
-__device__ __forceinline__ void trace_beam(const Step2DParams &p, const EnvShared &sh, int b,
-                                           const unsigned *s_gt, unsigned *s_win,
-                                           unsigned *s_near, int &rc, int &gc, float &dmin_m,
-                                           float &dmin_t) {
-    const float2 cs = p.beam_cs[sh.ray_off + b];
-    const float dx = fsub(fmul(sh.c, cs.x), fmul(sh.s, cs.y));
-    const float dy = fadd(fmul(sh.s, cs.x), fmul(sh.c, cs.y));
-    const int Dx = __float2int_rn(fmul(dx, 1073741824.0f));
-    const int Dy = __float2int_rn(fmul(dy, 1073741824.0f));
-    const int W = sh.W, H = sh.H;
-    const int Px = sh.Px, Py = sh.Py;
-    const int i0 = sh.ri, j0 = sh.rj;
-    const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
-    const int sx = (Dx > 0) - (Dx < 0), sy = (Dy > 0) - (Dy < 0);
-    const long long adx = Dx < 0 ? -(long long)Dx : (long long)Dx;
-    const long long ady = Dy < 0 ? -(long long)Dy : (long long)Dy;
-    // Q16 distance from the origin to the first grid line along each axis.
-    const long long nx0 = Dx > 0 ? ((long long)(i0 + 1) << 16) - Px
-                                 : (Dx < 0 ? (long long)Px - ((long long)i0 << 16) : 65536);
-    const long long ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - Py
-                                 : (Dy < 0 ? (long long)Py - ((long long)j0 << 16) : 65536);
-    // The next X crossing is strictly earlier than the next Y crossing iff
-    // nx/adx < ny/ady, i.e. e = nx*ady - ny*adx < 0 (ties step Y).
-    const long long e0 = nx0 * ady - ny0 * adx;
-    const long long dA = ady << 16, dB = adx << 16;
-    const int syW = sy * W;
-
-    bool hit = false;
-    float z_true = p.r_max;
-    int cells_gt = 0;
-    if (in0) {
-        int k = j0 * W + i0;
-        cells_gt = 1;
-        if (gt_bit(s_gt, k)) {
-            hit = true;
-            z_true = 0.0f;
-        } else {
-            const int Ks = crossings_le(nx0, adx, p.Tmax) + crossings_le(ny0, ady, p.Tmax);
-            int i = i0, j = j0;
-            long long e = e0;
-            bool lastx = false;
-            for (int s = 0; s < Ks; ++s) {
-                lastx = e < 0;
-                if (lastx) {
-                    i += sx;
-                    k += sx;
-                    e += dA;
-                } else {
-                    j += sy;
-                    k += syW;
-                    e -= dB;
-                }
-                if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
-                ++cells_gt;
-                if (gt_bit(s_gt, k)) {
-                    hit = true;
-                    break;
-                }
-            }
-            if (hit) {
-                // entry parameter of the hit cell: the crossing that entered it
-                const long long n = lastx ? nx0 + ((long long)(abs(i - i0) - 1) << 16)
-                                          : ny0 + ((long long)(abs(j - j0) - 1) << 16);
-                const long long ad = lastx ? adx : ady;
-                z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
-            }
-        }
-    }
-    float z = z_true;
-    if (hit) {
-        const float gz = det_gauss(p.key, (unsigned)sh.e, (unsigned)sh.start.gstep, (unsigned)b);
-        z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, gz)), 0.0f), p.r_max);
-    }
-    const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
-
-    int cells_upd = 0;
-    if (in0) {
-        const int Ku = crossings_le(nx0, adx, Tz) + crossings_le(ny0, ady, Tz);
-        int i = i0, j = j0, k = j0 * W + i0;
-        long long e = e0;
-        for (int s = 0;; ++s) {
-            const bool last = s == Ku;
-            add_count<kPartial>(p, sh, i, j, k, last && hit, s_win, s_near);
-            ++cells_upd;
-            if (last) break;
-            if (e < 0) {
-                i += sx;
-                k += sx;
-                e += dA;
-            } else {
-                j += sy;
-                k += syW;
-                e -= dB;
-            }
-            if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
-        }
-    }
-    const long long ro = sh.ray_off + b;
-    p.z[ro] = z;
-    if (p.flags & ASLAM_FLAG_DEBUG) {
-        p.z_true[ro] = z_true;
-        p.hit[ro] = hit ? 1 : 0;
-    }
-    if (p.out_obs) p.out_obs[(long long)sh.e * (p.b_max + 2) + b] = z;
-    rc += cells_upd;
-    gc += cells_gt;
-    dmin_m = fminf(dmin_m, z);
-    dmin_t = fminf(dmin_t, z_true);
+// Is the m-th x-crossing (m >= 1) strictly earlier than the n-th
+// y-crossing (n >= 1)?  Ties are taken Y first, as in the walk.
+__device__ __forceinline__ bool x_before_y(const Beam &b, int m, int n) {
+    return (b.nx0 + ((long long)(m - 1) << 16)) * b.ady <
+           (b.ny0 + ((long long)(n - 1) << 16)) * b.adx;
 }
 
+// Number of x-crossings among the first s crossings of the walk.
+__device__ __forceinline__ int x_steps_after(const Beam &b, int s) {
+    if (b.adx == 0) return 0;
+    if (b.ady == 0) return s;
+    int kx = __float2int_rd(__fdividef((float)s * (float)b.adx, (float)(b.adx + b.ady)));
+    kx = min(max(kx, 0), s);
+    // kx is the largest value whose kx-th x-crossing precedes the
+    // (s-kx+1)-th y-crossing; that predicate falls from true to false
+    if (kx == 0 || x_before_y(b, kx, s - kx + 1)) {
+        while (kx < s && x_before_y(b, kx + 1, s - kx)) ++kx;
+    } else {
+        do { --kx; } while (kx > 0 && !x_before_y(b, kx, s - kx + 1));
+    }
+    return kx;
+}
+
+// Walks cells s0 .. min(s0 + chunk, n) - 1 of beam b, where n = cells of its
+// belief walk (all in the map; the last one takes the hit of a returned beam).
+template <bool kPartial, bool kNear>
+__device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared &sh, int b,
+                                          int code, int s0, unsigned *s_win, unsigned *s_near) {
+    const Beam bm = beam_setup(p, sh.ray_off + b, sh.Px, sh.Py, sh.ri, sh.rj, sh.c, sh.s);
+    const int last = code & 0x3fffffff;              // index of the last cell
+    const bool hit = (code >> 30) & 1;
+    const int kx = s0 ? x_steps_after(bm, s0) : 0, ky = s0 - kx;
+    const int W = sh.W;
+    int i = sh.ri + bm.sx * kx, j = sh.rj + bm.sy * ky;
+    int k = j * W + i;
+    const long long dA = bm.ady << 16, dB = bm.adx << 16;
+    long long ee = (bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx;
+    const int syW = bm.sy * W;
+    const int s_end = min(last, s0 + p.chunk - 1);
+    for (int s = s0;; ++s) {
+        add_count<kPartial, kNear>(p, sh, i, j, k, hit && s == last, s_win, s_near);
+        if (s == s_end) break;
+        if (ee < 0) {
+            i += bm.sx;
+            k += bm.sx;
+            ee += dA;
+        } else {
+            j += bm.sy;
+            k += syW;
+            ee -= dB;
+        }
+    }
+    return s_end - s0 + 1;
+}
+
+// Entropy of log-odds L in 2^-40 nats from the half table h(|L|) (h is even).
+__device__ __forceinline__ long long h_of(const long long *s_lut, int L) { return s_lut[abs(L)]; }
+
 // Applies (h, m) to one cell's log-odds; returns the entropy change (2^-40 nats).
-__device__ __forceinline__ long long apply_cell(const Step2DParams &p, short &L, unsigned h,
-                                                unsigned m) {
+__device__ __forceinline__ long long apply_cell(const Step2DParams &p, const long long *s_lut,
+                                                short &L, unsigned h, unsigned m) {
     const int l0 = L;
     int l1 = l0 + (int)h * p.hit_q + (int)m * p.miss_q;
     l1 = min(max(l1, -p.clamp_q), p.clamp_q);
     L = (short)l1;
-    return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
+    return h_of(s_lut, l1) - h_of(s_lut, l0);
 }
 
-// Applies the 8-bit counters of 8 consecutive cells (two words) to their
-// int16 log-odds held in one int4.
-__device__ __forceinline__ long long apply8(const Step2DParams &p, uint2 cw, int4 &lv,
-                                            unsigned *dbg) {
+// Applies the 8-bit counters of 8 consecutive cells (two words).
+__device__ __forceinline__ long long apply8(const Step2DParams &p, const long long *s_lut,
+                                            uint2 cw, int4 &lv, unsigned *dbg) {
     short *L = reinterpret_cast<short *>(&lv);
     long long dh = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const unsigned c8 = ((q < 4 ? cw.x : cw.y) >> ((q & 3) << 3)) & 0xffu;
-        if (c8) dh += apply_cell(p, L[q], c8 >> 4, c8 & 0xfu);
+        if (c8) dh += apply_cell(p, s_lut, L[q], c8 >> 4, c8 & 0xfu);
         if (dbg) dbg[q] = ((c8 >> 4) << 16) | (c8 & 0xfu);
     }
     return dh;
 }
 
 // Applies 32-bit (hits << 16 | misses) counters of 8 consecutive cells.
-__device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const uint4 &c0,
-                                                 const uint4 &c1, int4 &lv, unsigned *dbg) {
+__device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const long long *s_lut,
+                                                 const uint4 &c0, const uint4 &c1, int4 &lv,
+                                                 unsigned *dbg) {
     short *L = reinterpret_cast<short *>(&lv);
     const unsigned c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     long long dh = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (c[q]) dh += apply_cell(p, L[q], c[q] >> 16, c[q] & 0xffffu);
+        if (c[q]) dh += apply_cell(p, s_lut, L[q], c[q] >> 16, c[q] & 0xffffu);
         if (dbg) dbg[q] = c[q];
     }
     return dh;
@@ -290,22 +391,26 @@ __device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const ui
 
 constexpr int kUnroll = 2;
 
-__global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
+__global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_gt = smem;
-    unsigned *s_win = smem + p.gt_words_max;
+    long long *s_lut = reinterpret_cast<long long *>(smem);           // [clamp_q + 1]
+    int *s_pref = reinterpret_cast<int *>(smem + p.lut_words);       // [b_max + 1]
+    int *s_first = s_pref + ((p.b_max + 1 + 3) & ~3);                 // [b_max]
+    int *s_beam = s_first + ((p.b_max + 3) & ~3);                     // [b_max]
+    unsigned *s_win = smem + p.lut_words + 3 * ((p.b_max + 1 + 3) & ~3);
     unsigned *s_near = s_win + p.win_words_max;
     __shared__ EnvShared sh;
     __shared__ long long r_dh[32];
-    __shared__ int r_rc[32], r_gc[32];
-    __shared__ float r_dm[32], r_dt[32];
-    __shared__ int s_next;
+    __shared__ int r_rc[32];
+    __shared__ int s_next, s_n0;
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
 
-    if (tid == 0) s_next = grab_item(p);
+    // entropy half table h(|L|), L = 0..clamp_q, shared by every env of the CTA
+    for (int q = tid; q <= p.clamp_q; q += nt) s_lut[q] = __ldg(&p.lut[p.clamp_q + q]);
+    if (tid == 0) s_next = (int)atomicAdd(p.queue, 1u);
     for (;;) {
         __syncthreads();                 // previous env finished, s_next visible
         const int item = s_next;
@@ -324,13 +429,49 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             break;
         }
         if (tid == 0) {
-            env_prologue(p, p.order[item], sh);
-            s_next = grab_item(p);   // one item ahead: its data streams into L2 meanwhile
+            const int e = p.order[item];
+            const EnvSense es = reinterpret_cast<const EnvSense *>(p.env_sense)[e];
+            const int W = p.W[e], H = p.H[e];
+            sh.e = e;
+            sh.W = W;
+            sh.H = H;
+            sh.B = p.B[e];
+            sh.R8 = p.R8[e];
+            sh.NB = 2 * sh.R8 - 1;
+            sh.map_off = p.map_off[e];
+            sh.ray_off = p.ray_off[e];
+            sh.start = es.start;
+            sh.reset = es.start.reset;
+            sh.Px = es.Px;
+            sh.Py = es.Py;
+            sh.ri = es.Px >> 16;
+            sh.rj = es.Py >> 16;
+            sh.col_cell = es.col_cell;
+            sh.c = es.c;
+            sh.s = es.s;
+            sh.gt_cells = es.gt_cells;
+            sh.dmin_meas = es.dmin_meas;
+            sh.dmin_true = es.dmin_true;
+            const int S = p.window;
+            sh.partial = (long long)W * H > (long long)S * S;
+            if (sh.partial) {
+                const int SW = min(S, W), SH = min(S, H);
+                sh.SW = SW;
+                sh.SH = SH;
+                sh.wx0 = min(max(sh.ri - SW / 2, 0), W - SW) & ~7;
+                sh.wy0 = min(max(sh.rj - SH / 2, 0), H - SH);
+            } else {
+                sh.SW = W;
+                sh.SH = H;
+                sh.wx0 = 0;
+                sh.wy0 = 0;
+            }
+            s_next = (int)atomicAdd(p.queue, 1u);
         }
         __syncthreads();
 
-        // ---- B: reset, stage ground truth, clear counters --------------------
-        const int e = sh.e, W = sh.W, H = sh.H;
+        // ---- reset, clear counters, chunk table --------------------------------
+        const int e = sh.e, W = sh.W, H = sh.H, B = sh.B;
         const long long ncell = (long long)W * H;
         const int nch = (int)((ncell + 7) >> 3);
         if (sh.reset) {
@@ -340,39 +481,84 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             for (long long q = tid; q < vn; q += nt) p.visit[vo + q] = -1;
         }
         {
-            const int words = (int)((ncell + 31) >> 5);
-            const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + sh.gtb_off);
-            uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
-            for (int q = tid; q < (words + 3) >> 2; q += nt) dst[q] = __ldg(&src[q]);
             const int cw = sh.partial ? (sh.SW * sh.SH + 3) >> 2 : (int)((ncell + 3) >> 2);
             uint4 *wz = reinterpret_cast<uint4 *>(s_win);
             for (int q = tid; q < (cw + 3) >> 2; q += nt) wz[q] = make_uint4(0, 0, 0, 0);
             for (int q = tid; q < sh.NB * sh.NB; q += nt) s_near[q] = 0u;
-            if (debug) {
+            if (debug)
                 for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
+        }
+        // Chunk table.  Chunks 0 .. n0-1 are the first chunks of the n0 beams
+        // with cells (beam ids in s_first); the rest, in beam order, are the
+        // later chunks (s_pref: running count of later chunks per beam).
+        for (int b = tid; b < B; b += nt) {
+            const int code = p.ray_code[sh.ray_off + b];
+            s_pref[b + 1] = code < 0 ? 0 : (code & 0x3fffffff) / p.chunk;     // later chunks
+            s_first[b] = code < 0 ? 0 : 1;
+        }
+        if (tid == 0) s_pref[0] = 0;
+        __syncthreads();
+        // inclusive scans of both by warp 0 / warp 1, in slices of 32
+        if (warp < 2) {
+            int *arr = warp == 0 ? s_pref + 1 : s_first;
+            int carry = 0;
+            for (int base = 0; base < B; base += 32) {
+                const int b = base + lane;
+                int v = b < B ? arr[b] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += t;
+                }
+                if (b < B) arr[b] = v + carry;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+        const int n0 = B ? s_first[B - 1] : 0;
+        // scatter: the first-chunk slot of beam b is s_first[b] - 1
+        if (tid == 0) s_n0 = n0;
+        for (int b = tid; b < B; b += nt) {
+            if (p.ray_code[sh.ray_off + b] >= 0) s_beam[s_first[b] - 1] = b;
+        }
+        __syncthreads();
+
+        // ---- belief walks, chunked ---------------------------------------------
+        int rc = 0;
+        const int total = s_n0 + s_pref[B];
+        for (int q = tid; q < total; q += nt) {
+            if (q < s_n0) {
+                // first chunk of a beam: may touch the 32-bit block near the robot
+                const int b = s_beam[q];
+                const int code = p.ray_code[sh.ray_off + b];
+                rc += sh.partial ? walk_chunk<true, true>(p, sh, b, code, 0, s_win, s_near)
+                                 : walk_chunk<false, true>(p, sh, b, code, 0, s_win, s_near);
+            } else {
+                // later chunks start >= chunk >= 2*R8 steps out: after s steps a walk
+                // is >= s/2 cells (Chebyshev) from the robot, outside the near block
+                const int qq = q - s_n0;
+                int lo = 0, hi = B - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pref[mid] <= qq) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int b = lo;
+                const int code = p.ray_code[sh.ray_off + b];
+                const int s0 = (qq - s_pref[b] + 1) * p.chunk;
+                rc += sh.partial ? walk_chunk<true, false>(p, sh, b, code, s0, s_win, s_near)
+                                 : walk_chunk<false, false>(p, sh, b, code, s0, s_win, s_near);
             }
         }
         __syncthreads();
 
-        // ---- C: beams --------------------------------------------------------
-        int rc = 0, gc = 0;
-        float dmin_m = p.r_max, dmin_t = p.r_max;
-        if (sh.partial) {
-            for (int b = tid; b < sh.B; b += nt)
-                trace_beam<true>(p, sh, b, s_gt, s_win, s_near, rc, gc, dmin_m, dmin_t);
-        } else {
-            for (int b = tid; b < sh.B; b += nt)
-                trace_beam<false>(p, sh, b, s_gt, s_win, s_near, rc, gc, dmin_m, dmin_t);
-        }
-        __syncthreads();
-
-        // ---- D: apply counters to the log-odds -------------------------------
+        // ---- apply counters to the log-odds -------------------------------------
         long long dh = 0;
         short *Lenv = p.belief + sh.map_off;
         unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
         {
-            // 8-cell chunks of the shared window: the loads of kUnroll chunks
-            // are issued before any of them is used.
+            // 8-cell chunks of the shared counters: the loads of kUnroll chunks
+            // are issued before any of them is used
             const int SW = sh.SW, rch = (SW + 7) >> 3;
             const int nchunk = sh.partial ? sh.SH * rch : nch;
             const uint2 *cw2 = reinterpret_cast<const uint2 *>(s_win);
@@ -406,7 +592,7 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     if (gk[u] >= 0) {
-                        dh += apply8(p, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr);
+                        dh += apply8(p, s_lut, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr);
                         *reinterpret_cast<int4 *>(Lenv + gk[u]) = lv[u];
                     }
                 }
@@ -429,7 +615,7 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
                     cp[0] = make_uint4(0u, 0u, 0u, 0u);
                     cp[1] = make_uint4(0u, 0u, 0u, 0u);
                     int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
-                    dh += apply8_wide(p, c0, c1, lv, dbg ? dbg + k : nullptr);
+                    dh += apply8_wide(p, s_lut, c0, c1, lv, dbg ? dbg + k : nullptr);
                     *reinterpret_cast<int4 *>(Lenv + k) = lv;
                 }
             }
@@ -440,47 +626,38 @@ __global__ void __launch_bounds__(1024, 1) step2d_kernel(const Step2DParams p) {
             if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
                 const unsigned c = s_near[q];
                 const long long k = (long long)j * W + i;
-                if (c) dh += apply_cell(p, Lenv[k], c >> 16, c & 0xffffu);
+                if (c) dh += apply_cell(p, s_lut, Lenv[k], c >> 16, c & 0xffffu);
                 if (dbg) dbg[k] = c;
             }
         }
 
-        // ---- E: reductions, reward, observation ------------------------------
+        // ---- reductions, reward, observation ------------------------------------
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             dh += __shfl_down_sync(0xffffffffu, dh, o);
             rc += __shfl_down_sync(0xffffffffu, rc, o);
-            gc += __shfl_down_sync(0xffffffffu, gc, o);
-            dmin_m = fminf(dmin_m, __shfl_down_sync(0xffffffffu, dmin_m, o));
-            dmin_t = fminf(dmin_t, __shfl_down_sync(0xffffffffu, dmin_t, o));
         }
         if (lane == 0) {
             r_dh[warp] = dh;
             r_rc[warp] = rc;
-            r_gc[warp] = gc;
-            r_dm[warp] = dmin_m;
-            r_dt[warp] = dmin_t;
         }
         __syncthreads();
         if (tid == 0) {
             EnvTotals r;
             r.dHq = 0;
             r.ray_cells = 0;
-            r.gt_cells = 0;
-            r.dmin_meas = p.r_max;
-            r.dmin_true = p.r_max;
             for (int w = 0; w < nwarps; ++w) {
                 r.dHq += r_dh[w];
                 r.ray_cells += r_rc[w];
-                r.gt_cells += r_gc[w];
-                r.dmin_meas = fminf(r.dmin_meas, r_dm[w]);
-                r.dmin_true = fminf(r.dmin_true, r_dt[w]);
             }
+            r.gt_cells = sh.gt_cells;
+            r.dmin_meas = sh.dmin_meas;
+            r.dmin_true = sh.dmin_true;
             finish_env(p, e, W, H, sh.start, sh.col_cell, r);
         }
         if (p.out_obs) {
             float *o = p.out_obs + (long long)e * (p.b_max + 2);
-            for (int b = sh.B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
+            for (int b = B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
         }
     }
 }
@@ -558,17 +735,39 @@ __global__ void detmath_kernel(const float *x, const float *u, int n, float *s, 
 }  // namespace
 
 cudaError_t step2d_set_smem(size_t smem) {
-    return cudaFuncSetAttribute(step2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(update2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sense2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSenseSmemMax);
+}
+
+// Beams per sensing CTA: 64, more for larger maps so that the ground truth
+// staged per CTA stays at <= 256 bytes per thread.
+int sense_block(int gt_words_max) {
+    int t = 64;
+    while (t < 256 && 4LL * gt_words_max > 256LL * t) t *= 2;
+    return t;
 }
 
 cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step2d_kernel, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, update2d_kernel, block, smem);
 }
 
+// Integration (one thread per env), sensing (one CTA per bundle of
+// kSenseBlock beams) and the persistent per-env update CTAs.
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s) {
-    step2d_kernel<<<grid, block, smem, s>>>(p);
+    integrate2d_kernel<<<(p.E + 127) / 128, 128, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (p.n_bundles > 0) {
+        const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
+        sense2d_kernel<<<p.n_bundles, p.sense_block, gt_bytes, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    update2d_kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 

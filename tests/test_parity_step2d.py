@@ -54,7 +54,7 @@ def test_paper_scale_small_batch(aslam_gpu, orc):
                noise_sigma_m=0.01)
 
 
-@pytest.mark.parametrize("window,threads", [(64, 128), (128, 96), (200, 256)])
+@pytest.mark.parametrize("window,threads", [(64, 128), (128, 160), (200, 256)])
 def test_partial_window_and_global_counters(aslam_gpu, orc, window, threads):
     inp = synth.paper_scale(E=4, seed=777)
     acts = synth.random_actions(6, 4, 9)
