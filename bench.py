@@ -7,15 +7,17 @@ noise sigma = 0.01 m, int16 log-odds, 1000 steps of random (v, w) actions
 and a synthetic uncertainty signal U_t (composite reward, Eq. 7-17).
 
 A "step" is one call of the whole path (action integration, raycast, log-odds
-update, reward, observation) for all envs: one kernel launch.  Inputs (all
-steps' actions and U_t) are resident in HBM before timing; L2 is flushed
-(256 MiB write) between timed steps, each step is timed with its own CUDA
-event pair on the launching stream.
+update, reward, observation) for all envs: three kernel launches (integrate,
+sense, update; one for the 3-D variant).  Inputs (all steps' actions and U_t)
+are resident in HBM before timing; L2 is flushed (256 MiB write) between
+timed steps, each step is timed with its own CUDA event pair on the
+launching stream, and the library's own events time each kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank steps its own 750 envs (weak scaling, no
-collective on the data path); the max over ranks of the timed total is used.
+Under torchrun (N > 1) the job holds N x 750 envs and every rank steps its
+contiguous, cost-balanced share (weak scaling, no collective on the data
+path); the max over ranks of the timed total is used.
 `--impl reference` times the CPU oracle (the plain C definition of the
 method) on this host's cores on a bounded sample of the same workload.
 """
@@ -42,14 +44,22 @@ WORKLOAD = dict(workload="paper_scale: 750 envs x 256^2 cells @0.05 m, 360 beams
                 envs=750, map_side=256, beams=360, res_m=0.05, r_max_m=12.0, noise_sigma_m=0.01,
                 reward="composite Eq. 7-17", steps_of_actions="random (v,w)",
                 l2="flushed (256 MiB write) between timed steps")
-KERNEL_SOURCES = ["paper_2603_25834_gb300/csrc/step2d.cu",
-                  "paper_2603_25834_gb300/csrc/aslam_internal.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step2d_paper_scale_traffic.json")
+KERNEL_SOURCES = {"2d": ["paper_2603_25834_gb300/csrc/step2d.cu",
+                         "paper_2603_25834_gb300/csrc/aslam_internal.cuh",
+                         "paper_2603_25834_gb300/csrc/env_common.cuh"],
+                  "3d": ["paper_2603_25834_gb300/csrc/step3d.cu",
+                         "paper_2603_25834_gb300/csrc/aslam_internal.cuh",
+                         "paper_2603_25834_gb300/csrc/env_common.cuh"]}
 
 
-def kernel_hash():
+def traffic_file(kernel, workload):
+    return os.path.join(ROOT, "profiles", "%s_%s_traffic.json" % (kernel.replace("_kernel", ""),
+                                                                   workload))
+
+
+def kernel_hash(dims="2d"):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[dims]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -268,7 +278,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2603_25834_gb300 import aslam, synth
+    from paper_2603_25834_gb300 import aslam, shard, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -279,37 +289,47 @@ def main():
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
 
+    # Weak scaling: E envs per GPU, world * E in the whole job; each rank
+    # builds and steps its contiguous, cost-balanced share of the global set
+    # (env_base = first global index keeps every env's noise stream).
     cfg_kw = dict(r_max_m=12.0, noise_sigma_m=0.01)
     if args.workload == "3d":
-        E = args.envs if args.envs != 750 else 512
-        inp = synth.voxel_batch(E=E, seed=synth.BASE_SEED + 100_000 * rank)
+        E_all = (args.envs if args.envs != 750 else 512) * world
+        lo, hi = shard.env_range(np.ones(E_all, np.int64), world, rank)
+        inp = synth.voxel_batch(E=E_all, envs=range(lo, hi))
         cfg_kw = dict(r_max_m=20.0, noise_sigma_m=0.01, n_rings=16)
-        workload = dict(workload="3d: %d envs x 128x128x32 voxels @0.1 m (floor, boxes, pillars), "
-                                 "16 rings x 512 azimuths over +-15 deg at 0.5 m, 20 m, "
-                                 "sigma 0.01 m, CUDA graph" % E,
-                        envs=E, res_m=0.1, r_max_m=20.0, noise_sigma_m=0.01,
+        workload = dict(workload="3d: %d envs per GPU x 128x128x32 voxels @0.1 m (floor, boxes, "
+                                 "pillars), 16 rings x 512 azimuths over +-15 deg at 0.5 m, 20 m, "
+                                 "sigma 0.01 m, CUDA graph" % (E_all // world),
+                        envs=E_all, res_m=0.1, r_max_m=20.0, noise_sigma_m=0.01,
                         reward="composite Eq. 7-17", l2="flushed (256 MiB write) between timed steps")
     elif args.workload == "uneven":
-        E = args.envs if args.envs != 750 else 4096
-        inp = synth.uneven(E=E, seed=synth.BASE_SEED + 100_000 * rank)
-        workload = dict(workload="uneven: %d envs, sides {128,256,384,512} @0.05 m, beams "
-                                 "{180,360,720}, 12 m, sigma 0.01 m, persistent launch, CUDA graph" % E,
-                        envs=E, res_m=0.05, r_max_m=12.0, noise_sigma_m=0.01,
+        E_all = (args.envs if args.envs != 750 else 4096) * world
+        side, nb = synth.uneven_shapes(E_all)
+        lo, hi = shard.env_range(shard.env_cost(side, side, nb), world, rank)
+        inp = synth.uneven(E=E_all, envs=range(lo, hi))
+        workload = dict(workload="uneven: %d envs per GPU, sides {128,256,384,512} @0.05 m, beams "
+                                 "{180,360,720}, 12 m, sigma 0.01 m, persistent launch, CUDA graph"
+                                 % (E_all // world),
+                        envs=E_all, res_m=0.05, r_max_m=12.0, noise_sigma_m=0.01,
                         reward="composite Eq. 7-17", l2="flushed (256 MiB write) between timed steps",
-                        mean_beams=float(inp.n_beams.mean()),
-                        mean_cells=float((inp.map_w.astype(np.int64) * inp.map_h).mean()))
+                        mean_beams=float(nb.mean()),
+                        mean_cells=float((side.astype(np.int64) ** 2).mean()))
     else:
-        E = args.envs
-        inp = synth.paper_scale(E=E, seed=synth.BASE_SEED + 100_000 * rank)
-        workload = dict(WORKLOAD, envs=E)
+        E_all = args.envs * world
+        lo, hi = shard.env_range(np.ones(E_all, np.int64), world, rank)
+        inp = synth.paper_scale(E=E_all, envs=range(lo, hi))
+        workload = dict(WORKLOAD, envs=E_all)
+    E = hi - lo
+    cfg_kw["env_base"] = lo
     batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE,
                           threads_per_cta=args.threads, window_cells=args.window, **cfg_kw)
     tuned = None
     if not args.no_autotune and not args.threads and not args.window:
         tuned = batch.autotune()
     K, W = args.steps, args.warmup
-    acts = torch.from_numpy(synth.random_actions(K + W, E, 7 + rank)).to(dev)
-    uu = torch.from_numpy(synth.random_uncertainty(K + W, E, 8 + rank)).to(dev)
+    acts = torch.from_numpy(synth.random_actions(K + W, E_all, 7)[:, lo:hi].copy()).to(dev)
+    uu = torch.from_numpy(synth.random_uncertainty(K + W, E_all, 8)[:, lo:hi].copy()).to(dev)
     reward = torch.empty(E, device=dev)
     obs = torch.empty(E, batch.b_max + 2, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -319,6 +339,8 @@ def main():
     st = batch.state()
     for s in range(W):
         batch.step_fused(acts[s], uu[s], reward, obs)
+    # per-kernel CUDA events inside the library, recorded on the launching stream
+    batch.profile_begin(K)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     clocks = ClockSampler(dev.index)
@@ -338,13 +360,11 @@ def main():
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
+    kernel_ms, prof_steps = batch.profile_end()
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     ray_cells = int(rc_acc.item())
     gt_cells = int(gc_acc.item())
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
+    total_ms_max = shard.max_over_ranks(total_ms, dev)
     batch.sync_status()
 
     # ---- graph-captured replay of the same step (reported beside) ----
@@ -372,8 +392,8 @@ def main():
 
     # ---- end to end through the public API with host buffers ----
     K2 = min(args.e2e_steps, K)
-    h_acts = torch.from_numpy(synth.random_actions(K2, E, 17 + rank)).pin_memory()
-    h_u = torch.from_numpy(synth.random_uncertainty(K2, E, 18 + rank)).pin_memory()
+    h_acts = torch.from_numpy(synth.random_actions(K2, E_all, 17)[:, lo:hi].copy()).pin_memory()
+    h_u = torch.from_numpy(synth.random_uncertainty(K2, E_all, 18)[:, lo:hi].copy()).pin_memory()
     h_rew = torch.empty(K2, E).pin_memory()
     h_obs = torch.empty(K2, E, batch.b_max + 2).pin_memory()
     d_a = torch.empty(E, 2, device=dev)
@@ -395,32 +415,49 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t2.item())
-    h2d = E * 2 * 4 + E * 4
-    d2h = E * 4 + E * (batch.b_max + 2) * 4
+    e2e_ms = shard.max_over_ranks(e2e_ms, dev)
+    h2d = shard.sum_over_ranks(E * 2 * 4 + E * 4, dev)
+    d2h = shard.sum_over_ranks(E * 4 + E * (batch.b_max + 2) * 4, dev)
+    ray_cells_all = shard.sum_over_ranks(ray_cells, dev)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    value = world * E * K / (total_ms_max / 1e3)
+    value = E_all * K / (total_ms_max / 1e3)
     ms_step = total_ms_max / K
-    # Algorithmic bytes of one launch: every updated cell read+written as
-    # int16 (4 B), every ground-truth cell read (1 B), ranges and observation
-    # written, pose/action/reward (24 B per env).
+    # Algorithmic bytes per launch (per-unit figures x units of one launch):
+    # each cell an update walk visits is an int16 read + write (4 B); each
+    # ground-truth cell a sensing walk visits is 1 bit of the packed world
+    # (1/8 B); per beam a 4 B range and a 4 B walk code written by the
+    # sensing and read by the update; per env the observation row
+    # (b_max + 2) x 4 B and 24 B of pose, action and reward.
     Bsum = int(batch.ray_off[-1])
-    alg_bytes = (ray_cells * 4 + gt_cells * 1) / K + Bsum * 4 + E * (batch.b_max + 2) * 4 + E * 24
+    rc_step, gt_step = ray_cells / K, gt_cells / K
+    io_env = E * (batch.b_max + 2) * 4 + E * 24
+    dims = "3d" if args.workload == "3d" else "2d"
+    if dims == "3d":
+        kbytes = {"step3d_kernel": rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env}
+    else:
+        kbytes = {"integrate2d_kernel": E * 24 + E * 72,
+                  "sense2d_kernel": gt_step / 8 + Bsum * 8,
+                  "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
+    step_bytes = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    kern = max(kernel_ms, key=kernel_ms.get)
+    k_ms = kernel_ms[kern] / prof_steps
+    achieved = kbytes[kern] / (k_ms / 1e3) / 1e9
+    kernels = {k: {"ms_per_launch": v / prof_steps, "share": v / sum(kernel_ms.values()),
+                   "alg_bytes_per_launch": kbytes[k],
+                   "achieved_gbs": kbytes[k] / (v / prof_steps / 1e3) / 1e9}
+               for k, v in kernel_ms.items()}
     traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as fh:
+    tf = traffic_file(kern, args.workload)
+    if os.path.exists(tf):
+        with open(tf) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_hash") == kernel_hash():
+        if tr.get("kernel_hash") == kernel_hash(dims) and tr.get("envs") == E:
             traffic = tr.get("dram_bytes_per_launch")
     cpu = None
     if not args.no_cpu_baseline and args.workload == "paper_scale":
@@ -435,19 +472,22 @@ def main():
         "vs_baseline": None, "dtype": "i16+f32", "data": "synthetic",
         "config": dict(workload, autotuned=({"threads_per_cta": tuned[0], "window_cells": tuned[1]}
                                             if tuned else None)),
-        "ray_cells_per_s": world * ray_cells / (total_ms_max / 1e3),
+        "ray_cells_per_s": ray_cells_all / (total_ms_max / 1e3),
         "ray_cells_per_step": ray_cells / K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)",
-                     "bytes_per_launch": alg_bytes,
-                     "kernel": "step3d_kernel" if args.workload == "3d" else "step2d_kernel"},
+                     "bytes_per_launch": kbytes[kern], "ms_per_launch": k_ms, "kernel": kern},
+        "kernels": kernels,
+        "step_roofline": {"bytes_per_step": step_bytes,
+                          "achieved": step_bytes / (ms_step / 1e3) / 1e9,
+                          "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * E * K2 / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": E_all * K2 / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "graph": {"value": world * E * gk / (g_ms / 1e3), "unit": UNIT, "steps": gk,
+        "graph": {"value": E_all * gk / (g_ms / 1e3), "unit": UNIT, "steps": gk,
                   "ms_per_step": g_ms / gk},
-        "gpu_launches": K,
+        "gpu_launches": K * len(kernel_ms),
         "clocks": clk,
     }
     print(json.dumps(line))

@@ -117,6 +117,11 @@ typedef struct {
     const int32_t *h_map_d;        /* HOST [E]: depth D (voxels) */
     int32_t n_rings;
     float sensor_z_m, elev_min_rad, elev_max_rad;
+    /* Global index of env 0 (>= 0, env_base + n_envs <= 2^31 - 1): the
+     * range-noise counter of env e is env_base + e, so a batch holding envs
+     * [lo, hi) of a larger set, created with env_base = lo, draws the same
+     * noise as those envs do in one batch of the whole set (default 0). */
+    int32_t env_base;
 } aslam_config;
 
 #define ASLAM_MAX_BEAMS 1024
@@ -222,6 +227,26 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream);
 aslam_status aslam_state_bytes(aslam_batch *b, size_t *bytes);
 aslam_status aslam_save_state(aslam_batch *b, void *h_buf, size_t bytes, void *stream);
 aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, void *stream);
+
+/*
+ * Per-kernel device timing of aslam_step / aslam_step_fused (graph replays
+ * are not timed).  aslam_profile_begin creates CUDA events for the next
+ * max_steps (1 .. 2^20) steps; each of those steps records one event before
+ * its first kernel and one after each kernel, on its own stream.
+ * aslam_profile_end waits for the last recorded event, writes the summed
+ * device time in ms of kernel k to h_ms[k] (host double
+ * [ASLAM_MAX_STEP_KERNELS], zero past the last kernel), the number of
+ * kernels a step launches to *h_n_kernels and the number of timed steps to
+ * *h_n_steps, and releases the events; ASLAM_ERR_STATE without a begin.
+ * aslam_kernel_name(b, k) is the name of kernel k ("integrate2d_kernel",
+ * "sense2d_kernel", "update2d_kernel"; 3-D: "step3d_kernel"), NULL past the
+ * last.  A static string, owned by the library.
+ */
+#define ASLAM_MAX_STEP_KERNELS 4
+aslam_status aslam_profile_begin(aslam_batch *b, int32_t max_steps);
+aslam_status aslam_profile_end(aslam_batch *b, double *h_ms, int32_t *h_n_kernels,
+                               int32_t *h_n_steps);
+const char *aslam_kernel_name(const aslam_batch *b, int32_t k);
 
 /* Release the host handle (the caller frees the workspace). */
 void aslam_destroy_batch(aslam_batch *b);

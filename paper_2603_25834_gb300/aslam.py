@@ -55,7 +55,7 @@ class AslamConfig(C.Structure):
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
         ("seed", C.c_uint64), ("flags", C.c_int32), ("window_cells", C.c_int32),
         ("h_map_d", P), ("n_rings", C.c_int32), ("sensor_z_m", C.c_float),
-        ("elev_min_rad", C.c_float), ("elev_max_rad", C.c_float),
+        ("elev_min_rad", C.c_float), ("elev_max_rad", C.c_float), ("env_base", C.c_int32),
     ]
 
 
@@ -92,6 +92,9 @@ EXPORTS = {
     "aslam_state_bytes": ([P, C.POINTER(C.c_size_t)], C.c_int),
     "aslam_save_state": ([P, P, C.c_size_t, P], C.c_int),
     "aslam_load_state": ([P, P, C.c_size_t, P], C.c_int),
+    "aslam_profile_begin": ([P, C.c_int32], C.c_int),
+    "aslam_profile_end": ([P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+    "aslam_kernel_name": ([P, C.c_int32], C.c_char_p),
     "aslam_destroy_batch": ([P], None),
     "aslam_status_string": ([C.c_int], C.c_char_p),
     "aslam_last_error": ([P], C.c_char_p),
@@ -316,6 +319,18 @@ class Batch2D:
         best = (C.c_int32 * 2)()
         _check(self.lib.aslam_autotune(self.handle, best, _stream(stream)), self.handle)
         return int(best[0]), int(best[1])
+
+    def profile_begin(self, max_steps):
+        """Time each kernel of the next max_steps steps with CUDA events."""
+        _check(self.lib.aslam_profile_begin(self.handle, int(max_steps)), self.handle)
+
+    def profile_end(self):
+        """{kernel name: summed device ms} and the number of timed steps."""
+        ms = (C.c_double * 4)()
+        nk, ns = C.c_int32(), C.c_int32()
+        _check(self.lib.aslam_profile_end(self.handle, ms, C.byref(nk), C.byref(ns)), self.handle)
+        names = [self.lib.aslam_kernel_name(self.handle, k).decode() for k in range(nk.value)]
+        return {n: float(ms[k]) for k, n in enumerate(names)}, int(ns.value)
 
     def save_state(self, stream=None):
         n = C.c_size_t()

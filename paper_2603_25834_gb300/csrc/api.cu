@@ -76,6 +76,8 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (c->struct_size != sizeof(aslam_config)) return fail("config struct_size mismatch");
     if (c->version != ASLAM_CONFIG_VERSION) return fail("config version mismatch");
     if (c->n_envs < 1) return fail("n_envs must be >= 1");
+    if (c->env_base < 0 || (long long)c->env_base + c->n_envs > 2147483647LL)
+        return fail("env_base out of [0, 2^31 - 1 - n_envs]");
     if (c->dims != 2 && c->dims != 3) return fail("dims must be 2 or 3");
     if (c->dims == 3) {
         if (!c->h_map_d) return fail("h_map_d is NULL for a 3-D batch");
@@ -243,6 +245,9 @@ struct aslam_batch {
     cudaGraphExec_t gexec = nullptr;
     std::string err;
     std::vector<int> order;
+    // per-kernel timing (aslam_profile_begin/end): (kernels + 1) events per step
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_cap = 0, prof_n = 0;
 };
 
 namespace {
@@ -267,6 +272,16 @@ aslam_status cuda_fail(aslam_batch *b, cudaError_t e, const char *where) {
 template <class T>
 T *at(aslam_batch *b, size_t off) {
     return reinterpret_cast<T *>(b->ws + off);
+}
+
+int step_kernels(const aslam_batch *b) {
+    return b->hi.dims == 3 ? kStep3DKernels : kStep2DKernels;
+}
+
+void release_profile(aslam_batch *b) {
+    for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
+    b->prof_ev.clear();
+    b->prof_cap = b->prof_n = 0;
 }
 
 // Shared-memory needs of a window side S: words of 8-bit counters for the
@@ -499,6 +514,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.kappa = cfg->kappa;
         p.u_hi = cfg->u_hi;
         p.key = make_uint2((unsigned)cfg->seed, (unsigned)(cfg->seed >> 32));
+        p.env_base = cfg->env_base;
         p.W = at<int>(b, o.W);
         p.H = at<int>(b, o.H);
         p.B = at<int>(b, o.B);
@@ -663,10 +679,15 @@ aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const floa
     p.u_in = d_u;
     p.out_reward = d_reward;
     p.out_obs = d_obs;
+    const cudaEvent_t *ev = nullptr;
+    if (b->prof_n < b->prof_cap) {
+        ev = &b->prof_ev[(size_t)b->prof_n * (step_kernels(b) + 1)];
+        ++b->prof_n;
+    }
     if (b->hi.dims == 3)
-        CK(launch_step3d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
+        CK(launch_step3d(p, b->grid, b->block, b->smem, (cudaStream_t)stream, ev), "aslam_step");
     else
-        CK(launch_step2d(p, b->grid, b->block, b->smem, (cudaStream_t)stream), "aslam_step");
+        CK(launch_step2d(p, b->grid, b->block, b->smem, (cudaStream_t)stream, ev), "aslam_step");
     return ASLAM_OK;
 }
 
@@ -877,8 +898,62 @@ aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, v
     return ASLAM_OK;
 }
 
+aslam_status aslam_profile_begin(aslam_batch *b, int32_t max_steps) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (max_steps < 1 || max_steps > (1 << 20))
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "max_steps must be in [1, 2^20]");
+    release_profile(b);
+    const size_t n = (size_t)max_steps * (step_kernels(b) + 1);
+    b->prof_ev.reserve(n);
+    for (size_t i = 0; i < n; ++i) {
+        cudaEvent_t e;
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            release_profile(b);
+            return cuda_fail(b, ce, "aslam_profile_begin");
+        }
+        b->prof_ev.push_back(e);
+    }
+    b->prof_cap = max_steps;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_profile_end(aslam_batch *b, double *h_ms, int32_t *h_n_kernels,
+                               int32_t *h_n_steps) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!h_ms || !h_n_kernels || !h_n_steps) return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL argument");
+    if (b->prof_cap == 0) return fail_b(b, ASLAM_ERR_STATE, "no aslam_profile_begin");
+    const int nk = step_kernels(b);
+    for (int k = 0; k < ASLAM_MAX_STEP_KERNELS; ++k) h_ms[k] = 0.0;
+    aslam_status st = ASLAM_OK;
+    if (b->prof_n > 0) {
+        cudaError_t ce = cudaEventSynchronize(b->prof_ev[(size_t)b->prof_n * (nk + 1) - 1]);
+        for (int i = 0; i < b->prof_n && ce == cudaSuccess; ++i) {
+            const cudaEvent_t *ev = &b->prof_ev[(size_t)i * (nk + 1)];
+            for (int k = 0; k < nk && ce == cudaSuccess; ++k) {
+                float ms = 0.0f;
+                ce = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+                h_ms[k] += ms;
+            }
+        }
+        if (ce != cudaSuccess) st = cuda_fail(b, ce, "aslam_profile_end");
+    }
+    *h_n_kernels = nk;
+    *h_n_steps = b->prof_n;
+    release_profile(b);
+    return st;
+}
+
+const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
+    static const char *const k2[] = {"integrate2d_kernel", "sense2d_kernel", "update2d_kernel"};
+    if (!b || k < 0) return nullptr;
+    if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
+    return k < kStep2DKernels ? k2[k] : nullptr;
+}
+
 void aslam_destroy_batch(aslam_batch *b) {
     if (!b) return;
+    release_profile(b);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     delete b;

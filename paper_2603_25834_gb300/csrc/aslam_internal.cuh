@@ -147,6 +147,7 @@ struct Step2DParams {
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     uint2 key;
+    int env_base;                // global index of env 0 in the noise counter
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
@@ -192,13 +193,16 @@ constexpr unsigned kErrTimeout = 2u;
 void set_thread_error(const char *msg);
 
 // Launchers (defined next to their kernels).
+// `ev` (optional) receives an event record before the first kernel and
+// after each kernel of the step: 4 events for 2-D, 2 for 3-D.
+constexpr int kStep2DKernels = 3, kStep3DKernels = 1;
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s);
+                          cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s);
+                          cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step3d_set_smem(size_t smem);
 cudaError_t step3d_occupancy(int block, size_t smem, int *ctas_per_sm);
 cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm);

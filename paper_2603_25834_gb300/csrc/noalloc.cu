@@ -56,6 +56,7 @@ struct ScanParams {
     long long cells;
     float res, r_max, sigma;
     uint2 key;
+    int env_base;
     const uint8_t *gt;
     const float *pose;
     const int *step;
@@ -120,7 +121,7 @@ __global__ void scan_rays_kernel(const ScanParams p) {
         }
         z = z_true;
         if (hit) {
-            const float g = det_gauss(p.key, (unsigned)e, (unsigned)p.step[e], (unsigned)b);
+            const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)p.step[e], (unsigned)b);
             z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
         }
         const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
@@ -190,6 +191,8 @@ extern "C" aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const
     const int E = cfg->n_envs;
     if (E < 1 || E > kMaxEnvs)
         return na_fail(ASLAM_ERR_INVALID_ARG, "n_envs out of [1, 2048] (the static scratch maximum)");
+    if (cfg->env_base < 0 || (long long)cfg->env_base + E > 2147483647LL)
+        return na_fail(ASLAM_ERR_INVALID_ARG, "env_base out of [0, 2^31 - 1 - n_envs]");
     if (!cfg->h_map_w || !cfg->h_map_h || !cfg->h_n_beams || !h_gt_off || !d_gt || !d_pose ||
         !d_step || !d_belief || !d_ranges)
         return na_fail(ASLAM_ERR_INVALID_ARG, "NULL pointer argument");
@@ -256,6 +259,7 @@ extern "C" aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const
     p.r_max = cfg->r_max_m;
     p.sigma = cfg->noise_sigma_m;
     p.key = make_uint2((unsigned)cfg->seed, (unsigned)(cfg->seed >> 32));
+    p.env_base = cfg->env_base;
     p.gt = d_gt;
     p.pose = d_pose;
     p.step = d_step;

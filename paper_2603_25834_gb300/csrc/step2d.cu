@@ -1,26 +1,33 @@
-// step2d.cu -- the batched 2-D environment step on sm_103a, in two kernels.
+// step2d.cu -- the batched 2-D environment step on sm_103a, in three kernels.
 //
-// sense2d_kernel: one CTA per environment, one thread per beam.  Thread 0
-//   resets a done env and integrates the action (Euler unicycle, Sec. III-C
-//   Eq. 4 / Sec. IV-A robot); the env's ground truth is staged in shared
-//   memory as one bit per cell; every thread walks its beam's cells with an
-//   exact fixed-point traversal (Amanatides-Woo order, exact 64-bit
-//   comparisons, ties Y first) to the first occupied cell (Sec. IV-A LiDAR),
-//   draws the range noise, and records how many crossings the belief walk to
-//   the measured endpoint takes (Ku) and whether the beam returned.  It needs
-//   no counters, so every env of a batch can be in flight at once.
+// integrate2d_kernel: one thread per environment resets a done env to its
+//   next spawn pose and integrates the action (Euler unicycle, Sec. III-C
+//   Eq. 4 / Sec. IV-A robot), then writes the env's sensing header (Q16
+//   origin, heading sin/cos, collision cell, reduction seeds).
 //
-// update2d_kernel: one persistent CTA per environment, pulled from a
-//   longest-first queue.  The belief walks of all beams (one miss per crossed
-//   cell, a hit at the endpoint of a returned beam; Sec. III-D log-odds grid)
-//   are cut into chunks of `chunk` cells; a chunk starts by jumping the walk
-//   straight to its first step (the number of x-crossings among the first s
-//   crossings follows from the same exact comparisons), so the CTA's lanes
-//   share the work evenly instead of waiting for the longest beam.  Counts go
-//   to shared-memory counters; then every touched cell gets
+// sense2d_kernel: one small CTA per bundle of up to `sense_block` beams of
+//   one env.  The env's ground truth is staged in shared memory as one bit
+//   per cell; every thread walks its beam's cells with an exact fixed-point
+//   traversal (Amanatides-Woo order, exact 64-bit comparisons, ties Y first)
+//   to the first occupied cell (Sec. IV-A LiDAR), draws the range noise, and
+//   records how many cells the belief walk to the measured endpoint has
+//   inside the map and whether that endpoint takes a hit.  Per-env sums and
+//   minima go through one atomic per warp.  The first bundle of each env
+//   also starts an L2 bulk prefetch of the env's belief for the update.
+//
+// update2d_kernel: persistent CTAs pull environments from a longest-first
+//   queue.  The belief walks of all beams (one miss per crossed cell, a hit
+//   at the endpoint of a returned beam; Sec. III-D log-odds grid) are cut
+//   into chunks of `chunk` cells; a chunk starts by jumping the walk straight
+//   to its first step (the number of x-crossings among the first s crossings
+//   follows from the same exact comparisons), so the CTA's lanes share the
+//   work evenly instead of waiting for the longest beam.  Counts go to
+//   shared-memory counters; then every touched cell gets
 //   L' = clamp(L + h*HIT + m*MISS) once per scan (beam order does not
-//   matter), the entropy change comes from a fixed-point table, and thread 0
-//   finishes the reward (Eq. 7-17), visit grid (Eq. 8-9) and termination.
+//   matter) and the entropy change comes from a fixed-point table.  The last
+//   warp of the CTA does not walk: while the others walk env n it finishes
+//   env n-1 (reward Eq. 7-17, visit grid Eq. 8-9, termination, outputs) and
+//   loads env n+1's parameters.
 //
 // Counters.  A cell at Chebyshev distance d >= 2 from the robot's cell has
 // its centre at least d - 1/2 cells from the robot and lies in a disc of
@@ -92,10 +99,9 @@ __device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray,
 // Number of cells of the beam's walk that lie in the W x H map (the walk
 // leaves at the first crossing past the last column or row in its way).
 __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W, int H) {
-    const long long big = 1LL << 40;
     const int rx = b.sx > 0 ? W - 1 - i0 : i0;       // x-crossings that stay inside
     const int ry = b.sy > 0 ? H - 1 - j0 : j0;
-    if (b.adx == 0) return b.ady == 0 ? (int)big : ry + 1;
+    if (b.adx == 0) return b.ady == 0 ? 0x7fffffff : ry + 1;
     if (b.ady == 0) return rx + 1;
     const long long NX = b.nx0 + ((long long)rx << 16);    // the crossing that leaves along x
     const long long NY = b.ny0 + ((long long)ry << 16);    // ... along y
@@ -172,6 +178,8 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         int code = -1;
         if (in0) {
             int k = j0 * W + i0, cells = 1;
+            // cells of the walk inside the map (the walk stops at the border)
+            const int nm = cells_in_map(bm, i0, j0, W, H);
             if (gt_bit(gt, k)) {
                 hit = true;
                 z_true = 0.0f;
@@ -180,33 +188,28 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                 // nx/adx < ny/ady, i.e. e = nx*ady - ny*adx < 0 (ties step Y)
                 const int Ks = crossings_le(bm.nx0, bm.adx, p.Tmax) +
                                crossings_le(bm.ny0, bm.ady, p.Tmax);
-                const long long dA = bm.ady << 16, dB = bm.adx << 16;
+                const int nsteps = min(Ks, nm - 1);
+                const long long dA = bm.ady << 16, ndB = -(bm.adx << 16);
                 const int syW = bm.sy * W;
                 long long ee = bm.nx0 * bm.ady - bm.ny0 * bm.adx;
-                int i = i0, j = j0;
+                int st = 0, kx = 0;
                 bool lastx = false;
-                for (int s = 0; s < Ks; ++s) {
+                for (; st < nsteps; ++st) {
                     lastx = ee < 0;
-                    if (lastx) {
-                        i += bm.sx;
-                        k += bm.sx;
-                        ee += dA;
-                    } else {
-                        j += bm.sy;
-                        k += syW;
-                        ee -= dB;
-                    }
-                    if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;
-                    ++cells;
+                    k += lastx ? bm.sx : syW;
+                    ee += lastx ? dA : ndB;
+                    kx += lastx;
                     if (gt_bit(gt, k)) {
                         hit = true;
+                        ++st;
                         break;
                     }
                 }
+                cells = st + 1;                 // the start cell and every step taken
                 if (hit) {
                     // entry parameter of the hit cell: the crossing that entered it
-                    const long long n = lastx ? bm.nx0 + ((long long)(abs(i - i0) - 1) << 16)
-                                              : bm.ny0 + ((long long)(abs(j - j0) - 1) << 16);
+                    const long long n = lastx ? bm.nx0 + ((long long)(kx - 1) << 16)
+                                              : bm.ny0 + ((long long)(st - kx - 1) << 16);
                     const long long ad = lastx ? bm.adx : bm.ady;
                     z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
                 }
@@ -214,14 +217,13 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
             gc = cells;
             z = z_true;
             if (hit) {
-                const float g = det_gauss(p.key, (unsigned)e, (unsigned)esp->start.gstep, (unsigned)b);
+                const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)esp->start.gstep, (unsigned)b);
                 z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
             }
             const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
             const int Ku = crossings_le(bm.nx0, bm.adx, Tz) + crossings_le(bm.ny0, bm.ady, Tz);
             // belief walk: cells 0..Ku, cut at the map border; the endpoint
             // gets the hit only when it is in the map
-            const int nm = cells_in_map(bm, i0, j0, W, H);
             const int ncells = min(Ku + 1, nm);
             code = (ncells - 1) | ((hit && Ku < nm) ? (1 << 30) : 0);
         }
@@ -331,9 +333,10 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
     long long ee = (bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx;
     const int syW = bm.sy * W;
     const int s_end = min(last, s0 + p.chunk - 1);
-    for (int s = s0;; ++s) {
-        add_count<kPartial, kNear>(p, sh, i, j, k, hit && s == last, s_win, s_near);
-        if (s == s_end) break;
+    const bool hit_end = hit && s_end == last;
+    const int n_miss = s_end - s0 + (hit_end ? 0 : 1);   // the hit cell is added last
+    for (int c = 0; c < n_miss; ++c) {
+        add_count<kPartial, kNear>(p, sh, i, j, k, false, s_win, s_near);
         if (ee < 0) {
             i += bm.sx;
             k += bm.sx;
@@ -344,6 +347,7 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
             ee -= dB;
         }
     }
+    if (hit_end) add_count<kPartial, kNear>(p, sh, i, j, k, true, s_win, s_near);
     return s_end - s0 + 1;
 }
 
@@ -389,8 +393,69 @@ __device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const lo
     return dh;
 }
 
+// Fills sh with the env of queue item `item` (sh.e = -1 past the last).
+__device__ __forceinline__ void load_env(const Step2DParams &p, int item, EnvShared &sh) {
+    if (item >= p.E) {
+        sh.e = -1;
+        return;
+    }
+    const int e = p.order[item];
+    const EnvSense es = reinterpret_cast<const EnvSense *>(p.env_sense)[e];
+    const int W = p.W[e], H = p.H[e];
+    sh.e = e;
+    sh.W = W;
+    sh.H = H;
+    sh.B = p.B[e];
+    sh.R8 = p.R8[e];
+    sh.NB = 2 * sh.R8 - 1;
+    sh.map_off = p.map_off[e];
+    sh.ray_off = p.ray_off[e];
+    sh.start = es.start;
+    sh.reset = es.start.reset;
+    sh.Px = es.Px;
+    sh.Py = es.Py;
+    sh.ri = es.Px >> 16;
+    sh.rj = es.Py >> 16;
+    sh.col_cell = es.col_cell;
+    sh.c = es.c;
+    sh.s = es.s;
+    sh.gt_cells = es.gt_cells;
+    sh.dmin_meas = es.dmin_meas;
+    sh.dmin_true = es.dmin_true;
+    const int S = p.window;
+    sh.partial = (long long)W * H > (long long)S * S;
+    if (sh.partial) {
+        const int SW = min(S, W), SH = min(S, H);
+        sh.SW = SW;
+        sh.SH = SH;
+        sh.wx0 = min(max(sh.ri - SW / 2, 0), W - SW) & ~7;
+        sh.wy0 = min(max(sh.rj - SH / 2, 0), H - SH);
+    } else {
+        sh.SW = W;
+        sh.SH = H;
+        sh.wx0 = 0;
+        sh.wy0 = 0;
+    }
+}
+
+// Reward, termination and outputs of a finished env (one thread).
+__device__ __forceinline__ void finish_pending(const Step2DParams &p, const EnvShared &sh,
+                                               long long dHq, long long ray_cells) {
+    EnvTotals r;
+    r.dHq = dHq;
+    r.ray_cells = ray_cells;
+    r.gt_cells = sh.gt_cells;
+    r.dmin_meas = sh.dmin_meas;
+    r.dmin_true = sh.dmin_true;
+    finish_env(p, sh.e, sh.W, sh.H, sh.start, sh.col_cell, r);
+}
+
 constexpr int kUnroll = 2;
 
+// One persistent CTA per SM slot takes envs from a queue.  The last warp is
+// the control warp: while the others walk env n it finishes env n-1 (reward,
+// termination, outputs) and loads env n+1's parameters into the other half
+// of a two-slot shared buffer, so neither serial step delays the CTA.
 __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     long long *s_lut = reinterpret_cast<long long *>(smem);           // [clamp_q + 1]
@@ -399,76 +464,26 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     int *s_beam = s_first + ((p.b_max + 3) & ~3);                     // [b_max]
     unsigned *s_win = smem + p.lut_words + 3 * ((p.b_max + 1 + 3) & ~3);
     unsigned *s_near = s_win + p.win_words_max;
-    __shared__ EnvShared sh;
+    __shared__ EnvShared shb[2];
     __shared__ long long r_dh[32];
     __shared__ int r_rc[32];
-    __shared__ int s_next, s_n0;
+    __shared__ long long s_dHq;
+    __shared__ int s_rc, s_n0;
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int nwalk = nt - 32;                       // threads of the walking warps
+    const bool control = warp == nwarps - 1;
     const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
 
     // entropy half table h(|L|), L = 0..clamp_q, shared by every env of the CTA
     for (int q = tid; q <= p.clamp_q; q += nt) s_lut[q] = __ldg(&p.lut[p.clamp_q + q]);
-    if (tid == 0) s_next = (int)atomicAdd(p.queue, 1u);
-    for (;;) {
-        __syncthreads();                 // previous env finished, s_next visible
-        const int item = s_next;
-        __syncthreads();                 // everyone read s_next before it is replaced
-        if (item >= p.E) {
-            // Every CTA grabs exactly one out-of-range item before leaving;
-            // the last CTA to leave re-arms the queue for the next launch.
-            if (tid == 0) {
-                __threadfence();
-                if (atomicAdd(p.queue + 1, 1u) == gridDim.x - 1) {
-                    p.queue[0] = 0u;
-                    p.queue[1] = 0u;
-                    __threadfence();
-                }
-            }
-            break;
-        }
-        if (tid == 0) {
-            const int e = p.order[item];
-            const EnvSense es = reinterpret_cast<const EnvSense *>(p.env_sense)[e];
-            const int W = p.W[e], H = p.H[e];
-            sh.e = e;
-            sh.W = W;
-            sh.H = H;
-            sh.B = p.B[e];
-            sh.R8 = p.R8[e];
-            sh.NB = 2 * sh.R8 - 1;
-            sh.map_off = p.map_off[e];
-            sh.ray_off = p.ray_off[e];
-            sh.start = es.start;
-            sh.reset = es.start.reset;
-            sh.Px = es.Px;
-            sh.Py = es.Py;
-            sh.ri = es.Px >> 16;
-            sh.rj = es.Py >> 16;
-            sh.col_cell = es.col_cell;
-            sh.c = es.c;
-            sh.s = es.s;
-            sh.gt_cells = es.gt_cells;
-            sh.dmin_meas = es.dmin_meas;
-            sh.dmin_true = es.dmin_true;
-            const int S = p.window;
-            sh.partial = (long long)W * H > (long long)S * S;
-            if (sh.partial) {
-                const int SW = min(S, W), SH = min(S, H);
-                sh.SW = SW;
-                sh.SH = SH;
-                sh.wx0 = min(max(sh.ri - SW / 2, 0), W - SW) & ~7;
-                sh.wy0 = min(max(sh.rj - SH / 2, 0), H - SH);
-            } else {
-                sh.SW = W;
-                sh.SH = H;
-                sh.wx0 = 0;
-                sh.wy0 = 0;
-            }
-            s_next = (int)atomicAdd(p.queue, 1u);
-        }
-        __syncthreads();
+    if (tid == 0) load_env(p, (int)atomicAdd(p.queue, 1u), shb[0]);
+    __syncthreads();
+    int it = 0;
+    for (;; ++it) {
+        const EnvShared &sh = shb[it & 1];
+        if (sh.e < 0) break;                         // uniform: read after a barrier
 
         // ---- reset, clear counters, chunk table --------------------------------
         const int e = sh.e, W = sh.W, H = sh.H, B = sh.B;
@@ -523,35 +538,41 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         }
         __syncthreads();
 
-        // ---- belief walks, chunked ---------------------------------------------
+        // ---- belief walks, chunked (control warp: finish n-1, load n+1) ---------
         int rc = 0;
-        const int total = s_n0 + s_pref[B];
-        for (int q = tid; q < total; q += nt) {
-            if (q < s_n0) {
-                // first chunk of a beam: may touch the 32-bit block near the robot
-                const int b = s_beam[q];
-                const int code = p.ray_code[sh.ray_off + b];
-                rc += sh.partial ? walk_chunk<true, true>(p, sh, b, code, 0, s_win, s_near)
-                                 : walk_chunk<false, true>(p, sh, b, code, 0, s_win, s_near);
-            } else {
-                // later chunks start >= chunk >= 2*R8 steps out: after s steps a walk
-                // is >= s/2 cells (Chebyshev) from the robot, outside the near block
-                const int qq = q - s_n0;
-                int lo = 0, hi = B - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pref[mid] <= qq) lo = mid;
-                    else hi = mid - 1;
+        if (control) {
+            if (lane == 0) {
+                if (it > 0) finish_pending(p, shb[(it - 1) & 1], s_dHq, s_rc);
+                load_env(p, (int)atomicAdd(p.queue, 1u), shb[(it + 1) & 1]);
+            }
+        } else {
+            const int total = s_n0 + s_pref[B];
+            for (int q = tid; q < total; q += nwalk) {
+                if (q < s_n0) {
+                    // first chunk of a beam: may touch the 32-bit block near the robot
+                    const int b = s_beam[q];
+                    const int code = p.ray_code[sh.ray_off + b];
+                    rc += sh.partial ? walk_chunk<true, true>(p, sh, b, code, 0, s_win, s_near)
+                                     : walk_chunk<false, true>(p, sh, b, code, 0, s_win, s_near);
+                } else {
+                    // later chunks start >= chunk >= 2*R8 steps out: after s steps a walk
+                    // is >= s/2 cells (Chebyshev) from the robot, outside the near block
+                    const int qq = q - s_n0;
+                    int lo = 0, hi = B - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_pref[mid] <= qq) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int b = lo;
+                    const int code = p.ray_code[sh.ray_off + b];
+                    const int s0 = (qq - s_pref[b] + 1) * p.chunk;
+                    rc += sh.partial ? walk_chunk<true, false>(p, sh, b, code, s0, s_win, s_near)
+                                     : walk_chunk<false, false>(p, sh, b, code, s0, s_win, s_near);
                 }
-                const int b = lo;
-                const int code = p.ray_code[sh.ray_off + b];
-                const int s0 = (qq - s_pref[b] + 1) * p.chunk;
-                rc += sh.partial ? walk_chunk<true, false>(p, sh, b, code, s0, s_win, s_near)
-                                 : walk_chunk<false, false>(p, sh, b, code, s0, s_win, s_near);
             }
         }
         __syncthreads();
-
         // ---- apply counters to the log-odds -------------------------------------
         long long dh = 0;
         short *Lenv = p.belief + sh.map_off;
@@ -631,7 +652,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             }
         }
 
-        // ---- reductions, reward, observation ------------------------------------
+        // ---- reductions (the finish runs on the control warp next round) -------
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             dh += __shfl_down_sync(0xffffffffu, dh, o);
@@ -641,23 +662,32 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             r_dh[warp] = dh;
             r_rc[warp] = rc;
         }
-        __syncthreads();
-        if (tid == 0) {
-            EnvTotals r;
-            r.dHq = 0;
-            r.ray_cells = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                r.dHq += r_dh[w];
-                r.ray_cells += r_rc[w];
-            }
-            r.gt_cells = sh.gt_cells;
-            r.dmin_meas = sh.dmin_meas;
-            r.dmin_true = sh.dmin_true;
-            finish_env(p, e, W, H, sh.start, sh.col_cell, r);
-        }
         if (p.out_obs) {
             float *o = p.out_obs + (long long)e * (p.b_max + 2);
             for (int b = B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long a = 0;
+            int c = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                a += r_dh[w];
+                c += r_rc[w];
+            }
+            s_dHq = a;
+            s_rc = c;
+        }
+        __syncthreads();                 // s_dHq/s_rc and shb[(it+1)&1] visible
+    }
+    if (tid == 0) {
+        if (it > 0) finish_pending(p, shb[(it - 1) & 1], s_dHq, s_rc);
+        // Every CTA took exactly one out-of-range item; the last CTA to leave
+        // re-arms the queue for the next launch.
+        __threadfence();
+        if (atomicAdd(p.queue + 1, 1u) == gridDim.x - 1) {
+            p.queue[0] = 0u;
+            p.queue[1] = 0u;
+            __threadfence();
         }
     }
 }
@@ -757,18 +787,24 @@ cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm) {
 // Integration (one thread per env), sensing (one CTA per bundle of
 // kSenseBlock beams) and the persistent per-env update CTAs.
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s) {
+                          cudaStream_t s, const cudaEvent_t *ev) {
+    cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
     integrate2d_kernel<<<(p.E + 127) / 128, 128, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;
     if (p.n_bundles > 0) {
         const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
         sense2d_kernel<<<p.n_bundles, p.sense_block, gt_bytes, s>>>(p);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
     }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    if (e != cudaSuccess) return e;
     update2d_kernel<<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+    return e;
 }
 
 cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,

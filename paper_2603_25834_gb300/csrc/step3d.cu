@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                     gc += cells;
                     z = z_true;
                     if (hit) {
-                        const float g = det_gauss(p.key, (unsigned)e, (unsigned)sh.start.gstep, (unsigned)b);
+                        const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)sh.start.gstep, (unsigned)b);
                         z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
                     }
                     const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
@@ -372,9 +372,13 @@ cudaError_t step3d_occupancy(int block, size_t smem, int *ctas_per_sm) {
 }
 
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s) {
+                          cudaStream_t s, const cudaEvent_t *ev) {
+    cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
     step3d_kernel<<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    return e;
 }
 
 }  // namespace aslam

@@ -131,10 +131,12 @@ def plain_1env(seed=BASE_SEED, K=16):
     return _pack_batch([w], [90], 0.1, K, [np.random.default_rng(seed + 10_000_000)])
 
 
-def paper_scale(E=750, W=256, B=360, seed=BASE_SEED, K=16):
-    """E envs of WxW at 0.05 m with 20-40 rectangles and 5-15 discs, B beams."""
+def paper_scale(E=750, W=256, B=360, seed=BASE_SEED, K=16, envs=None):
+    """E envs of WxW at 0.05 m with 20-40 rectangles and 5-15 discs, B beams.
+    `envs` (default all): the indices of the envs to build, e.g. one rank's
+    contiguous share; env e is the same world wherever it is built."""
     worlds, rs = [], []
-    for e in range(E):
+    for e in (range(E) if envs is None else envs):
         rng = np.random.default_rng(seed + e)
         scale = (W / 256.0) ** 2
         worlds.append(make_world_2d(
@@ -142,16 +144,25 @@ def paper_scale(E=750, W=256, B=360, seed=BASE_SEED, K=16):
             n_rect=(max(1, round(20 * scale)), max(1, round(40 * scale))), rect_side=(0.2, 2.0),
             n_disc=(max(0, round(5 * scale)), max(0, round(15 * scale))), disc_r=(0.1, 0.6)))
         rs.append(np.random.default_rng(seed + 10_000_000 + e))
-    return _pack_batch(worlds, [B] * E, 0.05, K, rs)
+    return _pack_batch(worlds, [B] * len(worlds), 0.05, K, rs)
 
 
-def uneven(E=4096, sides=(128, 256, 384, 512), beams=(180, 360, 720), seed=BASE_SEED, K=8):
-    """E envs with map side and beam count drawn uniformly from the given sets."""
+def uneven_shapes(E=4096, sides=(128, 256, 384, 512), beams=(180, 360, 720), seed=BASE_SEED):
+    """Map side and beam count of each of the E envs of `uneven`."""
     pick = np.random.default_rng(seed - 1)
     side = pick.choice(np.asarray(sides), size=E)
     nb = pick.choice(np.asarray(beams), size=E)
+    return side, nb
+
+
+def uneven(E=4096, sides=(128, 256, 384, 512), beams=(180, 360, 720), seed=BASE_SEED, K=8,
+           envs=None):
+    """E envs with map side and beam count drawn uniformly from the given sets
+    (`envs`: the indices to build, default all)."""
+    side, nb = uneven_shapes(E, sides, beams, seed)
+    envs = range(E) if envs is None else envs
     worlds, rs = [], []
-    for e in range(E):
+    for e in envs:
         rng = np.random.default_rng(seed + e)
         s = int(side[e])
         scale = (s / 256.0) ** 2
@@ -160,7 +171,7 @@ def uneven(E=4096, sides=(128, 256, 384, 512), beams=(180, 360, 720), seed=BASE_
             n_rect=(max(1, round(20 * scale)), max(1, round(40 * scale))), rect_side=(0.2, 2.0),
             n_disc=(max(0, round(5 * scale)), max(0, round(15 * scale))), disc_r=(0.1, 0.6)))
         rs.append(np.random.default_rng(seed + 10_000_000 + e))
-    return _pack_batch(worlds, nb, 0.05, K, rs)
+    return _pack_batch(worlds, [int(nb[e]) for e in envs], 0.05, K, rs)
 
 
 def custom_2d(occs, beams, res, spawn):
@@ -262,15 +273,17 @@ def make_world_3d(W, H, D, res, rng, n_box=(8, 16), box_side=(0.5, 3.0), box_h=(
     return occ
 
 
-def voxel_batch(E=512, W=128, H=128, D=32, res=0.1, n_az=512, seed=BASE_SEED, K=8, clearance=0.3):
+def voxel_batch(E=512, W=128, H=128, D=32, res=0.1, n_az=512, seed=BASE_SEED, K=8, clearance=0.3,
+                envs=None):
     """E voxel worlds with floor, boxes and pillars (counts scaled to the floor
-    area of a 128 x 128 x 0.1 m world); spawns on free columns."""
+    area of a 128 x 128 x 0.1 m world); spawns on free columns (`envs`: the
+    indices to build, default all)."""
     grids, spawns = [], []
     scale = (W * H * res * res) / (128 * 128 * 0.01)
     n_box = (int(round(8 * scale)), max(int(round(16 * scale)), 1))
     n_pillar = (int(round(4 * scale)), max(int(round(10 * scale)), 1))
     side = (0.5, max(0.6, min(3.0, 0.4 * min(W, H) * res)))
-    for e in range(E):
+    for e in (range(E) if envs is None else envs):
         occ = make_world_3d(W, H, D, res, np.random.default_rng(seed + e), n_box=n_box,
                             box_side=side, n_pillar=n_pillar)
         grids.append(occ)
@@ -279,6 +292,7 @@ def voxel_batch(E=512, W=128, H=128, D=32, res=0.1, n_az=512, seed=BASE_SEED, K=
                                      clearance=clearance))
     off = np.zeros(E + 1, np.int64)
     off[1:] = np.cumsum([g.size for g in grids])
-    return Batch3DInputs(np.full(E, W, np.int32), np.full(E, H, np.int32), np.full(E, D, np.int32),
-                         np.full(E, n_az, np.int32), float(res),
+    n = len(grids)
+    return Batch3DInputs(np.full(n, W, np.int32), np.full(n, H, np.int32), np.full(n, D, np.int32),
+                         np.full(n, n_az, np.int32), float(res),
                          np.concatenate([g.reshape(-1) for g in grids]), off, np.stack(spawns))

@@ -213,3 +213,19 @@ def test_large_noise_moves_endpoint_far_from_hit(aslam_gpu, orc, sigma, window):
     acts = synth.random_actions(4, 4, 60)
     run_parity(aslam_gpu, orc, inp, acts, tag="noise-%g-%d" % (sigma, window), r_max_m=12.0,
                noise_sigma_m=sigma, gpu_kw=dict(window_cells=window))
+
+
+def test_env_base_shard_draws_the_global_noise(aslam_gpu, orc):
+    """Envs [3, 6) of a 6-env set in a batch of their own with env_base = 3
+    match the oracle stepping those envs under their global ids 3..5."""
+    part = synth.paper_scale(E=6, W=128, B=90, seed=55, envs=range(3, 6))
+    acts = synth.random_actions(5, 6, 4)[:, 3:]
+    gb = aslam_gpu.Batch2D(part, flags=aslam_gpu.FLAG_DEBUG, env_base=3, r_max_m=6.0,
+                           noise_sigma_m=0.02)
+    ob = orc.OracleBatch2D(part, env_ids=np.arange(3, 6), r_max=6.0, sigma=0.02)
+    for s in range(acts.shape[0]):
+        gb.step(torch.from_numpy(acts[s]).cuda())
+        torch.cuda.synchronize()
+        compare_step(gb, ob, ob.step(acts[s], counts=True), tag="env_base step %d" % s)
+    with pytest.raises(aslam_gpu.AslamError):
+        aslam_gpu.Batch2D(part, env_base=-1, r_max_m=6.0)
