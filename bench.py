@@ -261,7 +261,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_scale",
-                    choices=["paper_scale", "uneven", "diff", "3d"])
+                    choices=["paper_scale", "paper_sensor", "uneven", "diff", "3d"])
     ap.add_argument("--envs", type=int, default=750)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -315,6 +315,20 @@ def main():
                         reward="composite Eq. 7-17", l2="flushed (256 MiB write) between timed steps",
                         mean_beams=float(nb.mean()),
                         mean_cells=float((side.astype(np.int64) ** 2).mean()))
+    elif args.workload == "paper_sensor":
+        # the paper's LiDAR (Sec. IV-A): 128 rays over the front 180 degrees,
+        # 0.1-10 m, two decimal places; v in (0, 0.4) (Eq. 4)
+        E_all = args.envs * world
+        lo, hi = shard.env_range(np.ones(E_all, np.int64), world, rank)
+        inp = synth.paper_scale(E=E_all, B=128, envs=range(lo, hi))
+        cfg_kw = dict(r_max_m=10.0, noise_sigma_m=0.01, fov_rad=math.pi, r_min_m=0.1,
+                      range_decimals=2, v_max=0.4)
+        workload = dict(workload="paper_sensor: %d envs per GPU x 256^2 cells @0.05 m, 128 beams "
+                                 "over the front 180 deg, 0.1-10 m, 2 decimals, sigma 0.01 m, "
+                                 "v <= 0.4 m/s" % (E_all // world),
+                        envs=E_all, res_m=0.05, r_max_m=10.0, r_min_m=0.1, range_decimals=2,
+                        noise_sigma_m=0.01, reward="composite Eq. 7-17",
+                        l2="flushed (256 MiB write) between timed steps")
     else:
         E_all = args.envs * world
         lo, hi = shard.env_range(np.ones(E_all, np.int64), world, rank)
@@ -328,7 +342,8 @@ def main():
     if not args.no_autotune and not args.threads and not args.window:
         tuned = batch.autotune()
     K, W = args.steps, args.warmup
-    acts = torch.from_numpy(synth.random_actions(K + W, E_all, 7)[:, lo:hi].copy()).to(dev)
+    v_max = cfg_kw.get("v_max", 0.5)
+    acts = torch.from_numpy(synth.random_actions(K + W, E_all, 7, v_max=v_max)[:, lo:hi].copy()).to(dev)
     uu = torch.from_numpy(synth.random_uncertainty(K + W, E_all, 8)[:, lo:hi].copy()).to(dev)
     reward = torch.empty(E, device=dev)
     obs = torch.empty(E, batch.b_max + 2, device=dev)
@@ -392,7 +407,7 @@ def main():
 
     # ---- end to end through the public API with host buffers ----
     K2 = min(args.e2e_steps, K)
-    h_acts = torch.from_numpy(synth.random_actions(K2, E_all, 17)[:, lo:hi].copy()).pin_memory()
+    h_acts = torch.from_numpy(synth.random_actions(K2, E_all, 17, v_max=v_max)[:, lo:hi].copy()).pin_memory()
     h_u = torch.from_numpy(synth.random_uncertainty(K2, E_all, 18)[:, lo:hi].copy()).pin_memory()
     h_rew = torch.empty(K2, E).pin_memory()
     h_obs = torch.empty(K2, E, batch.b_max + 2).pin_memory()

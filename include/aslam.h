@@ -122,6 +122,14 @@ typedef struct {
      * [lo, hi) of a larger set, created with env_base = lo, draws the same
      * noise as those envs do in one batch of the whole set (default 0). */
     int32_t env_base;
+    /* Sensor quantisation of Sec. IV-A ("a minimum range of 0.1 m ... two
+     * decimal places of precision").  A returned beam's measured range is
+     * z = clip(round(z_true + sigma*n, range_decimals), r_min_m, r_max_m),
+     * the rounding done as rint(z * 10^d) / 10^d in fp32 (half to even);
+     * range_decimals = -1 (default) skips it, r_min_m = 0 (default) clips
+     * at 0.  A beam with no return reports r_max_m unrounded. */
+    float r_min_m;                 /* 0 <= r_min_m <= r_max_m */
+    int32_t range_decimals;        /* -1 (off) or 0..6 */
 } aslam_config;
 
 #define ASLAM_MAX_BEAMS 1024
@@ -227,6 +235,19 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream);
 aslam_status aslam_state_bytes(aslam_batch *b, size_t *bytes);
 aslam_status aslam_save_state(aslam_batch *b, void *h_buf, size_t bytes, void *stream);
 aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, void *stream);
+
+/*
+ * Uncertainty bridge for SLAM-agnostic fine-tuning (Sec. III-G, Eq. 21-22):
+ * alpha = min(1, t / t_bridge) (fp64, rounded once to fp32) and, per env,
+ * U = alpha * U_new + (1 - alpha) * U_old in fp32.  d_u_old / d_u_new:
+ * device float [E] (the training backend's and the external estimator's
+ * uncertainty); t >= 0 is the fine-tuning step, t_bridge >= 1.  Writes
+ * d_u_out [E] (optional) and/or the U slot (column b_max + 1) of the
+ * observation rows d_obs [E, b_max + 2] (optional); at least one is needed.
+ * The reward is not touched: the bridge changes only what the policy sees.
+ */
+aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d_u_new, int64_t t,
+                            int64_t t_bridge, float *d_u_out, float *d_obs, void *stream);
 
 /*
  * Per-kernel device timing of aslam_step / aslam_step_fused (graph replays

@@ -67,7 +67,8 @@ class OrcCfg(C.Structure):
         ("t_episode", C.c_int32), ("pad0", C.c_int32), ("seed", C.c_uint64),
         ("res", C.c_float), ("r_max", C.c_float), ("fov", C.c_float), ("sigma", C.c_float),
         ("dt", C.c_float), ("v_max", C.c_float), ("w_max", C.c_float), ("d_crash", C.c_float),
-        ("d_full", C.c_float), ("visit_cell", C.c_float),
+        ("d_full", C.c_float), ("visit_cell", C.c_float), ("r_min", C.c_float),
+        ("dec_scale", C.c_float),
         ("logodds_scale", C.c_double),
         ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
@@ -94,7 +95,8 @@ class OrcCfg3D(C.Structure):
         ("seed", C.c_uint64),
         ("res", C.c_float), ("r_max", C.c_float), ("sigma", C.c_float), ("dt", C.c_float),
         ("v_max", C.c_float), ("w_max", C.c_float), ("d_crash", C.c_float), ("d_full", C.c_float),
-        ("visit_cell", C.c_float), ("sensor_z", C.c_float),
+        ("visit_cell", C.c_float), ("sensor_z", C.c_float), ("r_min", C.c_float),
+        ("dec_scale", C.c_float),
         ("el_min", C.c_double), ("el_max", C.c_double), ("logodds_scale", C.c_double),
         ("lam_col", C.c_double), ("lam_explore", C.c_double), ("lam_abs", C.c_double),
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
@@ -132,6 +134,12 @@ def _declare(L):
     L.orc_walk2d.restype = C.c_int
     L.orc_beam_dirs.argtypes = [C.c_int, C.c_double, P, P]
     L.orc_ray_setup.argtypes = [C.c_float] * 7 + [C.POINTER(C.c_int32)] * 4
+    L.orc_measured_range.argtypes = [C.c_float] * 6
+    L.orc_measured_range.restype = C.c_float
+    L.orc_bridge_alpha.argtypes = [C.c_int64, C.c_int64]
+    L.orc_bridge_alpha.restype = C.c_float
+    L.orc_bridge_u.argtypes = [C.c_float, C.c_float, C.c_float]
+    L.orc_bridge_u.restype = C.c_float
     L.orc_cell_entropy.argtypes = [C.c_double]
     L.orc_cell_entropy.restype = C.c_double
     L.orc_map_entropy.argtypes = [P, C.c_int64, C.c_double]
@@ -218,8 +226,28 @@ def visit_dims(W, H, res, vc):
     return a.value, b.value
 
 
+def dec_scale(decimals):
+    """10^decimals as an fp32 scale of the range rounding (0: no rounding)."""
+    return 0.0 if decimals is None or decimals < 0 else float(np.float32(10.0 ** int(decimals)))
+
+
+def measured_range(z_true, g, sigma, r_min, r_max, decimals=-1):
+    return lib().orc_measured_range(C.c_float(z_true), C.c_float(g), C.c_float(sigma),
+                                    C.c_float(r_min), C.c_float(r_max),
+                                    C.c_float(dec_scale(decimals)))
+
+
+def bridge_u(u_old, u_new, t, t_bridge):
+    """Bridged uncertainty (fp32 arrays) at fine-tuning step t."""
+    a = lib().orc_bridge_alpha(int(t), int(t_bridge))
+    uo = np.asarray(u_old, np.float32).ravel()
+    un = np.asarray(u_new, np.float32).ravel()
+    return np.array([lib().orc_bridge_u(float(x), float(y), a) for x, y in zip(uo, un)],
+                    np.float32)
+
+
 # ---------------------------------------------------------------- batched 2-D step
-DEFAULTS = dict(r_max=5.0, fov=0.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0,
+DEFAULTS = dict(r_max=5.0, r_min=0.0, decimals=-1, fov=0.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0,
                 hit_q=870, miss_q=-410, clamp_q=3584, logodds_scale=1.0 / 1024.0,
                 t_episode=2048, d_crash=0.15, d_full=0.5, visit_cell=0.5,
                 lam_col=10.0, lam_explore=1.0, lam_abs=0.1, lam_delta=1.0, kappa=0.05,
@@ -264,7 +292,8 @@ class OracleBatch2D:
             n_envs=E, b_max=self.b_max, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"],
             t_episode=p["t_episode"], pad0=0, seed=p["seed"], res=inputs.res,
-            r_max=p["r_max"], fov=p["fov"], sigma=p["sigma"], dt=p["dt"], v_max=p["v_max"],
+            r_max=p["r_max"], r_min=p["r_min"], dec_scale=dec_scale(p["decimals"]),
+            fov=p["fov"], sigma=p["sigma"], dt=p["dt"], v_max=p["v_max"],
             w_max=p["w_max"], d_crash=p["d_crash"], d_full=p["d_full"],
             visit_cell=p["visit_cell"], logodds_scale=p["logodds_scale"],
             lam_col=p["lam_col"], lam_explore=p["lam_explore"], lam_abs=p["lam_abs"],
@@ -364,7 +393,7 @@ def walk3d(Px, Py, Pz, Dx, Dy, Dz, T, W, H, D):
     return cells[:n].copy(), en[:n].copy(), ea[:n].copy(), bool(left.value)
 
 
-DEFAULTS3D = dict(r_max=20.0, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0, hit_q=870, miss_q=-410,
+DEFAULTS3D = dict(r_max=20.0, r_min=0.0, decimals=-1, sigma=0.0, dt=0.1, v_max=0.5, w_max=1.0, hit_q=870, miss_q=-410,
                   clamp_q=3584, logodds_scale=1.0 / 1024.0, t_episode=2048, d_crash=0.15,
                   d_full=0.5, visit_cell=0.5, sensor_z=0.5, el_min=-15.0 * np.pi / 180,
                   el_max=15.0 * np.pi / 180, lam_col=10.0, lam_explore=1.0, lam_abs=0.1,
@@ -412,7 +441,8 @@ class OracleBatch3D:
         self.cfg = OrcCfg3D(
             n_envs=E, n_rings=self.R, n_az=self.A, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"], t_episode=p["t_episode"],
-            seed=p["seed"], res=inputs.res, r_max=p["r_max"], sigma=p["sigma"], dt=p["dt"],
+            seed=p["seed"], res=inputs.res, r_max=p["r_max"], r_min=p["r_min"],
+            dec_scale=dec_scale(p["decimals"]), sigma=p["sigma"], dt=p["dt"],
             v_max=p["v_max"], w_max=p["w_max"], d_crash=p["d_crash"], d_full=p["d_full"],
             visit_cell=p["visit_cell"], sensor_z=p["sensor_z"], el_min=p["el_min"],
             el_max=p["el_max"], logodds_scale=p["logodds_scale"], lam_col=p["lam_col"],

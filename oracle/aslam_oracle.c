@@ -11,7 +11,10 @@
  *     robot (Sec. III-C action space Eq. 4; Sec. IV-A robot; dt = 0.1 s);
  *   - the LiDAR sensor of Sec. IV-A: each beam's range is the distance to
  *     the first occupied ground-truth cell along the beam, plus Gaussian
- *     noise N(0, sigma^2), clipped to [0, r_max];
+ *     noise N(0, sigma^2), optionally rounded to a number of decimal places
+ *     (Sec. IV-A: "two decimal places of precision"), clipped to
+ *     [r_min, r_max] (Sec. IV-A: minimum range 0.1 m); a beam that meets no
+ *     obstacle within r_max reports r_max;
  *   - the log-odds occupancy-grid update of Sec. III-D: cells the beam
  *     crosses before its measured endpoint receive a "miss" increment, the
  *     endpoint cell a "hit" increment when the beam returned, and every cell
@@ -341,6 +344,8 @@ typedef struct {
     int32_t pad0;
     uint64_t seed;
     float res, r_max, fov, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
+    float r_min;               /* minimum range (m); returned ranges are clipped up to it */
+    float dec_scale;           /* 10^decimals of the range rounding, 0 for none */
     double logodds_scale;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     const int32_t *map_w, *map_h, *n_beams;
@@ -370,6 +375,37 @@ typedef struct {
     float *obs;                /* [E, b_max + 2] */
     int64_t *ray_cells, *gt_cells;
 } orc_out;
+
+/* Measured range of a returned beam (Sec. IV-A sensor): noise, then rounding
+ * to 1/dec_scale m (round half to even on the scaled value) when dec_scale
+ * > 0, then the clip to [r_min, r_max].  fp32, one IEEE operation at a time. */
+float orc_measured_range(float z_true, float g, float sigma, float r_min, float r_max,
+                         float dec_scale)
+{
+    float z = z_true + sigma * g;
+    if (dec_scale > 0.0f) {
+        float scaled = z * dec_scale;
+        z = rintf(scaled) / dec_scale;
+    }
+    return fminf(fmaxf(z, r_min), r_max);
+}
+
+/* Uncertainty bridge of the SLAM-agnostic fine-tuning wrapper (Sec. III-G,
+ * Eq. 21-22): alpha_t = min(1, t / T_bridge), evaluated in
+ * fp64 and rounded once to fp32; U = alpha * U_new + (1 - alpha) * U_old in
+ * fp32. */
+float orc_bridge_alpha(int64_t t, int64_t t_bridge)
+{
+    double a = (double)t / (double)t_bridge;
+    return (float)(a < 1.0 ? a : 1.0);
+}
+
+float orc_bridge_u(float u_old, float u_new, float alpha)
+{
+    float w_new = alpha * u_new;
+    float w_old = (1.0f - alpha) * u_old;
+    return w_new + w_old;
+}
 
 void orc_visit_dims(int32_t W, int32_t H, float res, float vc, int32_t *Vw, int32_t *Vh)
 {
@@ -469,8 +505,8 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
             if (hit) {
                 uint32_t eid = cfg->env_id ? (uint32_t)cfg->env_id[e] : (uint32_t)e;
                 float g = orc_gauss(cfg->seed, eid, (uint32_t)st->g[e], (uint32_t)b);
-                z = z_true + cfg->sigma * g;
-                z = fminf(fmaxf(z, 0.0f), cfg->r_max);
+                z = orc_measured_range(z_true, g, cfg->sigma, cfg->r_min, cfg->r_max,
+                                       cfg->dec_scale);
             }
             int32_t Tz = hit ? orc_q16_of_range(z, cfg->res) : Tmax;
             nc = orc_walk2d(Px, Py, Dx, Dy, Tz, W, H, cells, en, ea, cap, &left);

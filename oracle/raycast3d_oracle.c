@@ -25,6 +25,8 @@ void orc_sincosf(float x, float *s, float *c);
 float orc_gauss(uint64_t seed, uint32_t env, uint32_t step, uint32_t beam);
 double orc_cell_entropy(double l);
 void orc_visit_dims(int32_t W, int32_t H, float res, float vc, int32_t *Vw, int32_t *Vh);
+float orc_measured_range(float z_true, float g, float sigma, float r_min, float r_max,
+                         float dec_scale);
 
 static int64_t o3_floordiv(int64_t a, int64_t b)
 {
@@ -111,6 +113,7 @@ typedef struct {
     int32_t hit_q, miss_q, clamp_q, t_episode;
     uint64_t seed;
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell, sensor_z;
+    float r_min, dec_scale;    /* as in the 2-D sensor */
     double el_min, el_max, logodds_scale;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     const int32_t *map_w, *map_h, *map_d;
@@ -232,7 +235,8 @@ int orc_step3d(const orc_cfg3d *cfg, orc_state3d *st, const float *actions, cons
                 if (hit) {
                     uint32_t eid = cfg->env_id ? (uint32_t)cfg->env_id[e] : (uint32_t)e;
                     float g = orc_gauss(cfg->seed, eid, (uint32_t)st->g[e], (uint32_t)b);
-                    z = fminf(fmaxf(z_true + cfg->sigma * g, 0.0f), cfg->r_max);
+                    z = orc_measured_range(z_true, g, cfg->sigma, cfg->r_min, cfg->r_max,
+                                           cfg->dec_scale);
                 }
                 int32_t Tz = hit ? (int32_t)lrintf((z / cfg->res) * 65536.0f) : Tmax;
                 nc = orc_walk3d(Px, Py, Pz, Dx, Dy, Dz, Tz, W, H, Dd, cells, en, ea, cap, &left);

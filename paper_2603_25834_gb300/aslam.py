@@ -56,6 +56,7 @@ class AslamConfig(C.Structure):
         ("seed", C.c_uint64), ("flags", C.c_int32), ("window_cells", C.c_int32),
         ("h_map_d", P), ("n_rings", C.c_int32), ("sensor_z_m", C.c_float),
         ("elev_min_rad", C.c_float), ("elev_max_rad", C.c_float), ("env_base", C.c_int32),
+        ("r_min_m", C.c_float), ("range_decimals", C.c_int32),
     ]
 
 
@@ -92,6 +93,7 @@ EXPORTS = {
     "aslam_state_bytes": ([P, C.POINTER(C.c_size_t)], C.c_int),
     "aslam_save_state": ([P, P, C.c_size_t, P], C.c_int),
     "aslam_load_state": ([P, P, C.c_size_t, P], C.c_int),
+    "aslam_bridge_u": ([P, P, P, C.c_int64, C.c_int64, P, P, P], C.c_int),
     "aslam_profile_begin": ([P, C.c_int32], C.c_int),
     "aslam_profile_end": ([P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "aslam_kernel_name": ([P, C.c_int32], C.c_char_p),
@@ -159,7 +161,7 @@ def config_defaults() -> AslamConfig:
 
 
 _FLOAT_KEYS = {"res_m", "r_max_m", "fov_rad", "noise_sigma_m", "dt_s", "v_max", "w_max",
-               "sensor_z_m", "elev_min_rad", "elev_max_rad",
+               "sensor_z_m", "elev_min_rad", "elev_max_rad", "r_min_m",
                "d_crash", "d_full", "visit_cell_m", "logodds_scale", "lam_col", "lam_explore",
                "lam_abs", "lam_delta", "kappa", "u_hi"}
 
@@ -319,6 +321,16 @@ class Batch2D:
         best = (C.c_int32 * 2)()
         _check(self.lib.aslam_autotune(self.handle, best, _stream(stream)), self.handle)
         return int(best[0]), int(best[1])
+
+    def bridge_u(self, u_old, u_new, t, t_bridge, out=None, obs=None, stream=None):
+        """Blend the uncertainty of two estimators for fine-tuning step t (Eq. 21-22);
+        writes `out` (allocated when both out and obs are None) and/or obs[:, b_max+1]."""
+        if out is None and obs is None:
+            out = torch.empty(self.E, dtype=torch.float32, device=self.device)
+        _check(self.lib.aslam_bridge_u(self.handle, _dptr(u_old), _dptr(u_new), int(t),
+                                       int(t_bridge), _dptr(out), _dptr(obs), _stream(stream)),
+               self.handle)
+        return out
 
     def profile_begin(self, max_steps):
         """Time each kernel of the next max_steps steps with CUDA events."""

@@ -106,6 +106,9 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (!(c->dt_s >= 0.0f) || !(c->v_max >= 0.0f) || !(c->w_max >= 0.0f))
         return fail("dt_s, v_max, w_max must be >= 0");
     if (!(c->noise_sigma_m >= 0.0f)) return fail("noise_sigma_m must be >= 0");
+    if (!(c->r_min_m >= 0.0f) || !(c->r_min_m <= c->r_max_m))
+        return fail("r_min_m must be in [0, r_max_m]");
+    if (c->range_decimals < -1 || c->range_decimals > 6) return fail("range_decimals out of [-1, 6]");
     if (c->l_clamp_q < 1 || c->l_clamp_q > 8192) return fail("l_clamp_q out of [1, 8192]");
     if (std::abs(c->l_hit_q) > 32767 || std::abs(c->l_miss_q) > 32767)
         return fail("|l_hit_q|, |l_miss_q| must be <= 32767");
@@ -274,6 +277,20 @@ T *at(aslam_batch *b, size_t off) {
     return reinterpret_cast<T *>(b->ws + off);
 }
 
+}  // namespace
+
+namespace aslam {
+// 10^d as an fp32 scale of the range rounding (exact for d <= 10), 0 for none.
+float range_scale(int d) {
+    if (d < 0) return 0.0f;
+    float s = 1.0f;
+    for (int i = 0; i < d; ++i) s *= 10.0f;
+    return s;
+}
+}  // namespace aslam
+
+namespace {
+
 int step_kernels(const aslam_batch *b) {
     return b->hi.dims == 3 ? kStep3DKernels : kStep2DKernels;
 }
@@ -423,6 +440,8 @@ aslam_status aslam_config_init(aslam_config *c) {
     c->kappa = 0.05;
     c->u_hi = 1.0;
     c->seed = 20260325ull;
+    c->r_min_m = 0.0f;
+    c->range_decimals = -1;
     return ASLAM_OK;
 }
 
@@ -501,6 +520,8 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.res = cfg->res_m;
         p.r_max = cfg->r_max_m;
         p.sigma = cfg->noise_sigma_m;
+        p.r_min = cfg->r_min_m;
+        p.dec_scale = range_scale(cfg->range_decimals);
         p.dt = cfg->dt_s;
         p.v_max = cfg->v_max;
         p.w_max = cfg->w_max;
@@ -895,6 +916,20 @@ aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, v
         src += r.bytes;
     }
     CK(cudaStreamSynchronize((cudaStream_t)stream), "load synchronize");
+    return ASLAM_OK;
+}
+
+aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d_u_new, int64_t t,
+                            int64_t t_bridge, float *d_u_out, float *d_obs, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!d_u_old || !d_u_new) return fail_b(b, ASLAM_ERR_INVALID_ARG, "d_u_old / d_u_new is NULL");
+    if (!d_u_out && !d_obs) return fail_b(b, ASLAM_ERR_INVALID_ARG, "no output (d_u_out, d_obs)");
+    if (t < 0 || t_bridge < 1) return fail_b(b, ASLAM_ERR_INVALID_ARG, "need t >= 0 and t_bridge >= 1");
+    // alpha_t = min(1, t / T_bridge) (Eq. 21), in fp64, rounded once to fp32
+    const double a = (double)t / (double)t_bridge;
+    const float alpha = (float)(a < 1.0 ? a : 1.0);
+    CK(launch_bridge_u(d_u_old, d_u_new, alpha, b->hi.E, d_u_out, d_obs, b->hi.b_max + 2,
+                       b->hi.b_max + 1, (cudaStream_t)stream), "aslam_bridge_u");
     return ASLAM_OK;
 }
 

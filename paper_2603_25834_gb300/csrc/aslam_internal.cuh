@@ -119,6 +119,17 @@ __device__ __forceinline__ float det_gauss(uint2 key, unsigned env, unsigned ste
     return fmul(rad, det_cos2pi(u2));
 }
 
+// Measured range of a returned beam (Sec. IV-A sensor): Gaussian noise, then
+// rounding to 1/dec_scale m (half to even on the scaled value) when
+// dec_scale > 0, then the clip to [r_min, r_max].  One IEEE fp32 operation
+// at a time.
+__device__ __forceinline__ float measured_range(float z_true, float g, float sigma, float r_min,
+                                                float r_max, float dec_scale) {
+    float z = fadd(z_true, fmul(sigma, g));
+    if (dec_scale > 0.0f) z = fdiv(rintf(fmul(z, dec_scale)), dec_scale);
+    return fminf(fmaxf(z, r_min), r_max);
+}
+
 // Fixed-point helpers: metres -> Q16 cells, and the Q16 crossing count.
 __device__ __forceinline__ int q16_of(float v_m, float res) {
     return __float2int_rn(fmul(fdiv(v_m, res), 65536.0f));
@@ -147,7 +158,8 @@ struct Step2DParams {
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     uint2 key;
-    int env_base;                // global index of env 0 in the noise counter
+    int env_base;
+    float r_min, dec_scale;      // sensor quantisation (dec_scale 0: no rounding)                // global index of env 0 in the noise counter
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
@@ -192,6 +204,9 @@ constexpr unsigned kErrTimeout = 2u;
 // Records the calling thread's last error message (aslam_last_error(NULL)).
 void set_thread_error(const char *msg);
 
+// 10^d as the fp32 scale of the sensor's range rounding (0: no rounding).
+float range_scale(int d);
+
 // Launchers (defined next to their kernels).
 // `ev` (optional) receives an event record before the first kernel and
 // after each kernel of the step: 4 events for 2-D, 2 for 3-D.
@@ -201,6 +216,8 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
 cudaError_t step2d_set_smem(size_t smem);
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
+cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,
+                            float *u_out, float *obs, int row, int col, cudaStream_t s);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step3d_set_smem(size_t smem);

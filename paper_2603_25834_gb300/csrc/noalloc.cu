@@ -57,6 +57,7 @@ struct ScanParams {
     float res, r_max, sigma;
     uint2 key;
     int env_base;
+    float r_min, dec_scale;
     const uint8_t *gt;
     const float *pose;
     const int *step;
@@ -122,7 +123,7 @@ __global__ void scan_rays_kernel(const ScanParams p) {
         z = z_true;
         if (hit) {
             const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)p.step[e], (unsigned)b);
-            z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
+            z = measured_range(z_true, g, p.sigma, p.r_min, p.r_max, p.dec_scale);
         }
         const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
         // belief
@@ -260,6 +261,8 @@ extern "C" aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const
     p.sigma = cfg->noise_sigma_m;
     p.key = make_uint2((unsigned)cfg->seed, (unsigned)(cfg->seed >> 32));
     p.env_base = cfg->env_base;
+    p.r_min = cfg->r_min_m;
+    p.dec_scale = range_scale(cfg->range_decimals);
     p.gt = d_gt;
     p.pose = d_pose;
     p.step = d_step;

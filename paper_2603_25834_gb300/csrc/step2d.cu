@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
             z = z_true;
             if (hit) {
                 const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)esp->start.gstep, (unsigned)b);
-                z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
+                z = measured_range(z_true, g, p.sigma, p.r_min, p.r_max, p.dec_scale);
             }
             const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
             const int Ku = crossings_le(bm.nx0, bm.adx, Tz) + crossings_le(bm.ny0, bm.ady, Tz);
@@ -692,6 +692,16 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     }
 }
 
+// Bridged uncertainty (Sec. III-G, Eq. 22): U = alpha U_new + (1 - alpha) U_old.
+__global__ void bridge_u_kernel(const float *u_old, const float *u_new, float alpha, int E,
+                                float *u_out, float *obs, int row, int col) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const float u = fadd(fmul(alpha, u_new[e]), fmul(fsub(1.0f, alpha), u_old[e]));
+        if (u_out) u_out[e] = u;
+        if (obs) obs[(long long)e * row + col] = u;
+    }
+}
+
 __global__ void pack_gt_kernel(const uint8_t *gt, const long long *src_off, const int *W,
                                const int *H, const int *D, const long long *dst_words,
                                unsigned *bits) {
@@ -805,6 +815,12 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
     return e;
+}
+
+cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,
+                            float *u_out, float *obs, int row, int col, cudaStream_t s) {
+    bridge_u_kernel<<<(E + 255) / 256, 256, 0, s>>>(u_old, u_new, alpha, E, u_out, obs, row, col);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_gt(const uint8_t *gt, const long long *src_off, const int *W,

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                     z = z_true;
                     if (hit) {
                         const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)sh.start.gstep, (unsigned)b);
-                        z = fminf(fmaxf(fadd(z_true, fmul(p.sigma, g)), 0.0f), p.r_max);
+                        z = measured_range(z_true, g, p.sigma, p.r_min, p.r_max, p.dec_scale);
                     }
                     const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
                     Ku = crossings_le(r.nx0, r.ax, Tz) + crossings_le(r.ny0, r.ay, Tz) +

@@ -34,7 +34,8 @@ def orc_params(cfg):
                  l_clamp_q="clamp_q", t_episode="t_episode", d_crash="d_crash",
                  d_full="d_full", visit_cell_m="visit_cell", lam_col="lam_col",
                  lam_explore="lam_explore", lam_abs="lam_abs", lam_delta="lam_delta",
-                 kappa="kappa", u_hi="u_hi", seed="seed")
+                 kappa="kappa", u_hi="u_hi", seed="seed", r_min_m="r_min",
+                 range_decimals="decimals")
     return {names[k]: v for k, v in cfg.items() if k in names}
 
 

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 NAMES3 = dict(r_max_m="r_max", noise_sigma_m="sigma", sensor_z_m="sensor_z",
               elev_min_rad="el_min", elev_max_rad="el_max", t_episode="t_episode",
-              d_crash="d_crash", d_full="d_full")
+              d_crash="d_crash", d_full="d_full", r_min_m="r_min", range_decimals="decimals")
 
 
 def run3(aslam, orc, inp, rings, steps, envs=None, seed=5, counts=True, **cfg):
