@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default/tuned)")
     ap.add_argument("--window", type=int, default=0, help="shared window side (0: default/tuned)")
+    ap.add_argument("--u-mode", default="caller", choices=["caller", "scanmatch"],
+                    help="U_t from the caller (a synthetic signal) or from the in-step scan match")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -336,6 +338,12 @@ def main():
         workload = dict(WORKLOAD, envs=E_all)
     E = hi - lo
     cfg_kw["env_base"] = lo
+    if args.u_mode == "scanmatch":
+        if args.workload == "3d":
+            raise SystemExit("--u-mode scanmatch is 2-D only")
+        cfg_kw["u_mode"] = aslam.U_SCANMATCH
+        workload = dict(workload,
+                        u_t="in-step scan-match covariance (64 samples of one cell, Eq. 5-6)")
     batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE,
                           threads_per_cta=args.threads, window_cells=args.window, **cfg_kw)
     tuned = None
@@ -458,6 +466,9 @@ def main():
         kbytes = {"integrate2d_kernel": E * 24 + E * 72,
                   "sense2d_kernel": gt_step / 8 + Bsum * 8,
                   "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
+        if args.u_mode == "scanmatch":
+            # the belief read once per env, the covariance read and written, U written
+            kbytes["uq2d_kernel"] = 2 * int(batch.map_off[-1]) + E * (96 + 4)
     step_bytes = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
     peak, peak_kind = measured_peaks()
     kern = max(kernel_ms, key=kernel_ms.get)

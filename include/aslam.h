@@ -130,7 +130,27 @@ typedef struct {
      * at 0.  A beam with no return reports r_max_m unrounded. */
     float r_min_m;                 /* 0 <= r_min_m <= r_max_m */
     int32_t range_decimals;        /* -1 (off) or 0..6 */
+    /* In-step pose uncertainty (Sec. III-D, Eq. 5-6), 2-D only.  With
+     * u_mode = ASLAM_U_SCANMATCH the step computes U_t itself (the caller's
+     * d_u is ignored): the scan-match information of the soft expected-range
+     * model on the map before this scan, A = sum_b J_b J_b^T / sigma_r^2
+     * (J_b = d r_b / d(x, y, th) at the robot's pose; uq_samples samples of
+     * uq_step_m), is fused with the previous pose covariance propagated by
+     * one step of odometry noise Q = diag(uq_odo_sigma^2):
+     * Sigma_t = ((Sigma_{t-1} + Q)^-1 + A)^-1, Sigma = diag(uq_prior_sigma^2)
+     * after a reset; U_t = det(Sigma_t)^(1/3) / uq_u_scale (0: det(Q)^(1/3)).
+     * U_t then enters the reward (Eq. 7-17) and the observation (Eq. 3). */
+    int32_t u_mode;                /* ASLAM_U_CALLER (default) or ASLAM_U_SCANMATCH */
+    int32_t uq_samples;            /* 1 .. ASLAM_SOFT_MAX_SAMPLES (default 64) */
+    float uq_step_m;               /* >= 0; 0 = res_m */
+    float uq_range_sigma_m;        /* > 0 (default 0.01) */
+    float uq_odo_sigma[3];         /* > 0: x, y (m), theta (rad) per step (default 0.01) */
+    float uq_prior_sigma[3];       /* > 0 (default 0.01) */
+    float uq_u_scale;              /* >= 0 (default 0) */
 } aslam_config;
+
+#define ASLAM_U_CALLER    0
+#define ASLAM_U_SCANMATCH 1
 
 #define ASLAM_MAX_BEAMS 1024
 #define ASLAM_MAX_MAP_SIDE 8192
@@ -154,6 +174,7 @@ typedef struct {
     const int64_t *h_map_off;      /* HOST [E+1] cell offsets of each env's grid */
     const int64_t *h_ray_off;      /* HOST [E+1] offsets of each env's beams */
     int32_t b_max;                 /* max beams over envs (observation row = b_max + 2) */
+    double *pose_cov;              /* [E, 6] (xx, xy, xt, yy, yt, tt) with ASLAM_U_SCANMATCH, else NULL */
 } aslam_state_ptrs;
 
 /* Fill `cfg` with defaults (version, struct_size, constants). */

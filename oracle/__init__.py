@@ -74,12 +74,16 @@ class OrcCfg(C.Structure):
         ("lam_delta", C.c_double), ("kappa", C.c_double), ("u_hi", C.c_double),
         ("map_w", P), ("map_h", P), ("n_beams", P), ("map_off", P), ("visit_off", P),
         ("env_id", P),
+        ("u_mode", C.c_int32), ("uq_samples", C.c_int32), ("uq_step", C.c_float),
+        ("uq_range_sigma", C.c_float), ("uq_odo", C.c_float * 3), ("uq_prior", C.c_float * 3),
+        ("uq_u_scale", C.c_float),
     ]
 
 
 class OrcState(C.Structure):
     _fields_ = [("gt", P), ("belief", P), ("x", P), ("y", P), ("th", P), ("u_prev", P),
-                ("t", P), ("g", P), ("ep", P), ("done", P), ("visit", P), ("spawn", P)]
+                ("t", P), ("g", P), ("ep", P), ("done", P), ("visit", P), ("spawn", P),
+                ("sigma", P)]
 
 
 class OrcOut(C.Structure):
@@ -251,7 +255,9 @@ DEFAULTS = dict(r_max=5.0, r_min=0.0, decimals=-1, fov=0.0, sigma=0.0, dt=0.1, v
                 hit_q=870, miss_q=-410, clamp_q=3584, logodds_scale=1.0 / 1024.0,
                 t_episode=2048, d_crash=0.15, d_full=0.5, visit_cell=0.5,
                 lam_col=10.0, lam_explore=1.0, lam_abs=0.1, lam_delta=1.0, kappa=0.05,
-                u_hi=1.0, seed=20260325)
+                u_hi=1.0, seed=20260325, u_mode=0, uq_samples=64, uq_step=0.0,
+                uq_range_sigma=0.01, uq_odo=(0.01, 0.01, 0.01), uq_prior=(0.01, 0.01, 0.01),
+                uq_u_scale=0.0)
 
 
 class OracleBatch2D:
@@ -288,6 +294,10 @@ class OracleBatch2D:
         self.ep = np.zeros(E, dtype=np.int32)
         self.done = np.zeros(E, dtype=np.uint8)
         self.visit = np.full(int(self.visit_off[-1]), -1, dtype=np.int32)
+        # pose covariance (xx, xy, xt, yy, yt, tt): the prior until the first scan
+        pr = np.asarray(p["uq_prior"], np.float32).astype(np.float64)
+        self.sigma = np.zeros((E, 6), np.float64)
+        self.sigma[:, 0], self.sigma[:, 3], self.sigma[:, 5] = pr[0] ** 2, pr[1] ** 2, pr[2] ** 2
         self.cfg = OrcCfg(
             n_envs=E, b_max=self.b_max, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"],
@@ -300,13 +310,16 @@ class OracleBatch2D:
             lam_delta=p["lam_delta"], kappa=p["kappa"], u_hi=p["u_hi"],
             map_w=_ptr(self.map_w), map_h=_ptr(self.map_h), n_beams=_ptr(self.n_beams),
             map_off=_ptr(self.map_off), visit_off=_ptr(self.visit_off),
-            env_id=_ptr(self.env_ids))
+            env_id=_ptr(self.env_ids), u_mode=p["u_mode"], uq_samples=p["uq_samples"],
+            uq_step=p["uq_step"], uq_range_sigma=p["uq_range_sigma"],
+            uq_odo=(C.c_float * 3)(*p["uq_odo"]), uq_prior=(C.c_float * 3)(*p["uq_prior"]),
+            uq_u_scale=p["uq_u_scale"])
 
     def _state(self):
         return OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x),
                         y=_ptr(self.y), th=_ptr(self.th), u_prev=_ptr(self.u_prev),
                         t=_ptr(self.t), g=_ptr(self.g), ep=_ptr(self.ep), done=_ptr(self.done),
-                        visit=_ptr(self.visit), spawn=_ptr(self.spawn))
+                        visit=_ptr(self.visit), spawn=_ptr(self.spawn), sigma=_ptr(self.sigma))
 
     def step(self, actions, u=None, counts=False):
         """One step for all envs; returns a dict of this step's outputs."""

@@ -352,6 +352,9 @@ typedef struct {
     const int64_t *map_off;    /* [E+1] */
     const int64_t *visit_off;  /* [E+1] */
     const int32_t *env_id;     /* [E] index of each env in the noise stream, or NULL */
+    /* in-step pose uncertainty (u_mode 1): see orc_scan_uncertainty */
+    int32_t u_mode, uq_samples;
+    float uq_step, uq_range_sigma, uq_odo[3], uq_prior[3], uq_u_scale;
 } orc_cfg;
 
 typedef struct {
@@ -362,6 +365,7 @@ typedef struct {
     uint8_t *done;
     int32_t *visit;
     const float *spawn;        /* [E, n_spawn, 3] */
+    double *sigma;             /* [E, 6] pose covariance (xx, xy, xt, yy, yt, tt), u_mode 1 */
 } orc_state;
 
 enum { ORC_NT = 12 };          /* reward terms per env */
@@ -435,6 +439,101 @@ static void orc_reset_env(const orc_cfg *cfg, orc_state *st, int e)
     memset(st->belief + off, 0, (size_t)n * sizeof(int16_t));
     for (int64_t v = cfg->visit_off[e]; v < cfg->visit_off[e + 1]; ++v)
         st->visit[v] = -1;
+    if (st->sigma) {
+        double *S = st->sigma + 6 * (int64_t)e;
+        S[0] = (double)cfg->uq_prior[0] * cfg->uq_prior[0];
+        S[1] = S[2] = S[4] = 0.0;
+        S[3] = (double)cfg->uq_prior[1] * cfg->uq_prior[1];
+        S[5] = (double)cfg->uq_prior[2] * cfg->uq_prior[2];
+    }
+}
+
+/* ---- in-step pose uncertainty (Sec. III-D, Eq. 5-6) ------------------------ */
+
+typedef struct {
+    int32_t W, H, B, K;
+    double res, ds, fov;
+} orc_soft_cfg;                /* as in soft_range_oracle.c (same library) */
+
+double orc_soft_range(const orc_soft_cfg *c, const float *L, double x, double y, double th,
+                      int b, double gr, double *grad_pose, double *grad_map);
+
+static double orc_det3(const double *M)
+{
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+           M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+/* Inverse of a 3x3 matrix by its adjugate. */
+static void orc_inv3(const double *M, double *R)
+{
+    double d = orc_det3(M);
+    R[0] = (M[4] * M[8] - M[5] * M[7]) / d;
+    R[1] = (M[2] * M[7] - M[1] * M[8]) / d;
+    R[2] = (M[1] * M[5] - M[2] * M[4]) / d;
+    R[3] = (M[5] * M[6] - M[3] * M[8]) / d;
+    R[4] = (M[0] * M[8] - M[2] * M[6]) / d;
+    R[5] = (M[2] * M[3] - M[0] * M[5]) / d;
+    R[6] = (M[3] * M[7] - M[4] * M[6]) / d;
+    R[7] = (M[1] * M[6] - M[0] * M[7]) / d;
+    R[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+}
+
+/* The pose uncertainty of one env after this step's scan, from the map as
+ * it stands before the scan is integrated.  Scan-match information of the
+ * soft expected-range model (the Gauss-Newton Hessian of Eq. 5, Eq. 6):
+ * A = sum_b J_b J_b^T / sigma_r^2, J_b = d r_b / d(x, y, th) at the robot's
+ * pose, over the log-odds L * logodds_scale (nats).  It is fused with the
+ * previous covariance propagated by one step of odometry noise Q (the last
+ * block of a two-pose window): Sigma_t = ((Sigma_{t-1} + Q)^-1 + A)^-1.
+ * U_t = det(Sigma_t)^(1/3) / u_scale, u_scale = det(Q)^(1/3) unless given.
+ * Updates st->sigma and returns U_t. */
+static double orc_scan_uncertainty(const orc_cfg *cfg, orc_state *st, int e, float x, float y,
+                                   float th)
+{
+    const int32_t W = cfg->map_w[e], H = cfg->map_h[e], B = cfg->n_beams[e];
+    const int64_t off = cfg->map_off[e], n = (int64_t)W * H;
+    float *Lf = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k)
+        Lf[k] = (float)((double)st->belief[off + k] * cfg->logodds_scale);
+    orc_soft_cfg sc;
+    sc.W = W;
+    sc.H = H;
+    sc.B = B;
+    sc.K = cfg->uq_samples;
+    sc.res = cfg->res;
+    sc.ds = cfg->uq_step > 0.0f ? (double)cfg->uq_step : (double)cfg->res;
+    sc.fov = cfg->fov;
+    double A[9] = {0};
+    for (int b = 0; b < B; ++b) {
+        double J[3] = {0.0, 0.0, 0.0};
+        orc_soft_range(&sc, Lf, (double)x, (double)y, (double)th, b, 1.0, J, NULL);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                A[3 * i + j] += J[i] * J[j];
+    }
+    free(Lf);
+    const double s2 = (double)cfg->uq_range_sigma * cfg->uq_range_sigma;
+    double *S = st->sigma + 6 * (int64_t)e;
+    double P[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    for (int i = 0; i < 3; ++i)
+        P[4 * i] += (double)cfg->uq_odo[i] * cfg->uq_odo[i];
+    double Pi[9], Info[9], Sn[9];
+    orc_inv3(P, Pi);
+    for (int k = 0; k < 9; ++k)
+        Info[k] = Pi[k] + A[k] / s2;
+    orc_inv3(Info, Sn);
+    S[0] = Sn[0];
+    S[1] = 0.5 * (Sn[1] + Sn[3]);
+    S[2] = 0.5 * (Sn[2] + Sn[6]);
+    S[3] = Sn[4];
+    S[4] = 0.5 * (Sn[5] + Sn[7]);
+    S[5] = Sn[8];
+    double scale = cfg->uq_u_scale;
+    if (!(scale > 0.0))
+        scale = cbrt((double)cfg->uq_odo[0] * cfg->uq_odo[0] * cfg->uq_odo[1] * cfg->uq_odo[1] *
+                     cfg->uq_odo[2] * cfg->uq_odo[2]);
+    return cbrt(orc_det3(Sn)) / scale;
 }
 
 int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const float *u_in,
@@ -530,6 +629,11 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
         }
         free(cells);
 
+        /* In-step uncertainty from the map before this scan (u_mode 1). */
+        float u_scan = 0.0f;
+        if (cfg->u_mode == 1)
+            u_scan = (float)orc_scan_uncertainty(cfg, st, e, x, y, th);
+
         /* Map update: per-step sum of increments, then one clamp per cell. */
         int16_t *L = st->belief + off;
         double h_prev = orc_map_entropy(L, ncell, cfg->logodds_scale);
@@ -569,7 +673,8 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
         *vcell = st->t[e];
 
         /* Reward, Eq. 7-17. */
-        double Up = st->u_prev[e], U = u_in ? (double)u_in[e] : 0.0;
+        double Up = st->u_prev[e];
+        double U = cfg->u_mode == 1 ? (double)u_scan : (u_in ? (double)u_in[e] : 0.0);
         double cgate = orc_clip((cfg->u_hi - Up) / cfg->u_hi, 0.0, 1.0);
         cgate = cgate * cgate;                                      /* Eq. 11 */
         double iota = orc_clip(fmax(Up - U, 0.0) / cfg->kappa, 0.0, 1.0); /* Eq. 12 */

@@ -27,6 +27,8 @@ FLAG_DEBUG = 0x1
 FLAG_CHECKS = 0x2
 REWARD_ENTROPY = 0
 REWARD_COMPOSITE = 1
+U_CALLER = 0
+U_SCANMATCH = 1
 N_TERMS = 12
 TERM_NAMES = ["dH", "dcells", "I", "alpha_hug", "r_explore", "r_abs", "r_delta", "R",
               "collision", "dmin_meas", "dmin_true", "H"]
@@ -57,6 +59,9 @@ class AslamConfig(C.Structure):
         ("h_map_d", P), ("n_rings", C.c_int32), ("sensor_z_m", C.c_float),
         ("elev_min_rad", C.c_float), ("elev_max_rad", C.c_float), ("env_base", C.c_int32),
         ("r_min_m", C.c_float), ("range_decimals", C.c_int32),
+        ("u_mode", C.c_int32), ("uq_samples", C.c_int32), ("uq_step_m", C.c_float),
+        ("uq_range_sigma_m", C.c_float), ("uq_odo_sigma", C.c_float * 3),
+        ("uq_prior_sigma", C.c_float * 3), ("uq_u_scale", C.c_float),
     ]
 
 
@@ -64,7 +69,7 @@ class AslamStatePtrs(C.Structure):
     _fields_ = [("x", P), ("y", P), ("th", P), ("u_prev", P), ("t", P), ("g", P), ("ep", P),
                 ("done", P), ("belief", P), ("z", P), ("z_true", P), ("hit", P), ("counts", P),
                 ("ray_cells", P), ("gt_cells", P), ("terms", P), ("h_map_off", P),
-                ("h_ray_off", P), ("b_max", C.c_int32)]
+                ("h_ray_off", P), ("b_max", C.c_int32), ("pose_cov", P)]
 
 
 class AslamSoftConfig(C.Structure):
@@ -161,7 +166,8 @@ def config_defaults() -> AslamConfig:
 
 
 _FLOAT_KEYS = {"res_m", "r_max_m", "fov_rad", "noise_sigma_m", "dt_s", "v_max", "w_max",
-               "sensor_z_m", "elev_min_rad", "elev_max_rad", "r_min_m",
+               "sensor_z_m", "elev_min_rad", "elev_max_rad", "r_min_m", "uq_step_m",
+               "uq_range_sigma_m", "uq_u_scale",
                "d_crash", "d_full", "visit_cell_m", "logodds_scale", "lam_col", "lam_explore",
                "lam_abs", "lam_delta", "kappa", "u_hi"}
 
@@ -203,7 +209,10 @@ class Batch2D:
         for k, v in cfg.items():
             if not hasattr(c, k):
                 raise AslamError(1, "unknown config field %s" % k)
-            setattr(c, k, float(v) if k in _FLOAT_KEYS else int(v))
+            if isinstance(v, (tuple, list, np.ndarray)):
+                setattr(c, k, (C.c_float * len(v))(*[float(q) for q in v]))
+            else:
+                setattr(c, k, float(v) if k in _FLOAT_KEYS else int(v))
         self.cfg = c
         nbytes = C.c_size_t()
         _check(lib.aslam_workspace_bytes(C.byref(c), C.byref(nbytes)))
@@ -265,7 +274,9 @@ class Batch2D:
             counts=self._view(sp.counts, cells, torch.int32),
             ray_cells=self._view(sp.ray_cells, E, torch.int64),
             gt_cells=self._view(sp.gt_cells, E, torch.int64),
-            terms=self._view(sp.terms, E * N_TERMS, torch.float32).view(E, N_TERMS))
+            terms=self._view(sp.terms, E * N_TERMS, torch.float32).view(E, N_TERMS),
+            pose_cov=(self._view(sp.pose_cov, 6 * E, torch.float64).view(E, 6)
+                      if sp.pose_cov else None))
 
     def env_belief(self, e):
         st = self.state()["belief"]

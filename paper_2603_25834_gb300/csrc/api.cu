@@ -37,6 +37,7 @@ struct Offsets {
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
     size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, err, tune_actions;
+    size_t pose_cov, u_scan;
     size_t total;
 };
 
@@ -109,6 +110,17 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (!(c->r_min_m >= 0.0f) || !(c->r_min_m <= c->r_max_m))
         return fail("r_min_m must be in [0, r_max_m]");
     if (c->range_decimals < -1 || c->range_decimals > 6) return fail("range_decimals out of [-1, 6]");
+    if (c->u_mode != ASLAM_U_CALLER && c->u_mode != ASLAM_U_SCANMATCH) return fail("unknown u_mode");
+    if (c->u_mode == ASLAM_U_SCANMATCH) {
+        if (c->dims != 2) return fail("u_mode ASLAM_U_SCANMATCH needs dims = 2");
+        if (c->uq_samples < 1 || c->uq_samples > ASLAM_SOFT_MAX_SAMPLES)
+            return fail("uq_samples out of [1, ASLAM_SOFT_MAX_SAMPLES]");
+        if (!(c->uq_step_m >= 0.0f) || !(c->uq_range_sigma_m > 0.0f) || !(c->uq_u_scale >= 0.0f))
+            return fail("need uq_step_m >= 0, uq_range_sigma_m > 0, uq_u_scale >= 0");
+        for (int i = 0; i < 3; ++i)
+            if (!(c->uq_odo_sigma[i] > 0.0f) || !(c->uq_prior_sigma[i] > 0.0f))
+                return fail("uq_odo_sigma and uq_prior_sigma must be > 0");
+    }
     if (c->l_clamp_q < 1 || c->l_clamp_q > 8192) return fail("l_clamp_q out of [1, 8192]");
     if (std::abs(c->l_hit_q) > 32767 || std::abs(c->l_miss_q) > 32767)
         return fail("|l_hit_q|, |l_miss_q| must be <= 32767");
@@ -226,6 +238,9 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.queue = add(8);          // {next item, CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
+    const bool uq = c->u_mode == ASLAM_U_SCANMATCH;
+    o.pose_cov = add(uq ? 48 * E : 0);
+    o.u_scan = add(uq ? 4 * E : 0);
     o.total = pad_to(cur, kAlign);
     return o;
 }
@@ -292,7 +307,7 @@ float range_scale(int d) {
 namespace {
 
 int step_kernels(const aslam_batch *b) {
-    return b->hi.dims == 3 ? kStep3DKernels : kStep2DKernels;
+    return b->hi.dims == 3 ? kStep3DKernels : kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH);
 }
 
 void release_profile(aslam_batch *b) {
@@ -442,6 +457,15 @@ aslam_status aslam_config_init(aslam_config *c) {
     c->seed = 20260325ull;
     c->r_min_m = 0.0f;
     c->range_decimals = -1;
+    c->u_mode = ASLAM_U_CALLER;
+    c->uq_samples = 64;
+    c->uq_step_m = 0.0f;
+    c->uq_range_sigma_m = 0.01f;
+    for (int i = 0; i < 3; ++i) {
+        c->uq_odo_sigma[i] = 0.01f;
+        c->uq_prior_sigma[i] = 0.01f;
+    }
+    c->uq_u_scale = 0.0f;
     return ASLAM_OK;
 }
 
@@ -528,6 +552,22 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.d_crash = cfg->d_crash;
         p.d_full = cfg->d_full;
         p.visit_cell = cfg->visit_cell_m;
+        p.logodds_scale = cfg->logodds_scale;
+        p.u_mode = cfg->u_mode;
+        if (cfg->u_mode == ASLAM_U_SCANMATCH) {
+            p.uq_K = cfg->uq_samples;
+            p.uq_ds = cfg->uq_step_m > 0.0f ? cfg->uq_step_m : cfg->res_m;
+            p.uq_inv_s2 = 1.0 / ((double)cfg->uq_range_sigma_m * cfg->uq_range_sigma_m);
+            double qdet = 1.0;
+            for (int i = 0; i < 3; ++i) {
+                p.uq_q[i] = (double)cfg->uq_odo_sigma[i] * cfg->uq_odo_sigma[i];
+                p.uq_prior[i] = (double)cfg->uq_prior_sigma[i] * cfg->uq_prior_sigma[i];
+                qdet *= p.uq_q[i];
+            }
+            p.uq_scale = cfg->uq_u_scale > 0.0f ? (double)cfg->uq_u_scale : std::cbrt(qdet);
+            p.pose_cov = at<double>(b, o.pose_cov);
+            p.u_scan = at<float>(b, o.u_scan);
+        }
         p.lam_col = cfg->lam_col;
         p.lam_explore = cfg->lam_explore;
         p.lam_abs = cfg->lam_abs;
@@ -763,6 +803,7 @@ aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *o) {
     o->h_map_off = reinterpret_cast<const int64_t *>(b->hi.map_off.data());
     o->h_ray_off = reinterpret_cast<const int64_t *>(b->hi.ray_off.data());
     o->b_max = b->hi.b_max;
+    o->pose_cov = p.pose_cov;
     return ASLAM_OK;
 }
 
@@ -874,10 +915,12 @@ struct Region { void *ptr; size_t bytes; };
 std::vector<Region> state_regions(aslam_batch *b) {
     const Step2DParams &p = b->p;
     const size_t E = b->hi.E;
-    return {{p.x, 4 * E}, {p.y, 4 * E}, {p.th, 4 * E}, {p.u_prev, 4 * E}, {p.t, 4 * E},
-            {p.g, 4 * E}, {p.ep, 4 * E}, {p.done, 4 * E}, {p.Hq, 8 * E},
-            {p.belief, 2 * (size_t)b->hi.map_off[E]},
-            {p.visit, 4 * (size_t)b->hi.visit_off[E]}};
+    std::vector<Region> r = {{p.x, 4 * E}, {p.y, 4 * E}, {p.th, 4 * E}, {p.u_prev, 4 * E},
+                             {p.t, 4 * E}, {p.g, 4 * E}, {p.ep, 4 * E}, {p.done, 4 * E},
+                             {p.Hq, 8 * E}, {p.belief, 2 * (size_t)b->hi.map_off[E]},
+                             {p.visit, 4 * (size_t)b->hi.visit_off[E]}};
+    if (p.pose_cov) r.push_back({p.pose_cov, 48 * E});
+    return r;
 }
 }  // namespace
 
@@ -981,8 +1024,11 @@ aslam_status aslam_profile_end(aslam_batch *b, double *h_ms, int32_t *h_n_kernel
 
 const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
     static const char *const k2[] = {"integrate2d_kernel", "sense2d_kernel", "update2d_kernel"};
+    static const char *const k2u[] = {"integrate2d_kernel", "sense2d_kernel", "uq2d_kernel",
+                                      "update2d_kernel"};
     if (!b || k < 0) return nullptr;
     if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
+    if (b->p.u_mode == ASLAM_U_SCANMATCH) return k < kStep2DKernels + 1 ? k2u[k] : nullptr;
     return k < kStep2DKernels ? k2[k] : nullptr;
 }
 

@@ -159,7 +159,13 @@ struct Step2DParams {
     double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
     uint2 key;
     int env_base;
-    float r_min, dec_scale;      // sensor quantisation (dec_scale 0: no rounding)                // global index of env 0 in the noise counter
+    float r_min, dec_scale;      // sensor quantisation (dec_scale 0: no rounding)
+    // in-step pose uncertainty (u_mode 1)
+    int u_mode, uq_K;
+    float uq_ds, logodds_scale;
+    double uq_inv_s2, uq_q[3], uq_prior[3], uq_scale;
+    double *pose_cov;            // [E, 6]
+    float *u_scan;               // [E]                // global index of env 0 in the noise counter
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
@@ -210,12 +216,13 @@ float range_scale(int d);
 // Launchers (defined next to their kernels).
 // `ev` (optional) receives an event record before the first kernel and
 // after each kernel of the step: 4 events for 2-D, 2 for 3-D.
-constexpr int kStep2DKernels = 3, kStep3DKernels = 1;
+constexpr int kStep2DKernels = 3, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
+cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s);
 cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,
                             float *u_out, float *obs, int row, int col, cudaStream_t s);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,

@@ -734,6 +734,13 @@ __global__ void init_state_kernel(const Step2DParams p) {
         p.done[e] = 0;
         p.Hq[e] = (long long)p.W[e] * p.H[e] * p.Dd[e] * p.lut[p.clamp_q];
         p.reward[e] = 0.0f;
+        if (p.pose_cov) {
+            double *S = p.pose_cov + 6 * (long long)e;
+            S[0] = p.uq_prior[0];
+            S[1] = S[2] = S[4] = 0.0;
+            S[3] = p.uq_prior[1];
+            S[5] = p.uq_prior[2];
+        }
     }
 }
 
@@ -811,6 +818,18 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess) return e;
+    if (p.u_mode == 1) {
+        // in-step U_t from the map before this scan; the update's reward reads it
+        e = launch_uq2d(p, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+        if (e != cudaSuccess) return e;
+        Step2DParams q = p;
+        q.u_in = p.u_scan;
+        update2d_kernel<<<grid, block, smem, s>>>(q);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], s);
+        return e;
+    }
     update2d_kernel<<<grid, block, smem, s>>>(p);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);

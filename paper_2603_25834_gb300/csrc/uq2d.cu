@@ -1,0 +1,203 @@
+// uq2d.cu -- in-step pose uncertainty U_t of the 2-D step (Sec. III-D,
+// Eq. 5-6) on sm_103a.
+//
+// The scan-match information of the soft expected-range model: each beam's
+// range r_b = sum_k T_k p_k s_k + T_K * K*ds over K samples s_k = (k+1)*ds
+// of the belief (bilinear natural log-odds on cell centres, clamp to edge;
+// p_k = sigmoid(l_k), T_{k+1} = T_k (1 - p_k)), differentiated in forward
+// mode w.r.t. the pose (x, y, th); A = sum_b J_b J_b^T / sigma_r^2 is the
+// Gauss-Newton Hessian of the scan-to-map residuals.  It is fused with the
+// previous pose covariance propagated by one step of odometry noise Q
+// (the last block of a two-pose window with an odometry factor):
+//   Sigma_t = ((Sigma_{t-1} + Q)^-1 + A)^-1,   U_t = det(Sigma_t)^(1/3) / scale.
+//
+// Runs between the sensing and the update kernels, so the map is the one
+// built before this scan.  One CTA per env, one thread per beam.  Every
+// sample lies within K*ds of the robot, so the CTA first copies the map
+// window of half-side R = ceil(K*ds/res) + 2 cells around the robot's cell
+// (clamped to the map) into shared memory and reads its bilinear taps
+// there; lanes of a warp follow beams that fan out, and their taps would
+// otherwise touch up to 32 cache lines per load.  The six
+// sums of J J^T are reduced in a fixed order (deterministic); the 3x3
+// algebra runs in fp64 on one thread.  An env that resets this step has an
+// all-unknown map (cleared by the update kernel), hence A = 0.
+#include <cmath>
+
+#include "aslam_internal.cuh"
+
+namespace aslam {
+namespace {
+
+struct Tap {
+    float l, gx, gy;       // log-odds (nats) and its gradient per metre
+};
+
+// The map as the kernel reads it: the whole env grid in global memory, or
+// the window [x0, x0+ww) x [y0, y0+wh) of it staged in shared memory.
+struct MapView {
+    const short *L;
+    int W, H, x0, y0, ww;
+};
+
+__device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, float scale,
+                                           float px, float py, Tap &t) {
+    const float u = px * inv_res - 0.5f, v = py * inv_res - 0.5f;
+    const float fu = floorf(u), fv = floorf(v);
+    const float ax = u - fu, ay = v - fv;
+    const int i0 = (int)fu, j0 = (int)fv;
+    const int ia = min(max(i0, 0), m.W - 1) - m.x0, ib = min(max(i0 + 1, 0), m.W - 1) - m.x0;
+    const int ja = min(max(j0, 0), m.H - 1) - m.y0, jb = min(max(j0 + 1, 0), m.H - 1) - m.y0;
+    const float l00 = (float)m.L[ja * m.ww + ia] * scale;
+    const float l10 = (float)m.L[ja * m.ww + ib] * scale;
+    const float l01 = (float)m.L[jb * m.ww + ia] * scale;
+    const float l11 = (float)m.L[jb * m.ww + ib] * scale;
+    t.l = (1.f - ax) * (1.f - ay) * l00 + ax * (1.f - ay) * l10 + (1.f - ax) * ay * l01 +
+          ax * ay * l11;
+    t.gx = ((1.f - ay) * (l10 - l00) + ay * (l11 - l01)) * inv_res;
+    t.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * inv_res;
+}
+
+__device__ __forceinline__ double det3d(const double *M) {
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+           M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+// 3x3 inverse through the adjugate.
+__device__ __forceinline__ void inv3d(const double *M, double *R) {
+    const double d = det3d(M);
+    R[0] = (M[4] * M[8] - M[5] * M[7]) / d;
+    R[1] = (M[2] * M[7] - M[1] * M[8]) / d;
+    R[2] = (M[1] * M[5] - M[2] * M[4]) / d;
+    R[3] = (M[5] * M[6] - M[3] * M[8]) / d;
+    R[4] = (M[0] * M[8] - M[2] * M[6]) / d;
+    R[5] = (M[2] * M[3] - M[0] * M[5]) / d;
+    R[6] = (M[3] * M[7] - M[4] * M[6]) / d;
+    R[7] = (M[1] * M[6] - M[0] * M[7]) / d;
+    R[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+}
+
+// Three CTAs per SM (at most 42 registers a thread) hide the latency of
+// each beam's sample chain better than fewer, fatter CTAs.
+__global__ void __launch_bounds__(512, 3) uq2d_kernel(const Step2DParams p, int R, bool staged) {
+    extern __shared__ __align__(16) short s_win[];
+    __shared__ float red[6][32];
+    const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int W = p.W[e], H = p.H[e], B = p.B[e];
+    const bool reset = p.done[e] != 0;
+    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (!reset) {
+        const short *Lq = p.belief + p.map_off[e];
+        const float x = p.x[e], y = p.y[e], th = p.th[e];
+        MapView m{Lq, W, H, 0, 0, W};
+        if (staged) {
+            // every tap (clamped to the map) is within R cells of the robot's cell
+            const int ri = q16_of(x, p.res) >> 16, rj = q16_of(y, p.res) >> 16;
+            const int x0 = min(max(ri - R, 0), W - 1), x1 = min(max(ri + R, 0), W - 1);
+            const int y0 = min(max(rj - R, 0), H - 1), y1 = min(max(rj + R, 0), H - 1);
+            const int ww = x1 - x0 + 1, wh = y1 - y0 + 1;
+            for (int q = tid; q < ww * wh; q += nt) {
+                const int jj = q / ww, ii = q - jj * ww;
+                s_win[q] = __ldg(Lq + (long long)(y0 + jj) * W + x0 + ii);
+            }
+            m = MapView{s_win, W, H, x0, y0, ww};
+            __syncthreads();
+        }
+        float s, c;
+        det_sincos(th, s, c);
+        const float inv_res = 1.0f / p.res, scale = p.logodds_scale;
+        const float r_far = (float)p.uq_K * p.uq_ds;
+        for (int b = tid; b < B; b += nt) {
+            const float2 cs = p.beam_cs[p.ray_off[e] + b];
+            const float cp = c * cs.x - s * cs.y, sp = s * cs.x + c * cs.y;
+            float T = 1.f;
+            float dT0 = 0.f, dT1 = 0.f, dT2 = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
+            Tap t;
+            for (int k = 0; k < p.uq_K; ++k) {
+                const float sk = (float)(k + 1) * p.uq_ds;
+                bilinear_q(m, inv_res, scale, x + sk * cp, y + sk * sp, t);
+                // p = sigmoid(l), q = 1 - p, without cancellation (fast exp and
+                // divide: U carries a 1e-2 relative tolerance)
+                const float ex = __expf(-fabsf(t.l));
+                const float inv = __fdividef(1.0f, 1.0f + ex);
+                const float pr = t.l >= 0.f ? inv : ex * inv;
+                const float q = t.l >= 0.f ? ex * inv : inv;
+                const float dpl = pr * q;
+                const float d0 = dpl * t.gx, d1 = dpl * t.gy;
+                const float d2 = dpl * (t.gx * (-sk * sp) + t.gy * (sk * cp));
+                dr0 += (dT0 * pr + T * d0) * sk;
+                dr1 += (dT1 * pr + T * d1) * sk;
+                dr2 += (dT2 * pr + T * d2) * sk;
+                dT0 = dT0 * q - T * d0;
+                dT1 = dT1 * q - T * d1;
+                dT2 = dT2 * q - T * d2;
+                T *= q;
+            }
+            const float J0 = dr0 + dT0 * r_far, J1 = dr1 + dT1 * r_far, J2 = dr2 + dT2 * r_far;
+            a[0] += J0 * J0;
+            a[1] += J0 * J1;
+            a[2] += J0 * J2;
+            a[3] += J1 * J1;
+            a[4] += J1 * J2;
+            a[5] += J2 * J2;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float v = a[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A[6];
+        for (int q = 0; q < 6; ++q) {
+            double v = 0.0;
+            for (int w = 0; w < nw; ++w) v += (double)red[q][w];
+            A[q] = v * p.uq_inv_s2;
+        }
+        double *S = p.pose_cov + 6 * (long long)e;
+        double Sp[6];
+        if (reset) {
+            Sp[0] = p.uq_prior[0];
+            Sp[1] = Sp[2] = Sp[4] = 0.0;
+            Sp[3] = p.uq_prior[1];
+            Sp[5] = p.uq_prior[2];
+        } else {
+            for (int q = 0; q < 6; ++q) Sp[q] = S[q];
+        }
+        const double P[9] = {Sp[0] + p.uq_q[0], Sp[1], Sp[2], Sp[1], Sp[3] + p.uq_q[1], Sp[4],
+                             Sp[2], Sp[4], Sp[5] + p.uq_q[2]};
+        double Pi[9], Sn[9];
+        inv3d(P, Pi);
+        const double Info[9] = {Pi[0] + A[0], Pi[1] + A[1], Pi[2] + A[2],
+                                Pi[3] + A[1], Pi[4] + A[3], Pi[5] + A[4],
+                                Pi[6] + A[2], Pi[7] + A[4], Pi[8] + A[5]};
+        inv3d(Info, Sn);
+        S[0] = Sn[0];
+        S[1] = 0.5 * (Sn[1] + Sn[3]);
+        S[2] = 0.5 * (Sn[2] + Sn[6]);
+        S[3] = Sn[4];
+        S[4] = 0.5 * (Sn[5] + Sn[7]);
+        S[5] = Sn[8];
+        p.u_scan[e] = (float)(cbrt(det3d(Sn)) / p.uq_scale);
+    }
+}
+
+constexpr size_t kUqWindowMax = 48 * 1024;     // shared bytes for the staged map window
+
+}  // namespace
+
+cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s) {
+    int block = ((p.b_max + 31) / 32) * 32;
+    block = block < 64 ? 64 : (block > 512 ? 512 : block);
+    // samples reach K*ds from the robot; taps one cell further, plus rounding
+    const int R = (int)ceilf(((float)p.uq_K * p.uq_ds) / p.res) + 2;
+    const size_t win = 2 * (size_t)(2 * R + 1) * (2 * R + 1);
+    const bool staged = win <= kUqWindowMax;
+    uq2d_kernel<<<p.E, block, staged ? win : 0, s>>>(p, R, staged);
+    return cudaGetLastError();
+}
+
+}  // namespace aslam
