@@ -258,6 +258,81 @@ aslam_status aslam_save_state(aslam_batch *b, void *h_buf, size_t bytes, void *s
 aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, void *stream);
 
 /*
+ * Batched correlative scan matching (Sec. III-D: a discretised (dx, dy, dth)
+ * neighbourhood of the predicted pose is evaluated against the log-odds
+ * grid; the best candidate is an absolute pose measurement whose
+ * information is scaled by the normalised match score and the ambiguity
+ * margin between the best and second-best candidates).  2-D batches only.
+ *
+ * Candidates: translations (i, j) in [-n_xy, n_xy]^2 whole cells and
+ * rotations k in [-n_th, n_th] steps of dth_rad.  For each returned beam
+ * (range < r_max) its direction is rotated by th_k = th + k*dth (fp32, the
+ * library's sin/cos), its endpoint (x, y) + z*(cos, sin) is taken to a cell
+ * by floor(metres / res) and shifted by (i, j); the candidate's score is the
+ * sum over beams of the cell's occupancy evidence min(255, max(L, 0) >> 4)
+ * (0 outside the map).  Best: the highest score, ties to the lowest index
+ * ((k + n_th)(2n_xy+1) + (j + n_xy))(2n_xy+1) + (i + n_xy); second: the
+ * highest score of the candidates more than `sep` steps from the best in
+ * some coordinate.  With N returned beams: score_norm = best / (255 N),
+ * margin = (best - second) / best, w = score_norm * margin (each 0 when
+ * its denominator is 0), evaluated in fp64 and stored as fp32.
+ *
+ *   d_pose_pred [E, 3]  predicted poses (x, y, th)
+ *   d_ranges    [sum B] ranges, or NULL for the batch's last measured ranges
+ *   d_pose_out  [E, 3]  (x + i*res, y + j*res, th_k wrapped to [-pi, pi))
+ *   d_match     [E, 3]  (score_norm, margin, w)
+ *   d_scores    [E, 3]  int64 (best, second, best index)
+ */
+typedef struct {
+    uint32_t struct_size;          /* sizeof(aslam_csm_config) */
+    int32_t n_xy;                  /* 0..8 */
+    int32_t n_th;                  /* 0..8 */
+    int32_t sep;                   /* >= 0 */
+    float dth_rad;                 /* > 0 */
+} aslam_csm_config;
+
+/* Defaults: n_xy = 5, n_th = 5, sep = 1, dth_rad = 0.01. */
+aslam_status aslam_csm_config_init(aslam_csm_config *cfg);
+aslam_status aslam_csm(aslam_batch *b, const aslam_csm_config *cfg, const float *d_pose_pred,
+                       const float *d_ranges, float *d_pose_out, float *d_match,
+                       int64_t *d_scores, void *stream);
+
+/*
+ * Batched fixed-lag window Gauss-Newton (Sec. III-D, Eq. 5-6): per env a
+ * sliding window of L planar poses x_i = (x, y, th) with
+ *   a prior factor      r = x_0 - p                       information diag(d_prior_info)
+ *   odometry factors    r = (R(th_i)^T (t_{i+1} - t_i) - u_xy,
+ *                            wrap(th_{i+1} - th_i - u_th))  information diag(odo_info)
+ *   pose factors        r = x_i - z_i                      information diag(d_meas_info)
+ * (angle residuals wrapped to [-pi, pi); a zero information row disables a
+ * factor, e.g. a pose without a scan match).  `iters` Gauss-Newton steps
+ * x <- x + H^-1 (-g) in fp64, then at the final estimate the marginal
+ * covariance of the newest pose, Sigma_last = the last 3x3 block of H^-1
+ * (Eq. 6), and U = det(Sigma_last)^(1/3) / u_scale.
+ *   d_x         [E, L, 3] fp32, in: initial estimate, out: optimised window
+ *   d_odo       [E, L-1, 3]   d_meas, d_meas_info [E, L, 3]
+ *   d_prior, d_prior_info     [E, 3]
+ *   d_cov [E, 9], d_u [E], d_status [E] (0 ok, 1 singular normal matrix;
+ *   then cov and U are NaN): optional outputs.
+ */
+typedef struct {
+    uint32_t struct_size;          /* sizeof(aslam_flgn_config) */
+    int32_t n_envs;                /* E >= 1 */
+    int32_t window;                /* L in [1, 16] */
+    int32_t iters;                 /* 0 .. 20 */
+    float odo_info[3];             /* > 0: x, y (m^-2), th (rad^-2) */
+    float u_scale;                 /* > 0 */
+} aslam_flgn_config;
+
+/* Defaults: 1 env, L = 8, 3 iterations, odometry std 0.01 m / 0.01 rad,
+ * u_scale = 1e-4 (one step of that odometry noise). */
+aslam_status aslam_flgn_config_init(aslam_flgn_config *cfg);
+aslam_status aslam_fixed_lag_gn(const aslam_flgn_config *cfg, float *d_x, const float *d_odo,
+                                const float *d_meas, const float *d_meas_info,
+                                const float *d_prior, const float *d_prior_info, float *d_cov,
+                                float *d_u, int32_t *d_status, void *stream);
+
+/*
  * Uncertainty bridge for SLAM-agnostic fine-tuning (Sec. III-G, Eq. 21-22):
  * alpha = min(1, t / t_bridge) (fp64, rounded once to fp32) and, per env,
  * U = alpha * U_new + (1 - alpha) * U_old in fp32.  d_u_old / d_u_new:

@@ -6,7 +6,7 @@ leg may import this package.  It shares no code with the CUDA path
 paper_2603_25834_gb300.synth.
 
 The arithmetic lives in plain C (aslam_oracle.c, soft_range_oracle.c,
-raycast3d_oracle.c); this module compiles them with gcc and marshals numpy
+raycast3d_oracle.c, slam_oracle.c); this module compiles them with gcc and marshals numpy
 arrays through ctypes.  Every function cites the passage it follows in the
 C sources.  Pins: tests/test_oracle_*.py.
 """
@@ -21,7 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["aslam_oracle.c", "soft_range_oracle.c", "raycast3d_oracle.c"]
+_SOURCES = ["aslam_oracle.c", "soft_range_oracle.c", "raycast3d_oracle.c", "slam_oracle.c"]
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -140,6 +140,11 @@ def _declare(L):
     L.orc_ray_setup.argtypes = [C.c_float] * 7 + [C.POINTER(C.c_int32)] * 4
     L.orc_measured_range.argtypes = [C.c_float] * 6
     L.orc_measured_range.restype = C.c_float
+    L.orc_csm.argtypes = [P, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_double,
+                          P, C.c_float, C.c_float, C.c_float, C.c_int32, C.c_int32, C.c_int32,
+                          C.c_float, P, P, P]
+    L.orc_fixed_lag_gn.argtypes = [C.c_int, C.c_int, P, P, P, P, P, P, P, P]
+    L.orc_fixed_lag_gn.restype = C.c_int
     L.orc_bridge_alpha.argtypes = [C.c_int64, C.c_int64]
     L.orc_bridge_alpha.restype = C.c_float
     L.orc_bridge_u.argtypes = [C.c_float, C.c_float, C.c_float]
@@ -239,6 +244,36 @@ def measured_range(z_true, g, sigma, r_min, r_max, decimals=-1):
     return lib().orc_measured_range(C.c_float(z_true), C.c_float(g), C.c_float(sigma),
                                     C.c_float(r_min), C.c_float(r_max),
                                     C.c_float(dec_scale(decimals)))
+
+
+def csm(belief, res, r_max, fov, z, pose, n_xy=5, n_th=5, sep=1, dth=0.01):
+    """Correlative scan match of one env: belief int16 [H, W], ranges z [B],
+    predicted pose (x, y, th).  Returns (pose_out [3] fp32, match [3] fp32,
+    scores [3] int64 = best, second, best index)."""
+    Lb = np.ascontiguousarray(belief, dtype=np.int16)
+    H, W = Lb.shape
+    zz = np.ascontiguousarray(z, dtype=np.float32)
+    pose = np.asarray(pose, np.float32)
+    po = np.zeros(3, np.float32)
+    mt = np.zeros(3, np.float32)
+    sc = np.zeros(3, np.int64)
+    lib().orc_csm(_ptr(Lb), W, H, res, r_max, zz.size, fov, _ptr(zz), float(pose[0]),
+                  float(pose[1]), float(pose[2]), n_xy, n_th, sep, dth, _ptr(po), _ptr(mt),
+                  _ptr(sc))
+    return po, mt, sc
+
+
+def fixed_lag_gn(x, odo, meas, meas_info, prior, prior_info, odo_info, iters=3):
+    """One env's window (fp64): returns (x [L, 3], cov_last [3, 3], status)."""
+    x = np.array(x, np.float64).reshape(-1, 3).copy()
+    L = x.shape[0]
+    odo = np.ascontiguousarray(np.asarray(odo, np.float64).reshape(max(L - 1, 0), 3))
+    args = [np.ascontiguousarray(np.asarray(v, np.float64)) for v in
+            (meas, meas_info, prior, prior_info, odo_info)]
+    cov = np.zeros(9, np.float64)
+    rc = lib().orc_fixed_lag_gn(L, int(iters), _ptr(x), _ptr(odo), *[_ptr(a) for a in args],
+                                _ptr(cov))
+    return x, cov.reshape(3, 3), rc
 
 
 def bridge_u(u_old, u_new, t, t_bridge):

@@ -72,6 +72,16 @@ class AslamStatePtrs(C.Structure):
                 ("h_ray_off", P), ("b_max", C.c_int32), ("pose_cov", P)]
 
 
+class AslamCsmConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("n_xy", C.c_int32), ("n_th", C.c_int32),
+                ("sep", C.c_int32), ("dth_rad", C.c_float)]
+
+
+class AslamFlgnConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("n_envs", C.c_int32), ("window", C.c_int32),
+                ("iters", C.c_int32), ("odo_info", C.c_float * 3), ("u_scale", C.c_float)]
+
+
 class AslamSoftConfig(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("n_envs", C.c_int32), ("map_w", C.c_int32),
                 ("map_h", C.c_int32), ("n_beams", C.c_int32), ("n_samples", C.c_int32),
@@ -99,6 +109,10 @@ EXPORTS = {
     "aslam_save_state": ([P, P, C.c_size_t, P], C.c_int),
     "aslam_load_state": ([P, P, C.c_size_t, P], C.c_int),
     "aslam_bridge_u": ([P, P, P, C.c_int64, C.c_int64, P, P, P], C.c_int),
+    "aslam_csm_config_init": ([C.POINTER(AslamCsmConfig)], C.c_int),
+    "aslam_flgn_config_init": ([C.POINTER(AslamFlgnConfig)], C.c_int),
+    "aslam_fixed_lag_gn": ([C.POINTER(AslamFlgnConfig), P, P, P, P, P, P, P, P, P, P], C.c_int),
+    "aslam_csm": ([P, C.POINTER(AslamCsmConfig), P, P, P, P, P, P], C.c_int),
     "aslam_profile_begin": ([P, C.c_int32], C.c_int),
     "aslam_profile_end": ([P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "aslam_kernel_name": ([P, C.c_int32], C.c_char_p),
@@ -343,6 +357,21 @@ class Batch2D:
                self.handle)
         return out
 
+    def csm(self, pose_pred, ranges=None, n_xy=5, n_th=5, sep=1, dth_rad=0.01, stream=None):
+        """Correlative scan matching of each env's scan against its grid (Sec. III-D).
+        Returns (pose_out [E,3] fp32, match [E,3] = score_norm, margin, w,
+        scores [E,3] int64 = best, second, best index)."""
+        c = AslamCsmConfig()
+        _check(self.lib.aslam_csm_config_init(C.byref(c)))
+        c.n_xy, c.n_th, c.sep, c.dth_rad = int(n_xy), int(n_th), int(sep), float(dth_rad)
+        pose_out = torch.empty(self.E, 3, dtype=torch.float32, device=self.device)
+        match = torch.empty(self.E, 3, dtype=torch.float32, device=self.device)
+        scores = torch.empty(self.E, 3, dtype=torch.int64, device=self.device)
+        _check(self.lib.aslam_csm(self.handle, C.byref(c), _dptr(pose_pred), _dptr(ranges),
+                                  _dptr(pose_out), _dptr(match), _dptr(scores), _stream(stream)),
+               self.handle)
+        return pose_out, match, scores
+
     def profile_begin(self, max_steps):
         """Time each kernel of the next max_steps steps with CUDA events."""
         _check(self.lib.aslam_profile_begin(self.handle, int(max_steps)), self.handle)
@@ -405,3 +434,25 @@ def scan_update_noalloc(inputs, gt, pose, step, belief, ranges, stream=None, **c
         setattr(c, k, float(v) if k in _FLOAT_KEYS else int(v))
     _check(lib.aslam_scan_update_noalloc(C.byref(c), _dptr(gt), off.ctypes.data_as(P), _dptr(pose),
                                          _dptr(step), _dptr(belief), _dptr(ranges), _stream(stream)))
+
+
+def fixed_lag_gn(x, odo, meas, meas_info, prior, prior_info, iters=3,
+                 odo_info=(1e4, 1e4, 1e4), u_scale=1e-4, stream=None):
+    """Batched fixed-lag window Gauss-Newton (Sec. III-D, Eq. 5-6) on device
+    tensors: x [E, L, 3] (optimised in place), odo [E, L-1, 3], meas and
+    meas_info [E, L, 3], prior and prior_info [E, 3].  Returns (cov [E, 3, 3],
+    u [E], status [E])."""
+    lib = load()
+    E, L = int(x.shape[0]), int(x.shape[1])
+    c = AslamFlgnConfig()
+    _check(lib.aslam_flgn_config_init(C.byref(c)))
+    c.n_envs, c.window, c.iters = E, L, int(iters)
+    c.odo_info = (C.c_float * 3)(*[float(v) for v in odo_info])
+    c.u_scale = float(u_scale)
+    cov = torch.empty(E, 3, 3, dtype=torch.float32, device=x.device)
+    u = torch.empty(E, dtype=torch.float32, device=x.device)
+    st = torch.empty(E, dtype=torch.int32, device=x.device)
+    _check(lib.aslam_fixed_lag_gn(C.byref(c), _dptr(x), _dptr(odo), _dptr(meas),
+                                  _dptr(meas_info), _dptr(prior), _dptr(prior_info), _dptr(cov),
+                                  _dptr(u), _dptr(st), _stream(stream)))
+    return cov, u, st

@@ -962,6 +962,80 @@ aslam_status aslam_load_state(aslam_batch *b, const void *h_buf, size_t bytes, v
     return ASLAM_OK;
 }
 
+aslam_status aslam_flgn_config_init(aslam_flgn_config *c) {
+    if (!c) return ASLAM_ERR_INVALID_ARG;
+    c->struct_size = sizeof(aslam_flgn_config);
+    c->n_envs = 1;
+    c->window = 8;
+    c->iters = 3;
+    for (int q = 0; q < 3; ++q) c->odo_info[q] = 1.0f / (0.01f * 0.01f);
+    c->u_scale = 1e-4f;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_fixed_lag_gn(const aslam_flgn_config *c, float *d_x, const float *d_odo,
+                                const float *d_meas, const float *d_meas_info,
+                                const float *d_prior, const float *d_prior_info, float *d_cov,
+                                float *d_u, int32_t *d_status, void *stream) {
+    auto fail = [](const char *m) {
+        set_thread_error(m);
+        return ASLAM_ERR_INVALID_ARG;
+    };
+    if (!c || c->struct_size != sizeof(aslam_flgn_config)) return fail("flgn config NULL or struct_size mismatch");
+    if (c->n_envs < 1) return fail("n_envs must be >= 1");
+    if (c->window < 1 || c->window > flgn_max_window()) return fail("window out of [1, 16]");
+    if (c->iters < 0 || c->iters > 20) return fail("iters out of [0, 20]");
+    for (int q = 0; q < 3; ++q)
+        if (!(c->odo_info[q] > 0.0f)) return fail("odo_info must be > 0");
+    if (!(c->u_scale > 0.0f)) return fail("u_scale must be > 0");
+    if (!d_x || !d_meas || !d_meas_info || !d_prior || !d_prior_info || (c->window > 1 && !d_odo))
+        return fail("NULL pointer argument");
+    cudaError_t e = launch_flgn(c->n_envs, c->window, c->iters, c->odo_info, c->u_scale, d_x,
+                                d_odo, d_meas, d_meas_info, d_prior, d_prior_info, d_cov, d_u,
+                                d_status, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_thread_error(cudaGetErrorString(e));
+        return ASLAM_ERR_CUDA;
+    }
+    return ASLAM_OK;
+}
+
+aslam_status aslam_csm_config_init(aslam_csm_config *c) {
+    if (!c) return ASLAM_ERR_INVALID_ARG;
+    c->struct_size = sizeof(aslam_csm_config);
+    c->n_xy = 5;
+    c->n_th = 5;
+    c->sep = 1;
+    c->dth_rad = 0.01f;
+    return ASLAM_OK;
+}
+
+aslam_status aslam_csm(aslam_batch *b, const aslam_csm_config *c, const float *d_pose_pred,
+                       const float *d_ranges, float *d_pose_out, float *d_match,
+                       int64_t *d_scores, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!c || c->struct_size != sizeof(aslam_csm_config))
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "csm config NULL or struct_size mismatch");
+    if (b->hi.dims != 2) return fail_b(b, ASLAM_ERR_INVALID_ARG, "aslam_csm needs a 2-D batch");
+    if (c->n_xy < 0 || c->n_xy > csm_max_n() || c->n_th < 0 || c->n_th > csm_max_n())
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "n_xy and n_th must be in [0, 8]");
+    if (c->sep < 0 || !(c->dth_rad > 0.0f))
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "need sep >= 0 and dth_rad > 0");
+    if (!d_pose_pred || !d_pose_out || !d_match || !d_scores)
+        return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL pointer argument");
+    // stage the evidence maps in shared memory when the largest one fits
+    size_t need = 0;
+    for (int e = 0; e < b->hi.E; ++e) need = std::max(need, csm_map_bytes(b->hi.W[e], b->hi.H[e]));
+    const size_t budget = 160 * 1024;
+    const size_t map_bytes = need <= budget ? need : 0;
+    if (map_bytes > 0) CK(csm_set_smem(map_bytes), "aslam_csm: shared memory");
+    CK(launch_csm2d(b->p, c->n_xy, c->n_th, c->sep, c->dth_rad, map_bytes, d_pose_pred,
+                    d_ranges ? d_ranges : b->p.z, d_pose_out, d_match,
+                    reinterpret_cast<long long *>(d_scores), (cudaStream_t)stream),
+       "aslam_csm");
+    return ASLAM_OK;
+}
+
 aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d_u_new, int64_t t,
                             int64_t t_bridge, float *d_u_out, float *d_obs, void *stream) {
     if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");

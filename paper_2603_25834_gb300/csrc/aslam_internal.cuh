@@ -223,6 +223,17 @@ cudaError_t step2d_set_smem(size_t smem);
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
 cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s);
+int flgn_max_window();
+cudaError_t launch_flgn(int E, int L, int iters, const float *wo, float u_scale, float *x,
+                        const float *odo, const float *meas, const float *meas_info,
+                        const float *prior, const float *prior_info, float *cov, float *u,
+                        int *status, cudaStream_t s);
+int csm_max_n();
+size_t csm_map_bytes(int W, int H);
+cudaError_t csm_set_smem(size_t bytes);
+cudaError_t launch_csm2d(const Step2DParams &p, int n_xy, int n_th, int sep, float dth,
+                         size_t map_bytes, const float *pose_pred, const float *ranges,
+                         float *pose_out, float *match, long long *scores, cudaStream_t s);
 cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,
                             float *u_out, float *obs, int row, int col, cudaStream_t s);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,
