@@ -333,8 +333,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default/tuned)")
     ap.add_argument("--window", type=int, default=0, help="shared window side (0: default/tuned)")
-    ap.add_argument("--u-mode", default="caller", choices=["caller", "scanmatch"],
-                    help="U_t from the caller (a synthetic signal) or from the in-step scan match")
+    ap.add_argument("--u-mode", default="caller",
+                    choices=["caller", "scanmatch", "fixedlag", "fixedlag_weighted"],
+                    help="U_t from the caller (a synthetic signal), the in-step scan-match "
+                         "covariance, or the in-step SLAM backbone (CSM + fixed-lag window; "
+                         "_weighted: confidence-weighted map update)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -405,12 +408,20 @@ def main():
         workload = dict(WORKLOAD, envs=E_all)
     E = hi - lo
     cfg_kw["env_base"] = lo
+    if args.u_mode != "caller" and args.workload == "3d":
+        raise SystemExit("an in-step --u-mode is 2-D only")
     if args.u_mode == "scanmatch":
-        if args.workload == "3d":
-            raise SystemExit("--u-mode scanmatch is 2-D only")
         cfg_kw["u_mode"] = aslam.U_SCANMATCH
         workload = dict(workload,
                         u_t="in-step scan-match covariance (64 samples of one cell, Eq. 5-6)")
+    elif args.u_mode.startswith("fixedlag"):
+        cfg_kw["u_mode"] = aslam.U_FIXEDLAG
+        cfg_kw["slam_weighted_update"] = int(args.u_mode == "fixedlag_weighted")
+        workload = dict(workload,
+                        u_t="in-step SLAM backbone: CSM 11x11x11 + 8-pose fixed-lag window, "
+                            "3 GN iterations (Eq. 5-6)%s"
+                            % (", confidence-weighted map update"
+                               if args.u_mode == "fixedlag_weighted" else ""))
     batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE,
                           threads_per_cta=args.threads, window_cells=args.window, **cfg_kw)
     tuned = None
@@ -538,12 +549,13 @@ def main():
             kbytes["uq2d_kernel"] = 2 * int(batch.map_off[-1]) + E * (96 + 4)
     step_bytes = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
     peak, peak_kind = measured_peaks()
-    kern = max(kernel_ms, key=kernel_ms.get)
+    kern = max((k for k in kernel_ms if k in kbytes), key=kernel_ms.get)
     k_ms = kernel_ms[kern] / prof_steps
     achieved = kbytes[kern] / (k_ms / 1e3) / 1e9
     kernels = {k: {"ms_per_launch": v / prof_steps, "share": v / sum(kernel_ms.values()),
-                   "alg_bytes_per_launch": kbytes[k],
-                   "achieved_gbs": kbytes[k] / (v / prof_steps / 1e3) / 1e9}
+                   "alg_bytes_per_launch": kbytes.get(k),
+                   "achieved_gbs": (kbytes[k] / (v / prof_steps / 1e3) / 1e9
+                                    if k in kbytes else None)}
                for k, v in kernel_ms.items()}
     traffic = None
     tf = traffic_file(kern, args.workload)

@@ -147,10 +147,35 @@ typedef struct {
     float uq_odo_sigma[3];         /* > 0: x, y (m), theta (rad) per step (default 0.01) */
     float uq_prior_sigma[3];       /* > 0 (default 0.01) */
     float uq_u_scale;              /* >= 0 (default 0) */
+    /* The SLAM backbone in the step (u_mode = ASLAM_U_FIXEDLAG, 2-D only;
+     * Sec. III-D).  Each step: the pose predicted from the window's newest
+     * estimate and this step's odometry (v dt, 0, w dt) is matched against
+     * the map before this scan (aslam_csm with the csm_* parameters); the
+     * match enters a sliding window of slam_window poses as a pose factor of
+     * information w * slam_meas_info, the odometry as a factor of
+     * information 1 / uq_odo_sigma^2, and the oldest pose is anchored at its
+     * current estimate with slam_prior_info; slam_iters Gauss-Newton steps
+     * (aslam_fixed_lag_gn) give the newest pose's marginal covariance Sigma_t
+     * and U_t = det(Sigma_t)^(1/3) / (uq_u_scale or det(Q)^(1/3)).  An env's
+     * window restarts at its reset; its first scan adds no pose factor.  With
+     * slam_weighted_update = 1 the scan's log-odds increments are scaled by
+     * the normalised match score s (1 for an episode's first scan):
+     * L' = clamp(L + rint(s * (h*HIT + m*MISS))) (fp32).  The map is built
+     * at the true pose; the estimate feeds U_t, the reward and the
+     * observation. */
+    int32_t slam_window;           /* 1 .. 16 (default 8) */
+    int32_t slam_iters;            /* 0 .. 20 (default 3) */
+    int32_t csm_n_xy, csm_n_th;    /* 0 .. 8 (default 5, 5) */
+    int32_t csm_sep;               /* >= 0 (default 1) */
+    float csm_dth_rad;             /* > 0 (default 0.01) */
+    float slam_meas_info[3];       /* > 0 (default 4e4 m^-2, 4e4 m^-2, 1e6 rad^-2) */
+    float slam_prior_info[3];      /* > 0 (default 1e4) */
+    int32_t slam_weighted_update;  /* 0 (default) or 1 */
 } aslam_config;
 
 #define ASLAM_U_CALLER    0
 #define ASLAM_U_SCANMATCH 1
+#define ASLAM_U_FIXEDLAG  2
 
 #define ASLAM_MAX_BEAMS 1024
 #define ASLAM_MAX_MAP_SIDE 8192
@@ -174,7 +199,13 @@ typedef struct {
     const int64_t *h_map_off;      /* HOST [E+1] cell offsets of each env's grid */
     const int64_t *h_ray_off;      /* HOST [E+1] offsets of each env's beams */
     int32_t b_max;                 /* max beams over envs (observation row = b_max + 2) */
-    double *pose_cov;              /* [E, 6] (xx, xy, xt, yy, yt, tt) with ASLAM_U_SCANMATCH, else NULL */
+    double *pose_cov;              /* [E, 6] (xx, xy, xt, yy, yt, tt) with ASLAM_U_SCANMATCH or
+                                    * ASLAM_U_FIXEDLAG, else NULL */
+    float *slam_window;            /* [E, L, 3] pose estimates, oldest first (ASLAM_U_FIXEDLAG) */
+    int32_t *slam_count;           /* [E] poses in each window */
+    float *slam_match;             /* [E, 3] this step's (score_norm, margin, w) */
+    int64_t *slam_scores;          /* [E, 3] this step's (best, second, best index) */
+    float *slam_match_pose;        /* [E, 3] this step's matched pose */
 } aslam_state_ptrs;
 
 /* Fill `cfg` with defaults (version, struct_size, constants). */
@@ -356,10 +387,12 @@ aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d
  * kernels a step launches to *h_n_kernels and the number of timed steps to
  * *h_n_steps, and releases the events; ASLAM_ERR_STATE without a begin.
  * aslam_kernel_name(b, k) is the name of kernel k ("integrate2d_kernel",
- * "sense2d_kernel", "update2d_kernel"; 3-D: "step3d_kernel"), NULL past the
- * last.  A static string, owned by the library.
+ * "sense2d_kernel", then "uq2d_kernel" with ASLAM_U_SCANMATCH or
+ * "slam_predict2d_kernel", "csm2d_kernel", "slam_window2d_kernel" with
+ * ASLAM_U_FIXEDLAG, then "update2d_kernel"; 3-D: "step3d_kernel"), NULL
+ * past the last.  A static string, owned by the library.
  */
-#define ASLAM_MAX_STEP_KERNELS 4
+#define ASLAM_MAX_STEP_KERNELS 8
 aslam_status aslam_profile_begin(aslam_batch *b, int32_t max_steps);
 aslam_status aslam_profile_end(aslam_batch *b, double *h_ms, int32_t *h_n_kernels,
                                int32_t *h_n_steps);

@@ -77,13 +77,19 @@ class OrcCfg(C.Structure):
         ("u_mode", C.c_int32), ("uq_samples", C.c_int32), ("uq_step", C.c_float),
         ("uq_range_sigma", C.c_float), ("uq_odo", C.c_float * 3), ("uq_prior", C.c_float * 3),
         ("uq_u_scale", C.c_float),
+        ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
+        ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth", C.c_float),
+        ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
+        ("slam_weighted", C.c_int32),
     ]
 
 
 class OrcState(C.Structure):
     _fields_ = [("gt", P), ("belief", P), ("x", P), ("y", P), ("th", P), ("u_prev", P),
                 ("t", P), ("g", P), ("ep", P), ("done", P), ("visit", P), ("spawn", P),
-                ("sigma", P)]
+                ("sigma", P), ("win_x", P), ("win_odo", P), ("win_meas", P), ("win_minfo", P),
+                ("win_n", P), ("slam_match", P), ("slam_pose", P), ("slam_scores", P),
+                ("slam_upd_w", P)]
 
 
 class OrcOut(C.Structure):
@@ -292,7 +298,9 @@ DEFAULTS = dict(r_max=5.0, r_min=0.0, decimals=-1, fov=0.0, sigma=0.0, dt=0.1, v
                 lam_col=10.0, lam_explore=1.0, lam_abs=0.1, lam_delta=1.0, kappa=0.05,
                 u_hi=1.0, seed=20260325, u_mode=0, uq_samples=64, uq_step=0.0,
                 uq_range_sigma=0.01, uq_odo=(0.01, 0.01, 0.01), uq_prior=(0.01, 0.01, 0.01),
-                uq_u_scale=0.0)
+                uq_u_scale=0.0, slam_window=8, slam_iters=3, csm_n_xy=5, csm_n_th=5, csm_sep=1,
+                csm_dth=0.01, slam_meas_info=(4e4, 4e4, 1e6), slam_prior_info=(1e4, 1e4, 1e4),
+                slam_weighted=0)
 
 
 class OracleBatch2D:
@@ -333,6 +341,16 @@ class OracleBatch2D:
         pr = np.asarray(p["uq_prior"], np.float32).astype(np.float64)
         self.sigma = np.zeros((E, 6), np.float64)
         self.sigma[:, 0], self.sigma[:, 3], self.sigma[:, 5] = pr[0] ** 2, pr[1] ** 2, pr[2] ** 2
+        Lw = int(p["slam_window"])
+        self.win_x = np.zeros((E, Lw, 3), np.float32)
+        self.win_odo = np.zeros((E, Lw, 3), np.float32)
+        self.win_meas = np.zeros((E, Lw, 3), np.float32)
+        self.win_minfo = np.zeros((E, Lw, 3), np.float32)
+        self.win_n = np.zeros(E, np.int32)
+        self.slam_match = np.zeros((E, 3), np.float32)
+        self.slam_pose = np.zeros((E, 3), np.float32)
+        self.slam_scores = np.zeros((E, 3), np.int64)
+        self.slam_upd_w = np.zeros(E, np.float32)
         self.cfg = OrcCfg(
             n_envs=E, b_max=self.b_max, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"],
@@ -348,13 +366,22 @@ class OracleBatch2D:
             env_id=_ptr(self.env_ids), u_mode=p["u_mode"], uq_samples=p["uq_samples"],
             uq_step=p["uq_step"], uq_range_sigma=p["uq_range_sigma"],
             uq_odo=(C.c_float * 3)(*p["uq_odo"]), uq_prior=(C.c_float * 3)(*p["uq_prior"]),
-            uq_u_scale=p["uq_u_scale"])
+            uq_u_scale=p["uq_u_scale"], slam_window=p["slam_window"], slam_iters=p["slam_iters"],
+            csm_n_xy=p["csm_n_xy"], csm_n_th=p["csm_n_th"], csm_sep=p["csm_sep"],
+            csm_dth=p["csm_dth"], slam_meas_info=(C.c_float * 3)(*p["slam_meas_info"]),
+            slam_prior_info=(C.c_float * 3)(*p["slam_prior_info"]),
+            slam_weighted=p["slam_weighted"])
 
     def _state(self):
         return OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x),
                         y=_ptr(self.y), th=_ptr(self.th), u_prev=_ptr(self.u_prev),
                         t=_ptr(self.t), g=_ptr(self.g), ep=_ptr(self.ep), done=_ptr(self.done),
-                        visit=_ptr(self.visit), spawn=_ptr(self.spawn), sigma=_ptr(self.sigma))
+                        visit=_ptr(self.visit), spawn=_ptr(self.spawn), sigma=_ptr(self.sigma),
+                        win_x=_ptr(self.win_x), win_odo=_ptr(self.win_odo),
+                        win_meas=_ptr(self.win_meas), win_minfo=_ptr(self.win_minfo),
+                        win_n=_ptr(self.win_n), slam_match=_ptr(self.slam_match),
+                        slam_pose=_ptr(self.slam_pose), slam_scores=_ptr(self.slam_scores),
+                        slam_upd_w=_ptr(self.slam_upd_w))
 
     def step(self, actions, u=None, counts=False):
         """One step for all envs; returns a dict of this step's outputs."""

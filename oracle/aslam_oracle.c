@@ -355,6 +355,10 @@ typedef struct {
     /* in-step pose uncertainty (u_mode 1): see orc_scan_uncertainty */
     int32_t u_mode, uq_samples;
     float uq_step, uq_range_sigma, uq_odo[3], uq_prior[3], uq_u_scale;
+    /* SLAM backbone in the step (u_mode 2): see orc_slam_backbone */
+    int32_t slam_window, slam_iters, csm_n_xy, csm_n_th, csm_sep;
+    float csm_dth, slam_meas_info[3], slam_prior_info[3];
+    int32_t slam_weighted;
 } orc_cfg;
 
 typedef struct {
@@ -365,7 +369,12 @@ typedef struct {
     uint8_t *done;
     int32_t *visit;
     const float *spawn;        /* [E, n_spawn, 3] */
-    double *sigma;             /* [E, 6] pose covariance (xx, xy, xt, yy, yt, tt), u_mode 1 */
+    double *sigma;             /* [E, 6] pose covariance (xx, xy, xt, yy, yt, tt), u_mode 1 and 2 */
+    float *win_x, *win_odo, *win_meas, *win_minfo;   /* [E, L, 3] window (u_mode 2) */
+    int32_t *win_n;            /* [E] poses in the window */
+    float *slam_match, *slam_pose;                    /* [E, 3] this step's scan match */
+    int64_t *slam_scores;      /* [E, 3] */
+    float *slam_upd_w;         /* [E] this step's map-update weight */
 } orc_state;
 
 enum { ORC_NT = 12 };          /* reward terms per env */
@@ -439,6 +448,8 @@ static void orc_reset_env(const orc_cfg *cfg, orc_state *st, int e)
     memset(st->belief + off, 0, (size_t)n * sizeof(int16_t));
     for (int64_t v = cfg->visit_off[e]; v < cfg->visit_off[e + 1]; ++v)
         st->visit[v] = -1;
+    if (st->win_n)
+        st->win_n[e] = 0;
     if (st->sigma) {
         double *S = st->sigma + 6 * (int64_t)e;
         S[0] = (double)cfg->uq_prior[0] * cfg->uq_prior[0];
@@ -536,6 +547,102 @@ static double orc_scan_uncertainty(const orc_cfg *cfg, orc_state *st, int e, flo
     return cbrt(orc_det3(Sn)) / scale;
 }
 
+void orc_csm(const int16_t *belief, int32_t W, int32_t H, float res, float r_max, int32_t B,
+             double fov, const float *z, float x, float y, float th, int32_t n, int32_t m,
+             int32_t sep, float dth, float *pose_out, float *match, int64_t *scores);
+int orc_fixed_lag_gn(int L, int iters, double *x, const double *odo, const double *meas,
+                     const double *wm, const double *prior, const double *wp, const double *wo,
+                     double *cov_last);
+
+/* The SLAM backbone of one env in the step (Sec. III-D), on the map before
+ * this scan: the pose predicted from the window's newest estimate and the
+ * odometry (v dt, 0, w dt) (the integrated pose when the window is fresh)
+ * is matched against the grid by orc_csm; the window of at most L poses
+ * slides, takes the prediction, the odometry factor and the match as a pose
+ * factor of information w * meas_info (none for an episode's first scan),
+ * anchors its oldest pose at the current estimate with prior_info, and is
+ * solved by orc_fixed_lag_gn.  Returns U_t = det(Sigma_last)^(1/3) / scale
+ * and writes this scan's map-update weight (the normalised match score, 1
+ * for an episode's first scan). */
+static double orc_slam_backbone(const orc_cfg *cfg, orc_state *st, int e, float x, float y,
+                                float th, float ux, float uth, const float *z, float *upd_w)
+{
+    const int32_t W = cfg->map_w[e], H = cfg->map_h[e], B = cfg->n_beams[e];
+    const int L = cfg->slam_window;
+    float *wx = st->win_x + (int64_t)e * L * 3, *wo_ = st->win_odo + (int64_t)e * L * 3;
+    float *wm = st->win_meas + (int64_t)e * L * 3, *wi = st->win_minfo + (int64_t)e * L * 3;
+    int n = st->win_n[e];
+    float pred[3];
+    if (n == 0) {
+        pred[0] = x; pred[1] = y; pred[2] = th;
+    } else {
+        const float *last = wx + 3 * (n - 1);
+        float s, c;
+        orc_sincosf(last[2], &s, &c);
+        const float pi_f = (float)3.14159265358979323846;
+        const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
+        pred[0] = last[0] + c * ux;
+        pred[1] = last[1] + s * ux;
+        float t = last[2] + uth;
+        if (t >= pi_f) t = t - two_pi_f;
+        if (t < -pi_f) t = t + two_pi_f;
+        pred[2] = t;
+    }
+    float *pm = st->slam_pose + 3 * (int64_t)e, *mt = st->slam_match + 3 * (int64_t)e;
+    orc_csm(st->belief + cfg->map_off[e], W, H, cfg->res, cfg->r_max, B, cfg->fov, z, pred[0],
+            pred[1], pred[2], cfg->csm_n_xy, cfg->csm_n_th, cfg->csm_sep, cfg->csm_dth, pm, mt,
+            st->slam_scores + 3 * (int64_t)e);
+    if (n == L) {
+        for (int i = 0; i + 1 < L; ++i)
+            for (int q = 0; q < 3; ++q) {
+                wx[3 * i + q] = wx[3 * i + 3 + q];
+                wm[3 * i + q] = wm[3 * i + 3 + q];
+                wi[3 * i + q] = wi[3 * i + 3 + q];
+                if (i + 2 < L) wo_[3 * i + q] = wo_[3 * i + 3 + q];
+            }
+        n = L - 1;
+    }
+    const int first = n == 0;
+    const float wgt = first ? 0.0f : mt[2];
+    *upd_w = first ? 1.0f : mt[0];
+    const float odo_step[3] = {ux, 0.0f, uth};
+    for (int q = 0; q < 3; ++q) {
+        wx[3 * n + q] = pred[q];
+        wm[3 * n + q] = pm[q];
+        wi[3 * n + q] = wgt * cfg->slam_meas_info[q];
+        if (n > 0) wo_[3 * (n - 1) + q] = odo_step[q];
+    }
+    ++n;
+    st->win_n[e] = n;
+    double xd[48], od[48], md[48], id[48], prior[3], pinfo[3], wod[3], cov[9];
+    for (int k = 0; k < 3 * n; ++k) {
+        xd[k] = wx[k];
+        md[k] = wm[k];
+        id[k] = wi[k];
+        od[k] = k < 3 * (n - 1) ? wo_[k] : 0.0;
+    }
+    for (int q = 0; q < 3; ++q) {
+        prior[q] = wx[q];
+        pinfo[q] = cfg->slam_prior_info[q];
+        wod[q] = 1.0 / ((double)cfg->uq_odo[q] * cfg->uq_odo[q]);
+    }
+    orc_fixed_lag_gn(n, cfg->slam_iters, xd, od, md, id, prior, pinfo, wod, cov);
+    for (int k = 0; k < 3 * n; ++k)
+        wx[k] = (float)xd[k];
+    double *S = st->sigma + 6 * (int64_t)e;
+    S[0] = cov[0];
+    S[1] = 0.5 * (cov[1] + cov[3]);
+    S[2] = 0.5 * (cov[2] + cov[6]);
+    S[3] = cov[4];
+    S[4] = 0.5 * (cov[5] + cov[7]);
+    S[5] = cov[8];
+    double scale = cfg->uq_u_scale;
+    if (!(scale > 0.0))
+        scale = cbrt((double)cfg->uq_odo[0] * cfg->uq_odo[0] * cfg->uq_odo[1] * cfg->uq_odo[1] *
+                     cfg->uq_odo[2] * cfg->uq_odo[2]);
+    return cbrt(orc_det3(cov)) / scale;
+}
+
 int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const float *u_in,
                orc_out *out)
 {
@@ -629,10 +736,17 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
         }
         free(cells);
 
-        /* In-step uncertainty from the map before this scan (u_mode 1). */
-        float u_scan = 0.0f;
+        /* In-step uncertainty from the map before this scan (u_mode 1 and 2). */
+        float u_scan = 0.0f, upd_w = -1.0f;
         if (cfg->u_mode == 1)
             u_scan = (float)orc_scan_uncertainty(cfg, st, e, x, y, th);
+        if (cfg->u_mode == 2)
+            u_scan = (float)orc_slam_backbone(cfg, st, e, x, y, th, v * cfg->dt, w * cfg->dt,
+                                              out->z + (int64_t)e * cfg->b_max, &upd_w);
+        if (cfg->u_mode == 2 && !cfg->slam_weighted)
+            upd_w = -1.0f;
+        if (st->slam_upd_w)
+            st->slam_upd_w[e] = upd_w;
 
         /* Map update: per-step sum of increments, then one clamp per cell. */
         int16_t *L = st->belief + off;
@@ -644,7 +758,10 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
             }
             if (hc[k] == 0 && mc[k] == 0)
                 continue;
-            int32_t nl = (int32_t)L[k] + hc[k] * cfg->hit_q + mc[k] * cfg->miss_q;
+            int32_t d = hc[k] * cfg->hit_q + mc[k] * cfg->miss_q;
+            if (upd_w >= 0.0f)
+                d = (int32_t)rintf(upd_w * (float)d);     /* confidence-weighted scan */
+            int32_t nl = (int32_t)L[k] + d;
             if (nl > cfg->clamp_q) nl = cfg->clamp_q;
             if (nl < -cfg->clamp_q) nl = -cfg->clamp_q;
             L[k] = (int16_t)nl;
@@ -674,7 +791,7 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
 
         /* Reward, Eq. 7-17. */
         double Up = st->u_prev[e];
-        double U = cfg->u_mode == 1 ? (double)u_scan : (u_in ? (double)u_in[e] : 0.0);
+        double U = cfg->u_mode != 0 ? (double)u_scan : (u_in ? (double)u_in[e] : 0.0);
         double cgate = orc_clip((cfg->u_hi - Up) / cfg->u_hi, 0.0, 1.0);
         cgate = cgate * cgate;                                      /* Eq. 11 */
         double iota = orc_clip(fmax(Up - U, 0.0) / cfg->kappa, 0.0, 1.0); /* Eq. 12 */

@@ -29,6 +29,7 @@ REWARD_ENTROPY = 0
 REWARD_COMPOSITE = 1
 U_CALLER = 0
 U_SCANMATCH = 1
+U_FIXEDLAG = 2
 N_TERMS = 12
 TERM_NAMES = ["dH", "dcells", "I", "alpha_hug", "r_explore", "r_abs", "r_delta", "R",
               "collision", "dmin_meas", "dmin_true", "H"]
@@ -62,6 +63,10 @@ class AslamConfig(C.Structure):
         ("u_mode", C.c_int32), ("uq_samples", C.c_int32), ("uq_step_m", C.c_float),
         ("uq_range_sigma_m", C.c_float), ("uq_odo_sigma", C.c_float * 3),
         ("uq_prior_sigma", C.c_float * 3), ("uq_u_scale", C.c_float),
+        ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
+        ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth_rad", C.c_float),
+        ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
+        ("slam_weighted_update", C.c_int32),
     ]
 
 
@@ -69,7 +74,8 @@ class AslamStatePtrs(C.Structure):
     _fields_ = [("x", P), ("y", P), ("th", P), ("u_prev", P), ("t", P), ("g", P), ("ep", P),
                 ("done", P), ("belief", P), ("z", P), ("z_true", P), ("hit", P), ("counts", P),
                 ("ray_cells", P), ("gt_cells", P), ("terms", P), ("h_map_off", P),
-                ("h_ray_off", P), ("b_max", C.c_int32), ("pose_cov", P)]
+                ("h_ray_off", P), ("b_max", C.c_int32), ("pose_cov", P), ("slam_window", P),
+                ("slam_count", P), ("slam_match", P), ("slam_scores", P), ("slam_match_pose", P)]
 
 
 class AslamCsmConfig(C.Structure):
@@ -181,7 +187,7 @@ def config_defaults() -> AslamConfig:
 
 _FLOAT_KEYS = {"res_m", "r_max_m", "fov_rad", "noise_sigma_m", "dt_s", "v_max", "w_max",
                "sensor_z_m", "elev_min_rad", "elev_max_rad", "r_min_m", "uq_step_m",
-               "uq_range_sigma_m", "uq_u_scale",
+               "uq_range_sigma_m", "uq_u_scale", "csm_dth_rad",
                "d_crash", "d_full", "visit_cell_m", "logodds_scale", "lam_col", "lam_explore",
                "lam_abs", "lam_delta", "kappa", "u_hi"}
 
@@ -290,7 +296,16 @@ class Batch2D:
             gt_cells=self._view(sp.gt_cells, E, torch.int64),
             terms=self._view(sp.terms, E * N_TERMS, torch.float32).view(E, N_TERMS),
             pose_cov=(self._view(sp.pose_cov, 6 * E, torch.float64).view(E, 6)
-                      if sp.pose_cov else None))
+                      if sp.pose_cov else None),
+            slam_window=(self._view(sp.slam_window, 3 * E * self.cfg.slam_window, torch.float32)
+                         .view(E, self.cfg.slam_window, 3) if sp.slam_window else None),
+            slam_count=self._view(sp.slam_count, E, torch.int32) if sp.slam_count else None,
+            slam_match=(self._view(sp.slam_match, 3 * E, torch.float32).view(E, 3)
+                        if sp.slam_match else None),
+            slam_scores=(self._view(sp.slam_scores, 3 * E, torch.int64).view(E, 3)
+                         if sp.slam_scores else None),
+            slam_match_pose=(self._view(sp.slam_match_pose, 3 * E, torch.float32).view(E, 3)
+                             if sp.slam_match_pose else None))
 
     def env_belief(self, e):
         st = self.state()["belief"]
@@ -378,7 +393,7 @@ class Batch2D:
 
     def profile_end(self):
         """{kernel name: summed device ms} and the number of timed steps."""
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * 8)()
         nk, ns = C.c_int32(), C.c_int32()
         _check(self.lib.aslam_profile_end(self.handle, ms, C.byref(nk), C.byref(ns)), self.handle)
         names = [self.lib.aslam_kernel_name(self.handle, k).decode() for k in range(nk.value)]

@@ -38,6 +38,8 @@ struct Offsets {
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
     size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, err, tune_actions;
     size_t pose_cov, u_scan;
+    size_t win_x, win_odo, win_meas, win_minfo, win_n, slam_pred, slam_odo, csm_pose, csm_match,
+        csm_scores, slam_upd_w;
     size_t total;
 };
 
@@ -110,9 +112,23 @@ bool validate(const aslam_config *c, std::string *msg) {
     if (!(c->r_min_m >= 0.0f) || !(c->r_min_m <= c->r_max_m))
         return fail("r_min_m must be in [0, r_max_m]");
     if (c->range_decimals < -1 || c->range_decimals > 6) return fail("range_decimals out of [-1, 6]");
-    if (c->u_mode != ASLAM_U_CALLER && c->u_mode != ASLAM_U_SCANMATCH) return fail("unknown u_mode");
-    if (c->u_mode == ASLAM_U_SCANMATCH) {
-        if (c->dims != 2) return fail("u_mode ASLAM_U_SCANMATCH needs dims = 2");
+    if (c->u_mode != ASLAM_U_CALLER && c->u_mode != ASLAM_U_SCANMATCH &&
+        c->u_mode != ASLAM_U_FIXEDLAG)
+        return fail("unknown u_mode");
+    if (c->u_mode == ASLAM_U_FIXEDLAG) {
+        if (c->slam_window < 1 || c->slam_window > 16) return fail("slam_window out of [1, 16]");
+        if (c->slam_iters < 0 || c->slam_iters > 20) return fail("slam_iters out of [0, 20]");
+        if (c->csm_n_xy < 0 || c->csm_n_xy > 8 || c->csm_n_th < 0 || c->csm_n_th > 8)
+            return fail("csm_n_xy and csm_n_th must be in [0, 8]");
+        if (c->csm_sep < 0 || !(c->csm_dth_rad > 0.0f)) return fail("need csm_sep >= 0, csm_dth_rad > 0");
+        for (int q = 0; q < 3; ++q)
+            if (!(c->slam_meas_info[q] > 0.0f) || !(c->slam_prior_info[q] > 0.0f))
+                return fail("slam_meas_info and slam_prior_info must be > 0");
+        if (c->slam_weighted_update != 0 && c->slam_weighted_update != 1)
+            return fail("slam_weighted_update must be 0 or 1");
+    }
+    if (c->u_mode != ASLAM_U_CALLER) {
+        if (c->dims != 2) return fail("an in-step u_mode needs dims = 2");
         if (c->uq_samples < 1 || c->uq_samples > ASLAM_SOFT_MAX_SAMPLES)
             return fail("uq_samples out of [1, ASLAM_SOFT_MAX_SAMPLES]");
         if (!(c->uq_step_m >= 0.0f) || !(c->uq_range_sigma_m > 0.0f) || !(c->uq_u_scale >= 0.0f))
@@ -238,9 +254,22 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.queue = add(8);          // {next item, CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
-    const bool uq = c->u_mode == ASLAM_U_SCANMATCH;
+    const bool uq = c->u_mode == ASLAM_U_SCANMATCH || c->u_mode == ASLAM_U_FIXEDLAG;
+    const bool sl = c->u_mode == ASLAM_U_FIXEDLAG;
     o.pose_cov = add(uq ? 48 * E : 0);
     o.u_scan = add(uq ? 4 * E : 0);
+    const size_t win = sl ? 12 * E * (size_t)c->slam_window : 0;
+    o.win_x = add(win);
+    o.win_odo = add(win);
+    o.win_meas = add(win);
+    o.win_minfo = add(win);
+    o.win_n = add(sl ? 4 * E : 0);
+    o.slam_pred = add(sl ? 12 * E : 0);
+    o.slam_odo = add(sl ? 12 * E : 0);
+    o.csm_pose = add(sl ? 12 * E : 0);
+    o.csm_match = add(sl ? 12 * E : 0);
+    o.csm_scores = add(sl ? 24 * E : 0);
+    o.slam_upd_w = add(sl ? 4 * E : 0);
     o.total = pad_to(cur, kAlign);
     return o;
 }
@@ -307,7 +336,8 @@ float range_scale(int d) {
 namespace {
 
 int step_kernels(const aslam_batch *b) {
-    return b->hi.dims == 3 ? kStep3DKernels : kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH);
+    if (b->hi.dims == 3) return kStep3DKernels;
+    return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : b->p.u_mode == ASLAM_U_FIXEDLAG ? 3 : 0);
 }
 
 void release_profile(aslam_batch *b) {
@@ -466,6 +496,16 @@ aslam_status aslam_config_init(aslam_config *c) {
         c->uq_prior_sigma[i] = 0.01f;
     }
     c->uq_u_scale = 0.0f;
+    c->slam_window = 8;
+    c->slam_iters = 3;
+    c->csm_n_xy = 5;
+    c->csm_n_th = 5;
+    c->csm_sep = 1;
+    c->csm_dth_rad = 0.01f;
+    c->slam_meas_info[0] = c->slam_meas_info[1] = 4e4f;     // sigma 5 mm at full confidence
+    c->slam_meas_info[2] = 1e6f;                             // sigma 1 mrad
+    for (int q = 0; q < 3; ++q) c->slam_prior_info[q] = 1e4f;
+    c->slam_weighted_update = 0;
     return ASLAM_OK;
 }
 
@@ -554,7 +594,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.visit_cell = cfg->visit_cell_m;
         p.logodds_scale = cfg->logodds_scale;
         p.u_mode = cfg->u_mode;
-        if (cfg->u_mode == ASLAM_U_SCANMATCH) {
+        if (cfg->u_mode == ASLAM_U_SCANMATCH || cfg->u_mode == ASLAM_U_FIXEDLAG) {
             p.uq_K = cfg->uq_samples;
             p.uq_ds = cfg->uq_step_m > 0.0f ? cfg->uq_step_m : cfg->res_m;
             p.uq_inv_s2 = 1.0 / ((double)cfg->uq_range_sigma_m * cfg->uq_range_sigma_m);
@@ -567,6 +607,38 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
             p.uq_scale = cfg->uq_u_scale > 0.0f ? (double)cfg->uq_u_scale : std::cbrt(qdet);
             p.pose_cov = at<double>(b, o.pose_cov);
             p.u_scan = at<float>(b, o.u_scan);
+        }
+        if (cfg->u_mode == ASLAM_U_FIXEDLAG) {
+            p.slam_L = cfg->slam_window;
+            p.slam_iters = cfg->slam_iters;
+            p.csm_n_xy = cfg->csm_n_xy;
+            p.csm_n_th = cfg->csm_n_th;
+            p.csm_sep = cfg->csm_sep;
+            p.csm_dth = cfg->csm_dth_rad;
+            p.slam_weighted = cfg->slam_weighted_update;
+            for (int q = 0; q < 3; ++q) {
+                p.slam_meas_info[q] = cfg->slam_meas_info[q];
+                p.slam_prior_info[q] = cfg->slam_prior_info[q];
+                p.slam_wo[q] = 1.0 / ((double)cfg->uq_odo_sigma[q] * cfg->uq_odo_sigma[q]);
+            }
+            size_t need = 0;
+            for (int e = 0; e < E; ++e) need = std::max(need, csm_map_bytes(hi.W[e], hi.H[e]));
+            p.csm_map_bytes = need <= 160 * 1024 ? need : 0;
+            if (p.csm_map_bytes > 0) {
+                ce = csm_set_smem(p.csm_map_bytes);
+                if (ce != cudaSuccess) { st = cuda_fail(b, ce, "create: csm shared memory"); break; }
+            }
+            p.win_x = at<float>(b, o.win_x);
+            p.win_odo = at<float>(b, o.win_odo);
+            p.win_meas = at<float>(b, o.win_meas);
+            p.win_minfo = at<float>(b, o.win_minfo);
+            p.win_n = at<int>(b, o.win_n);
+            p.slam_pred = at<float>(b, o.slam_pred);
+            p.slam_odo = at<float>(b, o.slam_odo);
+            p.csm_pose = at<float>(b, o.csm_pose);
+            p.csm_match = at<float>(b, o.csm_match);
+            p.csm_scores = at<long long>(b, o.csm_scores);
+            p.slam_upd_w = at<float>(b, o.slam_upd_w);
         }
         p.lam_col = cfg->lam_col;
         p.lam_explore = cfg->lam_explore;
@@ -804,6 +876,11 @@ aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *o) {
     o->h_ray_off = reinterpret_cast<const int64_t *>(b->hi.ray_off.data());
     o->b_max = b->hi.b_max;
     o->pose_cov = p.pose_cov;
+    o->slam_window = p.win_x;
+    o->slam_count = p.win_n;
+    o->slam_match = p.csm_match;
+    o->slam_scores = reinterpret_cast<int64_t *>(p.csm_scores);
+    o->slam_match_pose = p.csm_pose;
     return ASLAM_OK;
 }
 
@@ -920,6 +997,14 @@ std::vector<Region> state_regions(aslam_batch *b) {
                              {p.Hq, 8 * E}, {p.belief, 2 * (size_t)b->hi.map_off[E]},
                              {p.visit, 4 * (size_t)b->hi.visit_off[E]}};
     if (p.pose_cov) r.push_back({p.pose_cov, 48 * E});
+    if (p.win_n) {
+        const size_t w = 12 * E * (size_t)p.slam_L;
+        r.push_back({p.win_x, w});
+        r.push_back({p.win_odo, w});
+        r.push_back({p.win_meas, w});
+        r.push_back({p.win_minfo, w});
+        r.push_back({p.win_n, 4 * E});
+    }
     return r;
 }
 }  // namespace
@@ -1031,7 +1116,7 @@ aslam_status aslam_csm(aslam_batch *b, const aslam_csm_config *c, const float *d
     if (map_bytes > 0) CK(csm_set_smem(map_bytes), "aslam_csm: shared memory");
     CK(launch_csm2d(b->p, c->n_xy, c->n_th, c->sep, c->dth_rad, map_bytes, d_pose_pred,
                     d_ranges ? d_ranges : b->p.z, d_pose_out, d_match,
-                    reinterpret_cast<long long *>(d_scores), (cudaStream_t)stream),
+                    reinterpret_cast<long long *>(d_scores), false, (cudaStream_t)stream),
        "aslam_csm");
     return ASLAM_OK;
 }
@@ -1102,7 +1187,11 @@ const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
                                       "update2d_kernel"};
     if (!b || k < 0) return nullptr;
     if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
+    static const char *const k2s[] = {"integrate2d_kernel", "sense2d_kernel",
+                                      "slam_predict2d_kernel", "csm2d_kernel",
+                                      "slam_window2d_kernel", "update2d_kernel"};
     if (b->p.u_mode == ASLAM_U_SCANMATCH) return k < kStep2DKernels + 1 ? k2u[k] : nullptr;
+    if (b->p.u_mode == ASLAM_U_FIXEDLAG) return k < kStep2DKernels + 3 ? k2s[k] : nullptr;
     return k < kStep2DKernels ? k2[k] : nullptr;
 }
 

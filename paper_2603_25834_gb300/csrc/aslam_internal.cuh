@@ -165,7 +165,19 @@ struct Step2DParams {
     float uq_ds, logodds_scale;
     double uq_inv_s2, uq_q[3], uq_prior[3], uq_scale;
     double *pose_cov;            // [E, 6]
-    float *u_scan;               // [E]                // global index of env 0 in the noise counter
+    float *u_scan;               // [E]
+    // SLAM backbone in the step (u_mode 2)
+    int slam_L, slam_iters, csm_n_xy, csm_n_th, csm_sep, slam_weighted;
+    float csm_dth, slam_meas_info[3], slam_prior_info[3];
+    double slam_wo[3];           // odometry information 1 / uq_odo_sigma^2
+    size_t csm_map_bytes;
+    float *win_x, *win_odo, *win_meas, *win_minfo;   // [E, L, 3]
+    int *win_n;                                       // [E]
+    float *slam_pred, *slam_odo;                      // [E, 3]
+    float *csm_pose, *csm_match;                      // [E, 3]
+    long long *csm_scores;                            // [E, 3]
+    float *slam_upd_w;           // [E] this step's scan weight (u_mode 2)
+    const float *upd_w;          // per-env update weight, or null (unweighted)                // global index of env 0 in the noise counter
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
@@ -223,6 +235,7 @@ cudaError_t step2d_set_smem(size_t smem);
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
 cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s);
+cudaError_t launch_slam2d(const Step2DParams &p, cudaStream_t s, const cudaEvent_t *ev);
 int flgn_max_window();
 cudaError_t launch_flgn(int E, int L, int iters, const float *wo, float u_scale, float *x,
                         const float *odo, const float *meas, const float *meas_info,
@@ -233,7 +246,8 @@ size_t csm_map_bytes(int W, int H);
 cudaError_t csm_set_smem(size_t bytes);
 cudaError_t launch_csm2d(const Step2DParams &p, int n_xy, int n_th, int sep, float dth,
                          size_t map_bytes, const float *pose_pred, const float *ranges,
-                         float *pose_out, float *match, long long *scores, cudaStream_t s);
+                         float *pose_out, float *match, long long *scores, bool reset_empty,
+                         cudaStream_t s);
 cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,
                             float *u_out, float *obs, int row, int col, cudaStream_t s);
 cudaError_t launch_step3d(const Step2DParams &p, int grid, int block, size_t smem,

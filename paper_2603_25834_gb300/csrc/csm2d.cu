@@ -14,10 +14,11 @@
 // more than `sep` steps away in some coordinate) are exact.
 //
 // One CTA per env.  The env's evidence map (one byte per cell) is staged in
-// shared memory when it fits; the rotations are processed one at a time:
-// the endpoint cells of all beams for th_k go to shared memory, then each
-// thread sums one candidate over a slice of the beams, and the slices are
-// added in a fixed order into a shared score table.
+// shared memory when it fits, and the returned beams are compacted once;
+// the rotations are processed one at a time: the endpoint cells of the
+// returned beams for th_k go to shared memory (one thread per beam), then
+// each thread sums one candidate over a slice of the beams, and the slices
+// are added in a fixed order into a shared score table.
 #include <cmath>
 
 #include "aslam_internal.cuh"
@@ -34,6 +35,7 @@ struct CsmArgs {
     int n_xy, n_th, sep;
     float dth;
     size_t map_bytes;            // shared bytes for the staged evidence map (0: read global)
+    bool reset_empty;            // in the step: an env resetting now has an empty map
     const float *pose_pred;      // [E, 3]
     const float *ranges;         // [sum B]
     float *pose_out;             // [E, 3]
@@ -49,6 +51,8 @@ __device__ __forceinline__ unsigned evidence(short L) {
 __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, const CsmArgs a) {
     extern __shared__ __align__(16) unsigned char s_map[];
     __shared__ int2 s_cell[ASLAM_MAX_BEAMS];
+    __shared__ int s_ret[ASLAM_MAX_BEAMS];       // returned beams, in beam order
+    __shared__ int s_wcnt[kCsmBlock / 32];
     __shared__ int s_score[kCsmMaxRot * kCsmMaxCand];
     __shared__ int s_part[kCsmBlock];
     __shared__ int s_nret;
@@ -57,8 +61,12 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     const int W = p.W[e], H = p.H[e], B = p.B[e];
     const short *L = p.belief + p.map_off[e];
     const bool staged = a.map_bytes > 0;
+    // inside the step the map of an env that resets now is cleared only by
+    // the update kernel: it is empty for the match (no evidence anywhere)
+    const bool empty = a.reset_empty && p.done[e] != 0;
     if (staged)
-        for (long long q = tid; q < (long long)W * H; q += nt) s_map[q] = (unsigned char)evidence(L[q]);
+        for (long long q = tid; q < (long long)W * H; q += nt)
+            s_map[q] = empty ? (unsigned char)0 : (unsigned char)evidence(L[q]);
     const float x = a.pose_pred[3 * e], y = a.pose_pred[3 * e + 1], th = a.pose_pred[3 * e + 2];
     const float *z = a.ranges + p.ray_off[e];
     const float2 *bcs = p.beam_cs + p.ray_off[e];
@@ -66,34 +74,40 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     const int nslice = nt / NC;                  // beam slices per candidate
     const int c = tid % NC, sl = tid / NC;
     const int ci_off = c % side - a.n_xy, cj_off = c / side - a.n_xy;
-    if (tid == 0) s_nret = 0;
-    __syncthreads();
+    // the returned beams (range < r_max), compacted in beam order once
+    const int lane = tid & 31, warp = tid >> 5;
+    int nret = 0;
+    for (int b0 = 0; b0 < B; b0 += nt) {
+        const int b = b0 + tid;
+        const bool ret = b < B && z[b] < p.r_max;
+        const unsigned m = __ballot_sync(0xffffffffu, ret);
+        if (lane == 0) s_wcnt[warp] = __popc(m);
+        __syncthreads();
+        int off = nret, round = 0;
+        for (int w = 0; w < nt / 32; ++w) {
+            if (w < warp) off += s_wcnt[w];
+            round += s_wcnt[w];
+        }
+        if (ret) s_ret[off + __popc(m & ((1u << lane) - 1u))] = b;
+        __syncthreads();
+        nret += round;
+    }
+    if (tid == 0) s_nret = nret;
     for (int k = 0; k < NK; ++k) {
         const float thk = fadd(th, fmul((float)(k - a.n_th), a.dth));
         float sk, ck;
         det_sincos(thk, sk, ck);
-        // endpoint cells of the returned beams, compacted in beam order
+        // endpoint cells of the returned beams for th_k
         __syncthreads();
-        if (tid < 32) {
-            int base = 0;
-            for (int b0 = 0; b0 < B; b0 += 32) {
-                const int b = b0 + tid;
-                const bool ret = b < B && z[b] < p.r_max;
-                const unsigned m = __ballot_sync(0xffffffffu, ret);
-                if (ret) {
-                    const float2 bc = bcs[b];
-                    const float cx = fsub(fmul(ck, bc.x), fmul(sk, bc.y));
-                    const float cy = fadd(fmul(sk, bc.x), fmul(ck, bc.y));
-                    const float ex = fadd(x, fmul(z[b], cx)), ey = fadd(y, fmul(z[b], cy));
-                    s_cell[base + __popc(m & ((1u << tid) - 1u))] =
-                        make_int2((int)floorf(fdiv(ex, p.res)), (int)floorf(fdiv(ey, p.res)));
-                }
-                base += __popc(m);
-            }
-            if (tid == 0 && k == 0) s_nret = base;
+        for (int q = tid; q < nret; q += nt) {
+            const int b = s_ret[q];
+            const float2 bc = bcs[b];
+            const float cx = fsub(fmul(ck, bc.x), fmul(sk, bc.y));
+            const float cy = fadd(fmul(sk, bc.x), fmul(ck, bc.y));
+            const float ex = fadd(x, fmul(z[b], cx)), ey = fadd(y, fmul(z[b], cy));
+            s_cell[q] = make_int2((int)floorf(fdiv(ex, p.res)), (int)floorf(fdiv(ey, p.res)));
         }
         __syncthreads();
-        const int nret = s_nret;
         int acc = 0;
         if (sl < nslice) {
             for (int q = sl; q < nret; q += nslice) {
@@ -101,7 +115,7 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
                 const int i = cc.x + ci_off, j = cc.y + cj_off;
                 if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
                     const long long kk = (long long)j * W + i;
-                    acc += staged ? (int)s_map[kk] : (int)evidence(L[kk]);
+                    acc += staged ? (int)s_map[kk] : (empty ? 0 : (int)evidence(L[kk]));
                 }
             }
             s_part[tid] = acc;
@@ -186,8 +200,10 @@ cudaError_t csm_set_smem(size_t bytes) {
 
 cudaError_t launch_csm2d(const Step2DParams &p, int n_xy, int n_th, int sep, float dth,
                          size_t map_bytes, const float *pose_pred, const float *ranges,
-                         float *pose_out, float *match, long long *scores, cudaStream_t s) {
-    CsmArgs a{n_xy, n_th, sep, dth, map_bytes, pose_pred, ranges, pose_out, match, scores};
+                         float *pose_out, float *match, long long *scores, bool reset_empty,
+                         cudaStream_t s) {
+    CsmArgs a{n_xy, n_th, sep, dth, map_bytes, reset_empty, pose_pred, ranges, pose_out, match,
+              scores};
     csm2d_kernel<<<p.E, kCsmBlock, map_bytes, s>>>(p, a);
     return cudaGetLastError();
 }

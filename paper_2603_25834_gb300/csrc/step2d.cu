@@ -354,11 +354,15 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
 // Entropy of log-odds L in 2^-40 nats from the half table h(|L|) (h is even).
 __device__ __forceinline__ long long h_of(const long long *s_lut, int L) { return s_lut[abs(L)]; }
 
-// Applies (h, m) to one cell's log-odds; returns the entropy change (2^-40 nats).
+// Applies (h, m) to one cell's log-odds, scaled by the env's update weight
+// wgt when wgt >= 0 (rint of the fp32 product); returns the entropy change
+// (2^-40 nats).
 __device__ __forceinline__ long long apply_cell(const Step2DParams &p, const long long *s_lut,
-                                                short &L, unsigned h, unsigned m) {
+                                                short &L, unsigned h, unsigned m, float wgt) {
     const int l0 = L;
-    int l1 = l0 + (int)h * p.hit_q + (int)m * p.miss_q;
+    int d = (int)h * p.hit_q + (int)m * p.miss_q;
+    if (wgt >= 0.0f) d = (int)rintf(fmul(wgt, (float)d));
+    int l1 = l0 + d;
     l1 = min(max(l1, -p.clamp_q), p.clamp_q);
     L = (short)l1;
     return h_of(s_lut, l1) - h_of(s_lut, l0);
@@ -366,13 +370,13 @@ __device__ __forceinline__ long long apply_cell(const Step2DParams &p, const lon
 
 // Applies the 8-bit counters of 8 consecutive cells (two words).
 __device__ __forceinline__ long long apply8(const Step2DParams &p, const long long *s_lut,
-                                            uint2 cw, int4 &lv, unsigned *dbg) {
+                                            uint2 cw, int4 &lv, unsigned *dbg, float wgt) {
     short *L = reinterpret_cast<short *>(&lv);
     long long dh = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const unsigned c8 = ((q < 4 ? cw.x : cw.y) >> ((q & 3) << 3)) & 0xffu;
-        if (c8) dh += apply_cell(p, s_lut, L[q], c8 >> 4, c8 & 0xfu);
+        if (c8) dh += apply_cell(p, s_lut, L[q], c8 >> 4, c8 & 0xfu, wgt);
         if (dbg) dbg[q] = ((c8 >> 4) << 16) | (c8 & 0xfu);
     }
     return dh;
@@ -381,13 +385,13 @@ __device__ __forceinline__ long long apply8(const Step2DParams &p, const long lo
 // Applies 32-bit (hits << 16 | misses) counters of 8 consecutive cells.
 __device__ __forceinline__ long long apply8_wide(const Step2DParams &p, const long long *s_lut,
                                                  const uint4 &c0, const uint4 &c1, int4 &lv,
-                                                 unsigned *dbg) {
+                                                 unsigned *dbg, float wgt) {
     short *L = reinterpret_cast<short *>(&lv);
     const unsigned c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     long long dh = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (c[q]) dh += apply_cell(p, s_lut, L[q], c[q] >> 16, c[q] & 0xffffu);
+        if (c[q]) dh += apply_cell(p, s_lut, L[q], c[q] >> 16, c[q] & 0xffffu, wgt);
         if (dbg) dbg[q] = c[q];
     }
     return dh;
@@ -576,6 +580,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         // ---- apply counters to the log-odds -------------------------------------
         long long dh = 0;
         short *Lenv = p.belief + sh.map_off;
+        const float wgt = p.upd_w ? p.upd_w[e] : -1.0f;   // confidence weight of the scan
         unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
         {
             // 8-cell chunks of the shared counters: the loads of kUnroll chunks
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     if (gk[u] >= 0) {
-                        dh += apply8(p, s_lut, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr);
+                        dh += apply8(p, s_lut, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr, wgt);
                         *reinterpret_cast<int4 *>(Lenv + gk[u]) = lv[u];
                     }
                 }
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                     cp[0] = make_uint4(0u, 0u, 0u, 0u);
                     cp[1] = make_uint4(0u, 0u, 0u, 0u);
                     int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
-                    dh += apply8_wide(p, s_lut, c0, c1, lv, dbg ? dbg + k : nullptr);
+                    dh += apply8_wide(p, s_lut, c0, c1, lv, dbg ? dbg + k : nullptr, wgt);
                     *reinterpret_cast<int4 *>(Lenv + k) = lv;
                 }
             }
@@ -647,7 +652,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
                 const unsigned c = s_near[q];
                 const long long k = (long long)j * W + i;
-                if (c) dh += apply_cell(p, s_lut, Lenv[k], c >> 16, c & 0xffffu);
+                if (c) dh += apply_cell(p, s_lut, Lenv[k], c >> 16, c & 0xffffu, wgt);
                 if (dbg) dbg[k] = c;
             }
         }
@@ -734,6 +739,7 @@ __global__ void init_state_kernel(const Step2DParams p) {
         p.done[e] = 0;
         p.Hq[e] = (long long)p.W[e] * p.H[e] * p.Dd[e] * p.lut[p.clamp_q];
         p.reward[e] = 0.0f;
+        if (p.win_n) p.win_n[e] = 0;
         if (p.pose_cov) {
             double *S = p.pose_cov + 6 * (long long)e;
             S[0] = p.uq_prior[0];
@@ -818,6 +824,18 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess) return e;
+    if (p.u_mode == 2) {
+        // SLAM backbone: predict, scan-match, window Gauss-Newton -> U_t
+        e = launch_slam2d(p, s, ev ? ev + 3 : nullptr);
+        if (e != cudaSuccess) return e;
+        Step2DParams q = p;
+        q.u_in = p.u_scan;
+        q.upd_w = p.slam_weighted ? p.slam_upd_w : nullptr;
+        update2d_kernel<<<grid, block, smem, s>>>(q);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[6], s);
+        return e;
+    }
     if (p.u_mode == 1) {
         // in-step U_t from the map before this scan; the update's reward reads it
         e = launch_uq2d(p, s);

@@ -35,7 +35,9 @@ def orc_params(cfg):
                  d_full="d_full", visit_cell_m="visit_cell", lam_col="lam_col",
                  lam_explore="lam_explore", lam_abs="lam_abs", lam_delta="lam_delta",
                  kappa="kappa", u_hi="u_hi", seed="seed", r_min_m="r_min",
-                 range_decimals="decimals")
+                 range_decimals="decimals", slam_window="slam_window",
+                 slam_iters="slam_iters", csm_n_xy="csm_n_xy", csm_n_th="csm_n_th",
+                 csm_sep="csm_sep", csm_dth_rad="csm_dth")
     return {names[k]: v for k, v in cfg.items() if k in names}
 
 
