@@ -59,6 +59,17 @@ namespace {
 
 constexpr int kSenseSmemMax = 200 * 1024;   // ground truth of up to 1.6 M cells
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start once every CTA of the kernel before it has called
+// pdl_trigger (so all of those CTAs already hold their resources); it runs
+// its independent prologue, then pdl_wait blocks until that kernel has
+// finished and its writes are visible.  Without the launch attribute both
+// are no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned gt_bit(const unsigned *bits, int k) {
     return (bits[k >> 5] >> (k & 31)) & 1u;
 }
@@ -121,6 +132,7 @@ __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W
 // Integration kernel: one thread per env
 // ---------------------------------------------------------------------------
 __global__ void integrate2d_kernel(const Step2DParams p) {
+    pdl_trigger();                       // the sensing grid may start staging its maps
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += gridDim.x * blockDim.x) {
         const int W = p.W[e], H = p.H[e];
         EnvSense es;
@@ -156,6 +168,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         // while the beams are traced
         prefetch_l2(p.belief + p.map_off[e], (unsigned)min(2LL * W * H, 1LL << 30));
     }
+    pdl_trigger();                       // the update grid may start its prologue
     {
         // the env's ground truth, one bit per cell, into shared memory
         const int words = (int)(((long long)W * H + 31) >> 5);
@@ -163,6 +176,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
         for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
     }
+    pdl_wait();                          // the integration's EnvSense records are complete
     __syncthreads();
     int gc = 0;
     float dmin_m = p.r_max, dmin_t = p.r_max;
@@ -482,6 +496,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
 
     // entropy half table h(|L|), L = 0..clamp_q, shared by every env of the CTA
     for (int q = tid; q <= p.clamp_q; q += nt) s_lut[q] = __ldg(&p.lut[p.clamp_q + q]);
+    pdl_wait();                          // the sensing kernel's ray codes are complete
     if (tid == 0) load_env(p, (int)atomicAdd(p.queue, 1u), shb[0]);
     __syncthreads();
     int it = 0;
@@ -809,6 +824,24 @@ cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm) {
 
 // Integration (one thread per env), sensing (one CTA per bundle of
 // kSenseBlock beams) and the persistent per-env update CTAs.
+// Launches kernel<<<grid, block, smem, s>>>(p), as a programmatic dependent
+// of the preceding kernel when `pdl` is set.
+template <class Kernel>
+cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                       const Step2DParams &p) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev) {
     cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
@@ -817,10 +850,12 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;
+    // without per-kernel events the sensing and update kernels are launched
+    // as programmatic dependents of the kernel before them
+    const bool pdl = ev == nullptr;
     if (p.n_bundles > 0) {
         const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
-        sense2d_kernel<<<p.n_bundles, p.sense_block, gt_bytes, s>>>(p);
-        e = cudaGetLastError();
+        e = launch_pdl(sense2d_kernel, dim3(p.n_bundles), dim3(p.sense_block), gt_bytes, s, pdl, p);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess) return e;
@@ -848,8 +883,7 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], s);
         return e;
     }
-    update2d_kernel<<<grid, block, smem, s>>>(p);
-    e = cudaGetLastError();
+    e = launch_pdl(update2d_kernel, dim3(grid), dim3(block), smem, s, pdl && p.n_bundles > 0, p);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
     return e;
 }
