@@ -18,6 +18,8 @@
 //                 U = det(Sigma)^(1/3) (D-optimality, Table I "D-opt")
 #include <math.h>
 
+#include <algorithm>
+
 #include <string>
 
 #include "aslam_internal.cuh"
@@ -61,10 +63,11 @@ __device__ __forceinline__ void bilinear(const SoftParams &p, const float *L, fl
     s.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * p.inv_res;
 }
 
-// p = sigmoid(l) and q = 1 - p, each without cancellation.
+// p = sigmoid(l) and q = 1 - p, each without cancellation (fast exp and
+// divide: a few ulp, far inside the ranges' tolerance).
 __device__ __forceinline__ void sigmoid_pq(float l, float &pr, float &q) {
-    const float e = expf(-fabsf(l));
-    const float inv = 1.0f / (1.0f + e);
+    const float e = __expf(-fabsf(l));
+    const float inv = __fdividef(1.0f, 1.0f + e);
     if (l >= 0.f) {
         pr = inv;
         q = e * inv;
@@ -228,7 +231,9 @@ __device__ __forceinline__ double det3(const double *A) {
            A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
-__global__ void gn_kernel(const SoftParams p, const float *z, int iters, float *pose_out,
+// One thread per beam; three CTAs per SM hide the latency of the sample chains.
+__global__ void __launch_bounds__(512, 3) gn_kernel(const SoftParams p, const float *z, int iters,
+                                                    float *pose_out,
                           float *cov, float *u_out) {
     __shared__ float red[9][32];
     __shared__ float s_pose[3];
@@ -259,6 +264,7 @@ __global__ void gn_kernel(const SoftParams p, const float *z, int iters, float *
             double A[9] = {v[0] + (double)p.mu, v[1], v[2], v[1], v[3] + (double)p.mu, v[4],
                            v[2], v[4], v[5] + (double)p.mu};
             const double det = det3(A);
+            const double idet = 1.0 / det;
             if (it < iters) {
                 double d[3];
                 for (int col = 0; col < 3; ++col) {
@@ -267,7 +273,7 @@ __global__ void gn_kernel(const SoftParams p, const float *z, int iters, float *
                     M[col] = -(double)v[6];
                     M[3 + col] = -(double)v[7];
                     M[6 + col] = -(double)v[8];
-                    d[col] = det3(M) / det;
+                    d[col] = det3(M) * idet;
                 }
                 s_pose[0] = (float)((double)s_pose[0] + d[0]);
                 s_pose[1] = (float)((double)s_pose[1] + d[1]);
@@ -278,15 +284,15 @@ __global__ void gn_kernel(const SoftParams p, const float *z, int iters, float *
                 pose_out[3 * e + 2] = s_pose[2];
                 // Sigma = sigma^2 A^{-1} (adjugate / det), U = det(Sigma)^(1/3)
                 double Ai[9];
-                Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
-                Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
-                Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
-                Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
-                Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
-                Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
-                Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
-                Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
-                Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+                Ai[0] = (A[4] * A[8] - A[5] * A[7]) * idet;
+                Ai[1] = (A[2] * A[7] - A[1] * A[8]) * idet;
+                Ai[2] = (A[1] * A[5] - A[2] * A[4]) * idet;
+                Ai[3] = (A[5] * A[6] - A[3] * A[8]) * idet;
+                Ai[4] = (A[0] * A[8] - A[2] * A[6]) * idet;
+                Ai[5] = (A[2] * A[3] - A[0] * A[5]) * idet;
+                Ai[6] = (A[3] * A[7] - A[4] * A[6]) * idet;
+                Ai[7] = (A[1] * A[6] - A[0] * A[7]) * idet;
+                Ai[8] = (A[0] * A[4] - A[1] * A[3]) * idet;
                 if (cov)
                     for (int q = 0; q < 9; ++q) cov[9 * e + q] = (float)(p.sigma2 * Ai[q]);
                 if (u_out) {
@@ -350,7 +356,7 @@ aslam_status make_params(const aslam_soft_config *c, const float *L, const float
 
 int soft_block(int B) {
     int t = (B + 31) / 32 * 32;
-    return t < 64 ? 64 : (t > 256 ? 256 : t);
+    return t < 64 ? 64 : (t > 512 ? 512 : t);
 }
 
 aslam_status launch_ok(const char *where) {
@@ -410,9 +416,13 @@ aslam_status aslam_soft_range_bwd(const aslam_soft_config *c, const float *d_log
     aslam_status st = make_params(c, d_logodds, d_pose, &p);
     if (st != ASLAM_OK) return st;
     if (!d_grad_ranges || !d_grad_pose) return soft_fail(ASLAM_ERR_INVALID_ARG, "NULL gradient");
-    const int block = 128;
+    // as many beams per CTA as keep three CTAs' transmittances (4 K bytes a
+    // thread) within about 72 KB each, at most 256 and no more than the beams
+    int block = (int)((72 * 1024) / (4 * (size_t)p.K)) & ~31;
+    block = std::min(std::max(block, 32), std::min(256, (p.B + 31) / 32 * 32));
     const size_t smem = sizeof(float) * (size_t)p.K * block;
-    if (smem > 48 * 1024) {
+    {
+        // the static reduction buffer counts against the same per-block limit
         cudaError_t ce = cudaFuncSetAttribute(soft_bwd_kernel,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ce != cudaSuccess) return soft_fail(ASLAM_ERR_CUDA, "soft_range_bwd: shared memory");
