@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     extern __shared__ __align__(16) unsigned char s_map[];
     __shared__ int2 s_cell[ASLAM_MAX_BEAMS];
     __shared__ int s_ret[ASLAM_MAX_BEAMS];       // returned beams, in beam order
+    __shared__ float2 s_rot[kCsmMaxRot];         // (sin, cos) of each rotation
     __shared__ int s_wcnt[kCsmBlock / 32];
     __shared__ int s_score[kCsmMaxRot * kCsmMaxCand];
     __shared__ int s_part[kCsmBlock];
@@ -64,9 +65,22 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     // inside the step the map of an env that resets now is cleared only by
     // the update kernel: it is empty for the match (no evidence anywhere)
     const bool empty = a.reset_empty && p.done[e] != 0;
-    if (staged)
-        for (long long q = tid; q < (long long)W * H; q += nt)
-            s_map[q] = empty ? (unsigned char)0 : (unsigned char)evidence(L[q]);
+    // rows padded by 4 bytes: vertically adjacent cells fall in different banks
+    const int ws = W + 4;
+    if (staged) {
+        // (row, column) of element q tracked incrementally (no division per cell)
+        int ii = tid % W, jj = tid / W;
+        const int di = nt % W, dj = nt / W;
+        for (long long q = tid; q < (long long)W * H; q += nt) {
+            s_map[(long long)jj * ws + ii] = empty ? (unsigned char)0 : (unsigned char)evidence(L[q]);
+            ii += di;
+            jj += dj;
+            if (ii >= W) {
+                ii -= W;
+                ++jj;
+            }
+        }
+    }
     const float x = a.pose_pred[3 * e], y = a.pose_pred[3 * e + 1], th = a.pose_pred[3 * e + 2];
     const float *z = a.ranges + p.ray_off[e];
     const float2 *bcs = p.beam_cs + p.ray_off[e];
@@ -93,12 +107,15 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
         nret += round;
     }
     if (tid == 0) s_nret = nret;
-    for (int k = 0; k < NK; ++k) {
-        const float thk = fadd(th, fmul((float)(k - a.n_th), a.dth));
+    if (tid < NK) {
         float sk, ck;
-        det_sincos(thk, sk, ck);
+        det_sincos(fadd(th, fmul((float)(tid - a.n_th), a.dth)), sk, ck);
+        s_rot[tid] = make_float2(sk, ck);
+    }
+    for (int k = 0; k < NK; ++k) {
         // endpoint cells of the returned beams for th_k
         __syncthreads();
+        const float sk = s_rot[k].x, ck = s_rot[k].y;
         for (int q = tid; q < nret; q += nt) {
             const int b = s_ret[q];
             const float2 bc = bcs[b];
@@ -115,7 +132,8 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
                 const int i = cc.x + ci_off, j = cc.y + cj_off;
                 if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
                     const long long kk = (long long)j * W + i;
-                    acc += staged ? (int)s_map[kk] : (empty ? 0 : (int)evidence(L[kk]));
+                    acc += staged ? (int)s_map[(long long)j * ws + i]
+                                  : (empty ? 0 : (int)evidence(L[kk]));
                 }
             }
             s_part[tid] = acc;
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
 int csm_max_n() { return kCsmMaxN; }
 
 size_t csm_map_bytes(int W, int H) {
-    const size_t n = (size_t)W * H;
+    const size_t n = (size_t)(W + 4) * H;               // padded rows
     return (n + 15) & ~(size_t)15;
 }
 

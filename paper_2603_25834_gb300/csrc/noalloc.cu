@@ -117,7 +117,7 @@ __global__ void scan_rays_kernel(const ScanParams p) {
                 const long long n = lastx ? nx0 + ((long long)(abs(i - i0) - 1) << 16)
                                           : ny0 + ((long long)(abs(j - j0) - 1) << 16);
                 const long long ad = lastx ? adx : ady;
-                z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+                z_true = fmul(fmul(fdiv(__int2float_rn((int)n), __int2float_rn((int)ad)), 16384.0f), p.res);
             }
         }
         z = z_true;

@@ -107,6 +107,25 @@ __device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray,
     return b;
 }
 
+// A 64-bit integer as an approximate float, from its 32-bit halves (exact
+// 32-bit conversions only).
+__device__ __forceinline__ float approx_f32(long long v) {
+    return fmaf(__int2float_rn((int)(v >> 32)), 4294967296.0f, __uint2float_rn((unsigned)v));
+}
+
+// floor(D / (ad * 2^16)) for 0 <= D < 2^60, 0 < ad <= 2^30, when the quotient
+// is at most a map side (8192): a float estimate (relative error ~2^-22, so
+// off by at most one) corrected by exact 64-bit comparisons.
+__device__ __forceinline__ long long floor_div_q16(long long D, long long ad) {
+    const long long dv = ad << 16;
+    const float qf = __fdividef(approx_f32(D), approx_f32(dv));
+    long long q = qf < 1.0e9f ? (long long)__float2int_rd(qf) : 1000000000LL;
+    q = q < 0 ? 0 : q;
+    for (int t = 0; t < 8 && q * dv > D; ++t) --q;
+    for (int t = 0; t < 8 && (q + 1) * dv <= D; ++t) ++q;
+    return q;
+}
+
 // Number of cells of the beam's walk that lie in the W x H map (the walk
 // leaves at the first crossing past the last column or row in its way).
 __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W, int H) {
@@ -119,12 +138,12 @@ __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W
     if (NX * b.ady < NY * b.adx) {
         // leaves along x: y-crossings before it (ties go Y first, so <=)
         const long long D = NX * b.ady - b.ny0 * b.adx;
-        const long long cy = D < 0 ? 0 : D / (b.adx << 16) + 1;
+        const long long cy = D < 0 ? 0 : floor_div_q16(D, b.adx) + 1;
         return rx + (int)cy + 1;
     }
     // leaves along y: x-crossings strictly before it
     const long long D = NY * b.adx - b.nx0 * b.ady;
-    const long long cx = D <= 0 ? 0 : (D - 1) / (b.ady << 16) + 1;
+    const long long cx = D <= 0 ? 0 : floor_div_q16(D - 1, b.ady) + 1;
     return ry + (int)cx + 1;
 }
 
@@ -225,7 +244,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                     const long long n = lastx ? bm.nx0 + ((long long)(kx - 1) << 16)
                                               : bm.ny0 + ((long long)(st - kx - 1) << 16);
                     const long long ad = lastx ? bm.adx : bm.ady;
-                    z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+                    z_true = fmul(fmul(fdiv(__int2float_rn((int)n), __int2float_rn((int)ad)), 16384.0f), p.res);
                 }
             }
             gc = cells;
@@ -319,7 +338,7 @@ __device__ __forceinline__ bool x_before_y(const Beam &b, int m, int n) {
 __device__ __forceinline__ int x_steps_after(const Beam &b, int s) {
     if (b.adx == 0) return 0;
     if (b.ady == 0) return s;
-    int kx = __float2int_rd(__fdividef((float)s * (float)b.adx, (float)(b.adx + b.ady)));
+    int kx = __float2int_rd(__fdividef((float)s * (float)(int)b.adx, (float)(int)(b.adx + b.ady)));
     kx = min(max(kx, 0), s);
     // kx is the largest value whose kx-th x-crossing precedes the
     // (s-kx+1)-th y-crossing; that predicate falls from true to false

@@ -171,8 +171,11 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
         const int rounds = (sh.B + nt - 1) / nt;
         for (int q = 0; q < rounds; ++q) {
             // every lane runs the same number of rounds: the warp-synchronous
-            // belief walk below needs whole warps
-            const int b = tid + q * nt;
+            // belief walk below needs whole warps.  A warp keeps 32 adjacent
+            // azimuths, but the sector it takes rotates from round to round, so
+            // that warps facing near walls and warps facing open space even out
+            // before the CTA's barrier.
+            const int b = (q * nwarps + (warp + 5 * q) % nwarps) * 32 + lane;
             const bool valid = b < sh.B;
             Ray3 r;
             Walk3 w0;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                             if (w.last == 0) { n = r.nx0 + ((long long)(abs(w.i - i0) - 1) << 16); ad = r.ax; }
                             else if (w.last == 1) { n = r.ny0 + ((long long)(abs(w.j - j0) - 1) << 16); ad = r.ay; }
                             else { n = r.nz0 + ((long long)(abs(w.k - k0) - 1) << 16); ad = r.az; }
-                            z_true = fmul(fmul(fdiv(__ll2float_rn(n), __ll2float_rn(ad)), 16384.0f), p.res);
+                            z_true = fmul(fmul(fdiv(__int2float_rn((int)n), __int2float_rn((int)ad)), 16384.0f), p.res);
                         }
                     }
                     gc += cells;
