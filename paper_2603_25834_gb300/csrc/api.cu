@@ -295,6 +295,9 @@ struct aslam_batch {
     // per-kernel timing (aslam_profile_begin/end): (kernels + 1) events per step
     std::vector<cudaEvent_t> prof_ev;
     int prof_cap = 0, prof_n = 0;
+    // staged-map layout of aslam_csm for the last search width (-1: none)
+    int csm_n = -1, csm_ws = 0;
+    size_t csm_bytes = 0;
 };
 
 namespace {
@@ -621,8 +624,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                 p.slam_prior_info[q] = cfg->slam_prior_info[q];
                 p.slam_wo[q] = 1.0 / ((double)cfg->uq_odo_sigma[q] * cfg->uq_odo_sigma[q]);
             }
-            size_t need = 0;
-            for (int e = 0; e < E; ++e) need = std::max(need, csm_map_bytes(hi.W[e], hi.H[e]));
+            const size_t need = csm_map_layout(hi.W.data(), hi.H.data(), E, p.csm_n_xy, &p.csm_ws);
             p.csm_map_bytes = need <= 160 * 1024 ? need : 0;
             if (p.csm_map_bytes > 0) {
                 ce = csm_set_smem(p.csm_map_bytes);
@@ -1109,12 +1111,15 @@ aslam_status aslam_csm(aslam_batch *b, const aslam_csm_config *c, const float *d
     if (!d_pose_pred || !d_pose_out || !d_match || !d_scores)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "NULL pointer argument");
     // stage the evidence maps in shared memory when the largest one fits
-    size_t need = 0;
-    for (int e = 0; e < b->hi.E; ++e) need = std::max(need, csm_map_bytes(b->hi.W[e], b->hi.H[e]));
+    if (b->csm_n != c->n_xy) {
+        b->csm_bytes = csm_map_layout(b->hi.W.data(), b->hi.H.data(), b->hi.E, c->n_xy, &b->csm_ws);
+        b->csm_n = c->n_xy;
+    }
+    const int ws = b->csm_ws;
     const size_t budget = 160 * 1024;
-    const size_t map_bytes = need <= budget ? need : 0;
+    const size_t map_bytes = b->csm_bytes <= budget ? b->csm_bytes : 0;
     if (map_bytes > 0) CK(csm_set_smem(map_bytes), "aslam_csm: shared memory");
-    CK(launch_csm2d(b->p, c->n_xy, c->n_th, c->sep, c->dth_rad, map_bytes, d_pose_pred,
+    CK(launch_csm2d(b->p, c->n_xy, c->n_th, c->sep, c->dth_rad, map_bytes, ws, d_pose_pred,
                     d_ranges ? d_ranges : b->p.z, d_pose_out, d_match,
                     reinterpret_cast<long long *>(d_scores), false, (cudaStream_t)stream),
        "aslam_csm");

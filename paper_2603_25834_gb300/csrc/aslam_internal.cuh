@@ -170,7 +170,8 @@ struct Step2DParams {
     int slam_L, slam_iters, csm_n_xy, csm_n_th, csm_sep, slam_weighted;
     float csm_dth, slam_meas_info[3], slam_prior_info[3];
     double slam_wo[3];           // odometry information 1 / uq_odo_sigma^2
-    size_t csm_map_bytes;
+    size_t csm_map_bytes;                             // staged evidence map (0: read global)
+    int csm_ws;                                       // its row stride, bytes
     float *win_x, *win_odo, *win_meas, *win_minfo;   // [E, L, 3]
     int *win_n;                                       // [E]
     float *slam_pred, *slam_odo;                      // [E, 3]
@@ -242,10 +243,12 @@ cudaError_t launch_flgn(int E, int L, int iters, const float *wo, float u_scale,
                         const float *prior, const float *prior_info, float *cov, float *u,
                         int *status, cudaStream_t s);
 int csm_max_n();
-size_t csm_map_bytes(int W, int H);
+// shared bytes of the bordered evidence maps of E envs for a search of
+// +-n cells, and their row stride in bytes (*ws)
+size_t csm_map_layout(const int *W, const int *H, int E, int n, int *ws);
 cudaError_t csm_set_smem(size_t bytes);
 cudaError_t launch_csm2d(const Step2DParams &p, int n_xy, int n_th, int sep, float dth,
-                         size_t map_bytes, const float *pose_pred, const float *ranges,
+                         size_t map_bytes, int ws, const float *pose_pred, const float *ranges,
                          float *pose_out, float *match, long long *scores, bool reset_empty,
                          cudaStream_t s);
 cudaError_t launch_bridge_u(const float *u_old, const float *u_new, float alpha, int E,

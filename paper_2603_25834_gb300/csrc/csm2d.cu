@@ -13,12 +13,21 @@
 // lowest (k, j, i) index) and the second best (best score among candidates
 // more than `sep` steps away in some coordinate) are exact.
 //
-// One CTA per env.  The env's evidence map (one byte per cell) is staged in
-// shared memory when it fits, and the returned beams are compacted once;
-// the rotations are processed one at a time: the endpoint cells of the
-// returned beams for th_k go to shared memory (one thread per beam), then
-// each thread sums one candidate over a slice of the beams, and the slices
-// are added in a fixed order into a shared score table.
+// One CTA per env.  The returned beams are compacted once, then the
+// rotations are processed one at a time: the endpoint cells of the returned
+// beams for th_k go to shared memory (one thread per beam), each thread sums
+// one candidate over a slice of the beams, and the slices are added in a
+// fixed order into a shared score table.
+//
+// When it fits, the env's evidence map (one byte per cell) is staged in
+// shared memory inside a zero border of 2 n_xy cells, followed by 2 n_xy + 1
+// zero rows (the sentinel block).  An endpoint cell more than n_xy cells
+// outside the map scores 0 for every candidate and is pointed at the centre
+// of the sentinel block; any other endpoint's candidate cells all lie in the
+// bordered map.  So the per-rotation staging stores one shared address per
+// beam and the candidate loop is a load, an add, and nothing else.  The row
+// stride is chosen on the host so that the candidate rows one warp reads
+// fall in distinct shared-memory banks.
 #include <cmath>
 
 #include "aslam_internal.cuh"
@@ -35,6 +44,7 @@ struct CsmArgs {
     int n_xy, n_th, sep;
     float dth;
     size_t map_bytes;            // shared bytes for the staged evidence map (0: read global)
+    int ws;                      // row stride of the staged map, bytes (a multiple of 4)
     bool reset_empty;            // in the step: an env resetting now has an empty map
     const float *pose_pred;      // [E, 3]
     const float *ranges;         // [sum B]
@@ -48,9 +58,18 @@ __device__ __forceinline__ unsigned evidence(short L) {
     return (unsigned)(v < 255 ? v : 255);
 }
 
+// evidence bytes of the two int16 cells in w, low cell in the low byte
+__device__ __forceinline__ unsigned evidence2(unsigned w) {
+    return evidence((short)(w & 0xffffu)) | evidence((short)(w >> 16)) << 8;
+}
+
+// column of map cell 0 in the staged rows: the 2n-cell border rounded up to
+// a word, so that groups of 8 cells are stored as two aligned words
+__host__ __device__ __forceinline__ int csm_col0(int n) { return (2 * n + 3) & ~3; }
+
 __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, const CsmArgs a) {
     extern __shared__ __align__(16) unsigned char s_map[];
-    __shared__ int2 s_cell[ASLAM_MAX_BEAMS];
+    __shared__ int2 s_cell[ASLAM_MAX_BEAMS];     // staged map: .x is the shared address
     __shared__ int s_ret[ASLAM_MAX_BEAMS];       // returned beams, in beam order
     __shared__ float2 s_rot[kCsmMaxRot];         // (sin, cos) of each rotation
     __shared__ int s_wcnt[kCsmBlock / 32];
@@ -65,19 +84,46 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     // inside the step the map of an env that resets now is cleared only by
     // the update kernel: it is empty for the match (no evidence anywhere)
     const bool empty = a.reset_empty && p.done[e] != 0;
-    // rows padded by 4 bytes: vertically adjacent cells fall in different banks
-    const int ws = W + 4;
+    const int ws = a.ws, brd = 2 * a.n_xy, col0 = csm_col0(a.n_xy);
     if (staged) {
-        // (row, column) of element q tracked incrementally (no division per cell)
-        int ii = tid % W, jj = tid / W;
-        const int di = nt % W, dj = nt / W;
-        for (long long q = tid; q < (long long)W * H; q += nt) {
-            s_map[(long long)jj * ws + ii] = empty ? (unsigned char)0 : (unsigned char)evidence(L[q]);
-            ii += di;
-            jj += dj;
-            if (ii >= W) {
-                ii -= W;
-                ++jj;
+        uint4 *z4 = reinterpret_cast<uint4 *>(s_map);
+        for (int q = tid; q < (int)(a.map_bytes >> 4); q += nt) z4[q] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        unsigned char *m0 = s_map + brd * ws + col0;
+        if (!empty && (W & 7) == 0) {
+            // rows of whole 8-cell groups; env grids start on 512-byte
+            // boundaries, so each group is one aligned 16-byte load.  Four
+            // loads per thread are in flight before their stores.
+            const uint4 *L8 = reinterpret_cast<const uint4 *>(L);
+            const int wv = W >> 3, nv = wv * H;
+            for (int v0 = tid; v0 < nv; v0 += 4 * nt) {
+                uint4 r[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (v0 + u * nt < nv) r[u] = __ldg(&L8[v0 + u * nt]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int v = v0 + u * nt;
+                    if (v < nv) {
+                        const int jj = v / wv, ii = v - jj * wv;
+                        unsigned *d = reinterpret_cast<unsigned *>(m0 + jj * ws + 8 * ii);
+                        d[0] = evidence2(r[u].x) | evidence2(r[u].y) << 16;
+                        d[1] = evidence2(r[u].z) | evidence2(r[u].w) << 16;
+                    }
+                }
+            }
+        } else if (!empty) {
+            // (row, column) of element q tracked incrementally (no division per cell)
+            int ii = tid % W, jj = tid / W;
+            const int di = nt % W, dj = nt / W;
+            for (int q = tid; q < W * H; q += nt) {
+                m0[jj * ws + ii] = (unsigned char)evidence(L[q]);
+                ii += di;
+                jj += dj;
+                if (ii >= W) {
+                    ii -= W;
+                    ++jj;
+                }
             }
         }
     }
@@ -88,6 +134,9 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     const int nslice = nt / NC;                  // beam slices per candidate
     const int c = tid % NC, sl = tid / NC;
     const int ci_off = c % side - a.n_xy, cj_off = c / side - a.n_xy;
+    const int c_off = cj_off * ws + ci_off;      // candidate offset in the staged map
+    // centre of the zero sentinel block below the bordered map
+    const int sentinel = (H + 2 * brd + a.n_xy) * ws + a.n_xy;
     // the returned beams (range < r_max), compacted in beam order once
     const int lane = tid & 31, warp = tid >> 5;
     int nret = 0;
@@ -122,18 +171,27 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
             const float cx = fsub(fmul(ck, bc.x), fmul(sk, bc.y));
             const float cy = fadd(fmul(sk, bc.x), fmul(ck, bc.y));
             const float ex = fadd(x, fmul(z[b], cx)), ey = fadd(y, fmul(z[b], cy));
-            s_cell[q] = make_int2((int)floorf(fdiv(ex, p.res)), (int)floorf(fdiv(ey, p.res)));
+            const int i = (int)floorf(fdiv(ex, p.res)), j = (int)floorf(fdiv(ey, p.res));
+            if (staged) {
+                const bool near = i >= -a.n_xy && i < W + a.n_xy && j >= -a.n_xy && j < H + a.n_xy;
+                s_cell[q].x = near ? (j + brd) * ws + (i + col0) : sentinel;
+            } else {
+                s_cell[q] = make_int2(i, j);
+            }
         }
         __syncthreads();
         int acc = 0;
         if (sl < nslice) {
-            for (int q = sl; q < nret; q += nslice) {
-                const int2 cc = s_cell[q];
-                const int i = cc.x + ci_off, j = cc.y + cj_off;
-                if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H) {
-                    const long long kk = (long long)j * W + i;
-                    acc += staged ? (int)s_map[(long long)j * ws + i]
-                                  : (empty ? 0 : (int)evidence(L[kk]));
+            if (staged) {
+                const unsigned char *mc = s_map + c_off;
+                const int *addr = reinterpret_cast<const int *>(s_cell);
+                for (int q = sl; q < nret; q += nslice) acc += mc[addr[2 * q]];
+            } else {
+                for (int q = sl; q < nret; q += nslice) {
+                    const int2 cc = s_cell[q];
+                    const int i = cc.x + ci_off, j = cc.y + cj_off;
+                    if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H && !empty)
+                        acc += (int)evidence(L[(long long)j * W + i]);
                 }
             }
             s_part[tid] = acc;
@@ -206,9 +264,56 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
 
 int csm_max_n() { return kCsmMaxN; }
 
-size_t csm_map_bytes(int W, int H) {
-    const size_t n = (size_t)(W + 4) * H;               // padded rows
-    return (n + 15) & ~(size_t)15;
+namespace {
+
+// true when, for every base address, the lanes of each warp that read the
+// same beam (one slice) touch distinct words in distinct banks or share a
+// word: the staged candidate loads then take one shared-memory wavefront.
+// Moving the base by a word rotates every lane's bank by one, so the byte
+// offset of the base within its word is all that matters.
+bool csm_stride_conflict_free(int ws, int n) {
+    const int side = 2 * n + 1, NC = side * side, nslice = kCsmBlock / NC;
+    for (int w0 = 0; w0 < kCsmBlock; w0 += 32)
+        for (int base = 0; base < 4; ++base) {
+            int word_of_bank[32];
+            int slice_of_bank[32];
+            for (int k = 0; k < 32; ++k) word_of_bank[k] = -1;
+            for (int t = w0; t < w0 + 32; ++t) {
+                const int sl = t / NC, c = t % NC;
+                if (sl >= nslice) continue;
+                const int a = base + (c / side) * ws + c % side;     // offsets shifted by n
+                const int word = a >> 2, bank = word & 31;
+                if (word_of_bank[bank] >= 0 && slice_of_bank[bank] == sl &&
+                    word_of_bank[bank] != word)
+                    return false;
+                word_of_bank[bank] = word;
+                slice_of_bank[bank] = sl;
+            }
+        }
+    return true;
+}
+
+}  // namespace
+
+size_t csm_map_layout(const int *W, const int *H, int E, int n, int *ws) {
+    int wmax = 0, hmax = 0;
+    for (int e = 0; e < E; ++e) {
+        wmax = W[e] > wmax ? W[e] : wmax;
+        hmax = H[e] > hmax ? H[e] : hmax;
+    }
+    // bordered width in words; the first stride within 32 words that keeps
+    // a warp's candidate rows apart in the banks (else the narrowest)
+    const int w0 = (csm_col0(n) + wmax + 2 * n + 3) / 4;
+    int words = w0;
+    for (int w = w0; w < w0 + 32; ++w)
+        if (csm_stride_conflict_free(4 * w, n)) {
+            words = w;
+            break;
+        }
+    *ws = 4 * words;
+    // bordered map rows plus the sentinel block of 2n + 1 zero rows
+    const size_t bytes = (size_t)(4 * words) * (size_t)(hmax + 4 * n + 2 * n + 1);
+    return (bytes + 15) & ~(size_t)15;
 }
 
 cudaError_t csm_set_smem(size_t bytes) {
@@ -217,10 +322,10 @@ cudaError_t csm_set_smem(size_t bytes) {
 }
 
 cudaError_t launch_csm2d(const Step2DParams &p, int n_xy, int n_th, int sep, float dth,
-                         size_t map_bytes, const float *pose_pred, const float *ranges,
+                         size_t map_bytes, int ws, const float *pose_pred, const float *ranges,
                          float *pose_out, float *match, long long *scores, bool reset_empty,
                          cudaStream_t s) {
-    CsmArgs a{n_xy, n_th, sep, dth, map_bytes, reset_empty, pose_pred, ranges, pose_out, match,
+    CsmArgs a{n_xy, n_th, sep, dth, map_bytes, ws, reset_empty, pose_pred, ranges, pose_out, match,
               scores};
     csm2d_kernel<<<p.E, kCsmBlock, map_bytes, s>>>(p, a);
     return cudaGetLastError();

@@ -118,7 +118,7 @@ cudaError_t launch_slam2d(const Step2DParams &p, cudaStream_t s, const cudaEvent
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
     if (e != cudaSuccess) return e;
-    e = launch_csm2d(p, p.csm_n_xy, p.csm_n_th, p.csm_sep, p.csm_dth, p.csm_map_bytes,
+    e = launch_csm2d(p, p.csm_n_xy, p.csm_n_th, p.csm_sep, p.csm_dth, p.csm_map_bytes, p.csm_ws,
                      p.slam_pred, p.z, p.csm_pose, p.csm_match, p.csm_scores, true, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;

@@ -70,6 +70,23 @@ def test_csm_large_map_reads_global(aslam_gpu, orc):
     check(aslam_gpu, orc, inp, 6, 53, {"n_xy": 4, "n_th": 2}, r_max_m=8.0, noise_sigma_m=0.01)
 
 
+def test_csm_ragged_widths_stage_cell_by_cell(aslam_gpu, orc):
+    # widths that are not a multiple of 8 take the one-cell-at-a-time staging
+    rng = np.random.default_rng(913)
+    occ, spawn = [], []
+    for W, H in ((100, 90), (77, 64), (136, 41)):
+        g = np.zeros((H, W), np.uint8)
+        g[0, :] = g[-1, :] = g[:, 0] = g[:, -1] = 1
+        g[rng.integers(1, H - 1, 25), rng.integers(1, W - 1, 25)] = 1
+        g[H // 2 - 1:H // 2 + 2, W // 2 - 1:W // 2 + 2] = 0
+        occ.append(g)
+        cx, cy = (W // 2 + 0.5) * 0.05, (H // 2 + 0.5) * 0.05
+        spawn.append([[cx, cy, 0.3], [cx, cy, -1.2]])
+    inp = synth.custom_2d(occ, [120, 64, 90], 0.05, np.array(spawn, np.float32))
+    for kw in ({"n_xy": 5, "n_th": 3}, {"n_xy": 8, "n_th": 1, "sep": 3}, {"n_xy": 1, "n_th": 2}):
+        check(aslam_gpu, orc, inp, 6, 54, kw, r_max_m=4.0, noise_sigma_m=0.01)
+
+
 def test_csm_rejects_bad_config(aslam_gpu):
     b = aslam_gpu.Batch2D(synth.plain_1env(), r_max_m=5.0)
     pred = torch.zeros(1, 3, device="cuda")
