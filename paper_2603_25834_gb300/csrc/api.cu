@@ -386,11 +386,9 @@ int near_words(const HostInfo &hi) {
 int pref_words(const HostInfo &hi) { return 3 * (int)pad_to((size_t)hi.b_max + 1, 4); }
 int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }
 
-constexpr int kStaticSmem = 2048;
-
 int auto_window(const HostInfo &hi, int smem_optin, int clamp_q) {
-    long long budget_words = (smem_optin - kStaticSmem) / 4 - pref_words(hi) - near_words(hi) -
-                             lut_words(clamp_q);
+    long long budget_words = (smem_optin - (long long)update2d_static_smem()) / 4 -
+                             pref_words(hi) - near_words(hi) - lut_words(clamp_q);
     int S = (int)std::floor(std::sqrt(4.0 * (double)budget_words));
     S &= ~7;
     return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
@@ -400,7 +398,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     if (b->hi.dims == 3) {
         // voxel batches: ground-truth bits in shared memory, global counters
         const size_t smem = 4 * (size_t)b->hi.gt_words_max;
-        if (smem + kStaticSmem > (size_t)b->smem_optin)
+        if (smem + step3d_static_smem() > (size_t)b->smem_optin)
             return fail_b(b, ASLAM_ERR_UNSUPPORTED, "voxel map too large for shared memory");
         CK(step3d_set_smem(smem), "cudaFuncSetAttribute");
         int per_sm = 0;
@@ -418,7 +416,7 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
     const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) + pref_words(b->hi) + ww +
                              near_words(b->hi));
-    if (smem + kStaticSmem > (size_t)b->smem_optin)
+    if (smem + update2d_static_smem() > (size_t)b->smem_optin)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
     CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
     int per_sm = 0;

@@ -233,6 +233,8 @@ constexpr int kStep2DKernels = 3, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);
+size_t update2d_static_smem();                   // static shared bytes of the update kernel
+size_t step3d_static_smem();                     // ... of the voxel step kernel
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);
 cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s);

@@ -107,6 +107,16 @@ __device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray,
     return b;
 }
 
+// The traversal steps along x while e = nx*ady - ny*adx < 0 (nx, ny: Q16
+// distances to the next x and y grid lines), adding ady << 16 or
+// subtracting adx << 16 per step.  The low 16 bits of e never change and
+// lie in [0, 2^16), so e < 0 exactly when floor(e / 2^16) < 0, and the walk
+// can carry h = floor(e / 2^16) with steps +ady / -adx.  |e| <= 2^46 at the
+// start (nx, ny <= 2^16, adx, ady <= 2^30) and each step moves a negative h
+// up by at most 2^30 or a non-negative h down by at most 2^30, so h stays in
+// [-2^30, 2^30]: a 32-bit integer.
+__device__ __forceinline__ int dda_hi(long long e) { return (int)(e >> 16); }
+
 // A 64-bit integer as an approximate float, from its 32-bit halves (exact
 // 32-bit conversions only).
 __device__ __forceinline__ float approx_f32(long long v) {
@@ -222,15 +232,15 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                 const int Ks = crossings_le(bm.nx0, bm.adx, p.Tmax) +
                                crossings_le(bm.ny0, bm.ady, p.Tmax);
                 const int nsteps = min(Ks, nm - 1);
-                const long long dA = bm.ady << 16, ndB = -(bm.adx << 16);
                 const int syW = bm.sy * W;
-                long long ee = bm.nx0 * bm.ady - bm.ny0 * bm.adx;
+                int eh = dda_hi(bm.nx0 * bm.ady - bm.ny0 * bm.adx);
+                const int ady = (int)bm.ady, nadx = -(int)bm.adx;
                 int st = 0, kx = 0;
                 bool lastx = false;
                 for (; st < nsteps; ++st) {
-                    lastx = ee < 0;
+                    lastx = eh < 0;
                     k += lastx ? bm.sx : syW;
-                    ee += lastx ? dA : ndB;
+                    eh += lastx ? ady : nadx;
                     kx += lastx;
                     if (gt_bit(gt, k)) {
                         hit = true;
@@ -362,22 +372,22 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
     const int W = sh.W;
     int i = sh.ri + bm.sx * kx, j = sh.rj + bm.sy * ky;
     int k = j * W + i;
-    const long long dA = bm.ady << 16, dB = bm.adx << 16;
-    long long ee = (bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx;
+    int eh = dda_hi((bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx);
+    const int ady = (int)bm.ady, adx = (int)bm.adx;
     const int syW = bm.sy * W;
     const int s_end = min(last, s0 + p.chunk - 1);
     const bool hit_end = hit && s_end == last;
     const int n_miss = s_end - s0 + (hit_end ? 0 : 1);   // the hit cell is added last
     for (int c = 0; c < n_miss; ++c) {
         add_count<kPartial, kNear>(p, sh, i, j, k, false, s_win, s_near);
-        if (ee < 0) {
+        if (eh < 0) {
             i += bm.sx;
             k += bm.sx;
-            ee += dA;
+            eh += ady;
         } else {
             j += bm.sy;
             k += syW;
-            ee -= dB;
+            eh -= adx;
         }
     }
     if (hit_end) add_count<kPartial, kNear>(p, sh, i, j, k, true, s_win, s_near);
@@ -487,8 +497,6 @@ __device__ __forceinline__ void finish_pending(const Step2DParams &p, const EnvS
     finish_env(p, sh.e, sh.W, sh.H, sh.start, sh.col_cell, r);
 }
 
-constexpr int kUnroll = 2;
-
 // One persistent CTA per SM slot takes envs from a queue.  The last warp is
 // the control warp: while the others walk env n it finishes env n-1 (reward,
 // termination, outputs) and loads env n+1's parameters into the other half
@@ -506,6 +514,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     __shared__ int r_rc[32];
     __shared__ long long s_dHq;
     __shared__ int s_rc, s_n0;
+    __shared__ int s_tq[32 * 64];                // per-warp rings of touched chunks
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -617,46 +626,54 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         const float wgt = p.upd_w ? p.upd_w[e] : -1.0f;   // confidence weight of the scan
         unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
         {
-            // 8-cell chunks of the shared counters: the loads of kUnroll chunks
-            // are issued before any of them is used
+            // 8-cell chunks of the shared counters.  Each warp scans groups of
+            // 32 chunks and queues the touched ones (ballot) in a ring of 64
+            // in shared memory; whenever 32 are queued, every lane applies
+            // one, so the sparse touched chunks are applied by full warps.
             const int SW = sh.SW, rch = (SW + 7) >> 3;
             const int nchunk = sh.partial ? sh.SH * rch : nch;
             const uint2 *cw2 = reinterpret_cast<const uint2 *>(s_win);
-            for (int q0 = tid; q0 < nchunk; q0 += nt * kUnroll) {
-                uint2 cw[kUnroll];
-                int4 lv[kUnroll];
-                long long gk[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const int q = q0 + u * nt;
-                    cw[u] = make_uint2(0u, 0u);
-                    gk[u] = -1;
-                    if (q < nchunk) {
-                        long long k;
-                        int sidx;
-                        if (sh.partial) {
-                            const int jj = q / rch, cc = q - jj * rch;
-                            k = (long long)(sh.wy0 + jj) * W + sh.wx0 + 8 * cc;
-                            sidx = (jj * SW >> 3) + cc;
-                        } else {
-                            k = 8LL * q;
-                            sidx = q;
-                        }
-                        cw[u] = cw2[sidx];
-                        if (cw[u].x | cw[u].y) {
-                            gk[u] = k;
-                            lv[u] = *reinterpret_cast<const int4 *>(Lenv + k);
-                        }
-                    }
+            int *ring = s_tq + 64 * warp;
+            auto apply_chunk = [&](int q) {
+                long long k;
+                int sidx;
+                if (sh.partial) {
+                    const int jj = q / rch, cc = q - jj * rch;
+                    k = (long long)(sh.wy0 + jj) * W + sh.wx0 + 8 * cc;
+                    sidx = (jj * SW >> 3) + cc;
+                } else {
+                    k = 8LL * q;
+                    sidx = q;
                 }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    if (gk[u] >= 0) {
-                        dh += apply8(p, s_lut, cw[u], lv[u], dbg ? dbg + gk[u] : nullptr, wgt);
-                        *reinterpret_cast<int4 *>(Lenv + gk[u]) = lv[u];
+                int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
+                dh += apply8(p, s_lut, cw2[sidx], lv, dbg ? dbg + k : nullptr, wgt);
+                *reinterpret_cast<int4 *>(Lenv + k) = lv;
+            };
+            int head = 0, nq = 0;                        // warp-uniform
+            for (int base = 32 * warp; base < nchunk; base += nt) {
+                const int q = base + lane;
+                bool touched = false;
+                if (q < nchunk) {
+                    int sidx = q;
+                    if (sh.partial) {
+                        const int jj = q / rch;
+                        sidx = (jj * SW >> 3) + q - jj * rch;
                     }
+                    const uint2 c = cw2[sidx];
+                    touched = (c.x | c.y) != 0u;
                 }
+                const unsigned m = __ballot_sync(0xffffffffu, touched);
+                if (touched) ring[(head + nq + __popc(m & ((1u << lane) - 1u))) & 63] = q;
+                nq += __popc(m);
+                __syncwarp();
+                if (nq >= 32) {
+                    apply_chunk(ring[(head + lane) & 63]);
+                    head = (head + 32) & 63;
+                    nq -= 32;
+                }
+                __syncwarp();
             }
+            if (lane < nq) apply_chunk(ring[(head + lane) & 63]);
         }
         if (sh.partial) {
             // chunks outside the window, found through the touched-chunk bitmap
@@ -821,6 +838,12 @@ __global__ void detmath_kernel(const float *x, const float *u, int n, float *s, 
 
 }  // namespace
 
+size_t update2d_static_smem() {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, update2d_kernel) == cudaSuccess ? a.sharedSizeBytes
+                                                                      : (size_t)16384;
+}
+
 cudaError_t step2d_set_smem(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(update2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -829,7 +852,7 @@ cudaError_t step2d_set_smem(size_t smem) {
                                 kSenseSmemMax);
 }
 
-// Beams per sensing CTA: 64, more for larger maps so that the ground truth
+// Beams per sensing CTA: 128, more for larger maps so that the ground truth
 // staged per CTA stays at <= 256 bytes per thread.
 int sense_block(int gt_words_max) {
     // 128 beams per bundle: a 360-beam scan stages its ground truth three

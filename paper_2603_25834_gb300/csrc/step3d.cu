@@ -365,6 +365,12 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
 
 }  // namespace
 
+size_t step3d_static_smem() {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, step3d_kernel) == cudaSuccess ? a.sharedSizeBytes
+                                                                    : (size_t)16384;
+}
+
 cudaError_t step3d_set_smem(size_t smem) {
     return cudaFuncSetAttribute(step3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
