@@ -640,12 +640,12 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
             p.csm_scores = at<long long>(b, o.csm_scores);
             p.slam_upd_w = at<float>(b, o.slam_upd_w);
         }
-        p.lam_col = cfg->lam_col;
-        p.lam_explore = cfg->lam_explore;
-        p.lam_abs = cfg->lam_abs;
-        p.lam_delta = cfg->lam_delta;
-        p.kappa = cfg->kappa;
-        p.u_hi = cfg->u_hi;
+        p.lam_col = (float)cfg->lam_col;
+        p.lam_explore = (float)cfg->lam_explore;
+        p.lam_abs = (float)cfg->lam_abs;
+        p.lam_delta = (float)cfg->lam_delta;
+        p.kappa = (float)cfg->kappa;
+        p.u_hi = (float)cfg->u_hi;
         p.key = make_uint2((unsigned)cfg->seed, (unsigned)(cfg->seed >> 32));
         p.env_base = cfg->env_base;
         p.W = at<int>(b, o.W);

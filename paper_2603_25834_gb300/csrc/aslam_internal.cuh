@@ -156,7 +156,7 @@ struct Step2DParams {
     int near_words_max;          // shared words reserved for the 32-bit near block
     int dims, n_rings, Pz;       // 3-D: ring count and sensor height (Q16 voxels)
     float res, r_max, sigma, dt, v_max, w_max, d_crash, d_full, visit_cell;
-    double lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;
+    float lam_col, lam_explore, lam_abs, lam_delta, kappa, u_hi;   // fp32 copies (Eq. 7-17)
     uint2 key;
     int env_base;
     float r_min, dec_scale;      // sensor quantisation (dec_scale 0: no rounding)

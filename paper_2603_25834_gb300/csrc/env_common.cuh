@@ -64,12 +64,16 @@ struct EnvTotals {
 };
 
 // Entropy gain, visit grid (Eq. 8-9), reward terms (Eq. 7-17), termination
-// and the per-env outputs.  One thread.
+// and the per-env outputs.  One thread, in fp32: every term is a product or
+// quotient of a few fp32 inputs (a few ulp each), and the fp64 pipe of
+// sm_103a is slow enough that fp64 here would lengthen the step.
 __device__ __forceinline__ void finish_env(const Step2DParams &p, int e, int W, int H,
                                            const EnvStart &s, int col_cell, const EnvTotals &r) {
     const long long Hq = s.Hq + r.dHq;
     p.Hq[e] = Hq;
-    const double dH = -(double)r.dHq / kLutScale;    // H_{t-1} - H_t (nats)
+    constexpr float kInvLut = 1.0f / 1099511627776.0f;   // 2^-40, exact
+    // H_{t-1} - H_t (nats): one correctly rounded conversion, an exact scaling
+    const float dH = fmul(__ll2float_rn(-r.dHq), kInvLut);
     const int col = col_cell || (r.dmin_true < p.d_crash);
     const int Vw = p.Vw[e], Vh = p.Vh[e];
     const float vx0 = fmul(-0.5f, fmul((float)W, p.res));
@@ -80,42 +84,44 @@ __device__ __forceinline__ void finish_env(const Step2DParams &p, int e, int W, 
     vj = min(max(vj, 0), Vh - 1);
     int *vc = p.visit + p.visit_off[e] + (long long)vj * Vw + vi;
     const int last = *vc;
-    double dcells = 1.0;
-    if (last >= 0) dcells = fmin(fmax(0.5 * (double)(s.t - last) / (double)p.t_episode, 0.0), 1.0);
+    float dcells = 1.0f;
+    if (last >= 0)
+        dcells = fminf(fmaxf(fdiv(fmul(0.5f, (float)(s.t - last)), (float)p.t_episode), 0.0f), 1.0f);
     *vc = s.t;
-    const double Up = (double)s.u_prev;
-    const double U = p.u_in ? (double)p.u_in[e] : 0.0;
-    double cg = fmin(fmax((p.u_hi - Up) / p.u_hi, 0.0), 1.0);
-    cg = cg * cg;
-    const double iota = fmin(fmax(fmax(Up - U, 0.0) / p.kappa, 0.0), 1.0);
-    const double I = cg + (1.0 - cg) * iota;
-    const double r_explore = p.lam_explore * dcells * I;
-    const double eU = exp(Up);
-    const double r_abs = p.lam_abs * eU * Up;
-    const double r_delta = p.lam_delta * eU * (Up - U);
-    const double alpha = fmin(fmax(((double)r.dmin_meas - (double)p.d_crash) /
-                                       ((double)p.d_full - (double)p.d_crash), 0.0), 1.0);
-    const double r_explore_s = r_explore * alpha;
-    const double r_delta_s = (Up - U > 0.0) ? r_delta * alpha : r_delta;
-    const double R = col ? -p.lam_col : (r_explore_s - r_abs + r_delta_s);
+    const float Up = s.u_prev;
+    const float U = p.u_in ? p.u_in[e] : 0.0f;
+    const float dU = fsub(Up, U);                  // exact sign
+    float cg = fminf(fmaxf(fdiv(fsub(p.u_hi, Up), p.u_hi), 0.0f), 1.0f);
+    cg = fmul(cg, cg);
+    const float iota = fminf(fmaxf(fdiv(fmaxf(dU, 0.0f), p.kappa), 0.0f), 1.0f);
+    const float I = fadd(cg, fmul(fsub(1.0f, cg), iota));
+    const float r_explore = fmul(fmul(p.lam_explore, dcells), I);
+    const float eU = expf(Up);
+    const float r_abs = fmul(fmul(p.lam_abs, eU), Up);
+    const float r_delta = fmul(fmul(p.lam_delta, eU), dU);
+    const float alpha = fminf(fmaxf(fdiv(fsub(r.dmin_meas, p.d_crash), fsub(p.d_full, p.d_crash)),
+                                    0.0f), 1.0f);
+    const float r_explore_s = fmul(r_explore, alpha);
+    const float r_delta_s = dU > 0.0f ? fmul(r_delta, alpha) : r_delta;
+    const float R = col ? -p.lam_col : fadd(fsub(r_explore_s, r_abs), r_delta_s);
     float *tm = p.terms + (long long)e * kTerms;
-    tm[0] = (float)dH;
-    tm[1] = (float)dcells;
-    tm[2] = (float)I;
-    tm[3] = (float)alpha;
-    tm[4] = (float)r_explore_s;
-    tm[5] = (float)r_abs;
-    tm[6] = (float)r_delta_s;
-    tm[7] = (float)R;
+    tm[0] = dH;
+    tm[1] = dcells;
+    tm[2] = I;
+    tm[3] = alpha;
+    tm[4] = r_explore_s;
+    tm[5] = r_abs;
+    tm[6] = r_delta_s;
+    tm[7] = R;
     tm[8] = (float)col;
     tm[9] = r.dmin_meas;
     tm[10] = r.dmin_true;
-    tm[11] = (float)((double)Hq / kLutScale);
-    const float rew = p.reward_mode == ASLAM_REWARD_COMPOSITE ? (float)R : (float)dH;
+    tm[11] = fmul(__ll2float_rn(Hq), kInvLut);
+    const float rew = p.reward_mode == ASLAM_REWARD_COMPOSITE ? R : dH;
     p.reward[e] = rew;
     if (p.out_reward) p.out_reward[e] = rew;
     p.done[e] = (col || s.t >= p.t_episode) ? 1 : 0;
-    p.u_prev[e] = (float)U;
+    p.u_prev[e] = U;
     p.g[e] = s.gstep + 1;
     p.ray_cells[e] = r.ray_cells;
     p.gt_cells[e] = r.gt_cells;
