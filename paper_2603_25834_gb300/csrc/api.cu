@@ -251,7 +251,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
         for (int e = 0; e < hi.E; ++e) nb += (size_t)(hi.B[e] + sb - 1) / sb;
         o.bundles = add(8 * std::max<size_t>(nb, 1));
     }
-    o.queue = add(8);          // {next item, CTAs finished}
+    o.queue = add(16);         // {next item, CTAs finished, sensing CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
     const bool uq = c->u_mode == ASLAM_U_SCANMATCH || c->u_mode == ASLAM_U_FIXEDLAG;
@@ -779,7 +779,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
             e1 = cudaMemcpyAsync((void *)p.spawn, d_spawn, 12 * (size_t)E * cfg->n_spawn,
                                  cudaMemcpyDeviceToDevice, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.err, 0, 4, s);
-        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.queue, 0, 8, s);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.queue, 0, 16, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(at<void>(b, o.tune_actions), 0, 8 * (size_t)E, s);
         if (e1 == cudaSuccess)
             e1 = launch_pack_gt(d_gt, at<long long>(b, o.src_off), p.W, p.H, p.Dd, p.gtb_off,

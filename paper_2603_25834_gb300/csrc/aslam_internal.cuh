@@ -180,7 +180,8 @@ struct Step2DParams {
     float *slam_upd_w;           // [E] this step's scan weight (u_mode 2)
     const float *upd_w;          // per-env update weight, or null (unweighted)                // global index of env 0 in the noise counter
     // per-env static description
-    const int *W, *H, *B, *Vw, *Vh, *order, *R8, *Dd;
+    const int *W, *H, *B, *Vw, *Vh, *R8, *Dd;
+    int *order;                  // work order of the update queue (2-D: costliest first each step)
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
     const long long *map_off, *gtb_off, *ray_off, *visit_off;
     const float2 *beam_cs;

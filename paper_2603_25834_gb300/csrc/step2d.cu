@@ -51,6 +51,7 @@ struct EnvSense {
     EnvStart start;
     int Px, Py, col_cell, gt_cells;
     float c, s, dmin_meas, dmin_true;
+    int upd_cells;               // cells of this step's belief walks (update cost)
 };
 
 size_t env_sense_bytes() { return sizeof(EnvSense); }
@@ -173,10 +174,67 @@ __global__ void integrate2d_kernel(const Step2DParams p) {
         es.col_cell = !inside || gt_bit(p.gt_bits + p.gtb_off[e], rj * W + ri);
         det_sincos(es.start.th, es.s, es.c);
         es.gt_cells = 0;
+        es.upd_cells = 0;
         es.dmin_meas = p.r_max;      // reduced with atomicMin on the (positive) float bits
         es.dmin_true = p.r_max;
         reinterpret_cast<EnvSense *>(p.env_sense)[e] = es;
     }
+}
+
+// Work order of the update kernel's queue for this step, costliest env first
+// (longest-processing-time-first keeps the persistent CTAs' last envs short).
+// The cost is the env's belief-walk cells, bucketed into 256 classes of the
+// largest; a counting sort writes the order (order within a class is
+// arbitrary: each env is still updated whole by exactly one CTA).  Run by one
+// CTA once every sensing CTA has added its cells.
+constexpr int kOrderSmem = 1024;  // envs whose costs are kept in shared memory
+
+__device__ void order_envs_by_cost(const Step2DParams &p, unsigned *s_hist, int *s_cost,
+                                   int *s_max) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const EnvSense *es = reinterpret_cast<const EnvSense *>(p.env_sense);
+    const bool staged = p.E <= kOrderSmem;
+    for (int q = tid; q < 256; q += nt) s_hist[q] = 0u;
+    if (tid == 0) *s_max = 1;
+    int m = 0;
+    for (int e = tid; e < p.E; e += nt) {
+        const int c = __ldcg(&es[e].upd_cells);
+        if (staged) s_cost[e] = c;
+        m = max(m, c);
+    }
+    __syncthreads();
+    atomicMax(s_max, m);
+    __syncthreads();
+    const float scale = 255.0f / (float)*s_max;
+    auto bucket = [&](int e) {
+        const int c = staged ? s_cost[e] : __ldcg(&es[e].upd_cells);
+        return min(max(255 - (int)((float)c * scale), 0), 255);
+    };
+    for (int e = tid; e < p.E; e += nt) atomicAdd(&s_hist[bucket(e)], 1u);
+    __syncthreads();
+    if (tid < 32) {
+        // exclusive scan of the 256 class counts, 8 per lane
+        unsigned v[8], sum = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = s_hist[8 * tid + k];
+            sum += v[k];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += t;
+        }
+        unsigned run = incl - sum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s_hist[8 * tid + k] = run;
+            run += v[k];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < p.E; e += nt) p.order[atomicAdd(&s_hist[bucket(e)], 1u)] = e;
 }
 
 // ---------------------------------------------------------------------------
@@ -207,7 +265,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     }
     pdl_wait();                          // the integration's EnvSense records are complete
     __syncthreads();
-    int gc = 0;
+    int gc = 0, uc = 0;
     float dmin_m = p.r_max, dmin_t = p.r_max;
     if (b < B) {
         const unsigned *gt = s_gt;
@@ -269,6 +327,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
             // gets the hit only when it is in the map
             const int ncells = min(Ku + 1, nm);
             code = (ncells - 1) | ((hit && Ku < nm) ? (1 << 30) : 0);
+            uc = ncells;
         }
         p.ray_code[ray] = code;
         p.z[ray] = z;
@@ -284,14 +343,35 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         gc += __shfl_down_sync(0xffffffffu, gc, o);
+        uc += __shfl_down_sync(0xffffffffu, uc, o);
         dmin_m = fminf(dmin_m, __shfl_down_sync(0xffffffffu, dmin_m, o));
         dmin_t = fminf(dmin_t, __shfl_down_sync(0xffffffffu, dmin_t, o));
     }
     if (lane == 0) {
         atomicAdd(&esp->gt_cells, gc);
+        atomicAdd(&esp->upd_cells, uc);
         // ranges are >= 0, so their float bits order like the values
         atomicMin(reinterpret_cast<int *>(&esp->dmin_meas), __float_as_int(dmin_m));
         atomicMin(reinterpret_cast<int *>(&esp->dmin_true), __float_as_int(dmin_t));
+    }
+    // The last CTA to finish orders the envs for the update queue.  The
+    // barrier makes this CTA's atomics visible to thread 0, whose release
+    // ticket publishes them device-wide; the last ticket is also an acquire,
+    // and the barrier after it extends that to the whole CTA.
+    __shared__ unsigned s_hist[256];
+    __shared__ int s_cost[kOrderSmem];
+    __shared__ int s_max, s_last;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(old) : "l"(p.queue + 2) : "memory");
+        s_last = old == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        order_envs_by_cost(p, s_hist, s_cost, &s_max);
+        if (tid == 0) p.queue[2] = 0u;
     }
 }
 
@@ -522,8 +602,21 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     const bool control = warp == nwarps - 1;
     const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
 
-    // entropy half table h(|L|), L = 0..clamp_q, shared by every env of the CTA
-    for (int q = tid; q <= p.clamp_q; q += nt) s_lut[q] = __ldg(&p.lut[p.clamp_q + q]);
+    // entropy half table h(|L|), L = 0..clamp_q, shared by every env of the
+    // CTA; all of a thread's loads are in flight before its first store
+    {
+        constexpr int kLutUnroll = 8;
+        const long long *src = p.lut + p.clamp_q;
+        for (int q0 = tid; q0 <= p.clamp_q; q0 += kLutUnroll * nt) {
+            long long v[kLutUnroll];
+#pragma unroll
+            for (int u = 0; u < kLutUnroll; ++u)
+                if (q0 + u * nt <= p.clamp_q) v[u] = __ldg(src + q0 + u * nt);
+#pragma unroll
+            for (int u = 0; u < kLutUnroll; ++u)
+                if (q0 + u * nt <= p.clamp_q) s_lut[q0 + u * nt] = v[u];
+        }
+    }
     pdl_wait();                          // the sensing kernel's ray codes are complete
     if (tid == 0) load_env(p, (int)atomicAdd(p.queue, 1u), shb[0]);
     __syncthreads();
