@@ -383,7 +383,7 @@ int near_words(const HostInfo &hi) {
 
 // Shared words of the update kernel's per-beam chunk table and of the
 // entropy half table (int64 per |L| = 0..clamp).
-int pref_words(const HostInfo &hi) { return 3 * (int)pad_to((size_t)hi.b_max + 1, 4); }
+int pref_words(const HostInfo &hi) { return 2 * (int)pad_to((size_t)hi.b_max + 1, 4); }
 int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }
 
 int auto_window(const HostInfo &hi, int smem_optin, int clamp_q) {

@@ -585,15 +585,15 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     extern __shared__ __align__(16) unsigned smem[];
     long long *s_lut = reinterpret_cast<long long *>(smem);           // [clamp_q + 1]
     int *s_pref = reinterpret_cast<int *>(smem + p.lut_words);       // [b_max + 1]
-    int *s_first = s_pref + ((p.b_max + 1 + 3) & ~3);                 // [b_max]
-    int *s_beam = s_first + ((p.b_max + 3) & ~3);                     // [b_max]
-    unsigned *s_win = smem + p.lut_words + 3 * ((p.b_max + 1 + 3) & ~3);
+    int *s_beam = s_pref + ((p.b_max + 1 + 3) & ~3);                  // [b_max]
+    unsigned *s_win = smem + p.lut_words + 2 * ((p.b_max + 1 + 3) & ~3);
     unsigned *s_near = s_win + p.win_words_max;
     __shared__ EnvShared shb[2];
     __shared__ long long r_dh[32];
     __shared__ int r_rc[32];
     __shared__ long long s_dHq;
-    __shared__ int s_rc, s_n0;
+    __shared__ int s_rc;
+    __shared__ int s_wsum[130];                  // chunk table: warp sums, offsets, totals
     __shared__ int s_tq[32 * 64];                // per-warp rings of touched chunks
 
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -643,38 +643,60 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             if (debug)
                 for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
         }
-        // Chunk table.  Chunks 0 .. n0-1 are the first chunks of the n0 beams
-        // with cells (beam ids in s_first); the rest, in beam order, are the
-        // later chunks (s_pref: running count of later chunks per beam).
-        for (int b = tid; b < B; b += nt) {
-            const int code = p.ray_code[sh.ray_off + b];
-            s_pref[b + 1] = code < 0 ? 0 : (code & 0x3fffffff) / p.chunk;     // later chunks
-            s_first[b] = code < 0 ? 0 : 1;
-        }
+        // Chunk table, one pass over the beams by all warps.  Chunks 0 ..
+        // n0-1 are the first chunks of the n0 beams with cells (beam ids in
+        // s_beam); the rest, in beam order, are the later chunks (s_pref:
+        // running count of later chunks per beam).  Each warp scans 32 beams
+        // with shuffles, warp 0 scans the warp sums; n0 and nlater are the
+        // running totals (uniform).
+        int n0 = 0, nlater = 0;
         if (tid == 0) s_pref[0] = 0;
-        __syncthreads();
-        // inclusive scans of both by warp 0 / warp 1, in slices of 32
-        if (warp < 2) {
-            int *arr = warp == 0 ? s_pref + 1 : s_first;
-            int carry = 0;
-            for (int base = 0; base < B; base += 32) {
-                const int b = base + lane;
-                int v = b < B ? arr[b] : 0;
+        for (int b0 = 0; b0 < B; b0 += nt) {
+            const int b = b0 + tid;
+            const int code = b < B ? p.ray_code[sh.ray_off + b] : -1;
+            int vl = code < 0 ? 0 : (code & 0x3fffffff) / p.chunk;    // later chunks
+            int vf = code < 0 ? 0 : 1;                                  // a first chunk
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tl = __shfl_up_sync(0xffffffffu, vl, o);
+                const int tf = __shfl_up_sync(0xffffffffu, vf, o);
+                if (lane >= o) {
+                    vl += tl;
+                    vf += tf;
+                }
+            }
+            if (lane == 31) {
+                s_wsum[warp] = vl;
+                s_wsum[32 + warp] = vf;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int tl = lane < nwarps ? s_wsum[lane] : 0;
+                const int tf = lane < nwarps ? s_wsum[32 + lane] : 0;
+                int il = tl, jf = tf;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += t;
+                    const int ul = __shfl_up_sync(0xffffffffu, il, o);
+                    const int uf = __shfl_up_sync(0xffffffffu, jf, o);
+                    if (lane >= o) {
+                        il += ul;
+                        jf += uf;
+                    }
                 }
-                if (b < B) arr[b] = v + carry;
-                carry += __shfl_sync(0xffffffffu, v, 31);
+                s_wsum[64 + lane] = il - tl;             // exclusive warp offsets
+                s_wsum[96 + lane] = jf - tf;
+                if (lane == 31) {
+                    s_wsum[128] = il;                    // this round's totals
+                    s_wsum[129] = jf;
+                }
             }
-        }
-        __syncthreads();
-        const int n0 = B ? s_first[B - 1] : 0;
-        // scatter: the first-chunk slot of beam b is s_first[b] - 1
-        if (tid == 0) s_n0 = n0;
-        for (int b = tid; b < B; b += nt) {
-            if (p.ray_code[sh.ray_off + b] >= 0) s_beam[s_first[b] - 1] = b;
+            __syncthreads();
+            if (b < B) {
+                s_pref[b + 1] = nlater + s_wsum[64 + warp] + vl;
+                if (code >= 0) s_beam[n0 + s_wsum[96 + warp] + vf - 1] = b;
+            }
+            nlater += s_wsum[128];
+            n0 += s_wsum[129];
         }
         __syncthreads();
 
@@ -686,9 +708,9 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                 load_env(p, (int)atomicAdd(p.queue, 1u), shb[(it + 1) & 1]);
             }
         } else {
-            const int total = s_n0 + s_pref[B];
+            const int total = n0 + nlater;
             for (int q = tid; q < total; q += nwalk) {
-                if (q < s_n0) {
+                if (q < n0) {
                     // first chunk of a beam: may touch the 32-bit block near the robot
                     const int b = s_beam[q];
                     const int code = p.ray_code[sh.ray_off + b];
@@ -697,7 +719,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                 } else {
                     // later chunks start >= chunk >= 2*R8 steps out: after s steps a walk
                     // is >= s/2 cells (Chebyshev) from the robot, outside the near block
-                    const int qq = q - s_n0;
+                    const int qq = q - n0;
                     int lo = 0, hi = B - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
