@@ -197,10 +197,26 @@ __device__ void order_envs_by_cost(const Step2DParams &p, unsigned *s_hist, int 
     for (int q = tid; q < 256; q += nt) s_hist[q] = 0u;
     if (tid == 0) *s_max = 1;
     int m = 0;
-    for (int e = tid; e < p.E; e += nt) {
-        const int c = __ldcg(&es[e].upd_cells);
-        if (staged) s_cost[e] = c;
-        m = max(m, c);
+    if (staged && p.E <= 8 * nt) {
+        // every load of this thread in flight at once
+        int c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * nt;
+            c[u] = e < p.E ? __ldcg(&es[e].upd_cells) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * nt;
+            if (e < p.E) s_cost[e] = c[u];
+            m = max(m, c[u]);
+        }
+    } else {
+        for (int e = tid; e < p.E; e += nt) {
+            const int c = __ldcg(&es[e].upd_cells);
+            if (staged) s_cost[e] = c;
+            m = max(m, c);
+        }
     }
     __syncthreads();
     atomicMax(s_max, m);
@@ -356,17 +372,19 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     }
     // The last CTA to finish orders the envs for the update queue.  The
     // barrier makes this CTA's atomics visible to thread 0, whose release
-    // ticket publishes them device-wide; the last ticket is also an acquire,
-    // and the barrier after it extends that to the whole CTA.
+    // ticket publishes them device-wide; the CTA that takes the last ticket
+    // then fences (acquire), and the barrier after it extends that to the
+    // whole CTA.
     __shared__ unsigned s_hist[256];
     __shared__ int s_cost[kOrderSmem];
     __shared__ int s_max, s_last;
     __syncthreads();
     if (tid == 0) {
         unsigned old;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+        asm volatile("atom.release.gpu.global.add.u32 %0, [%1], 1;"
                      : "=r"(old) : "l"(p.queue + 2) : "memory");
         s_last = old == gridDim.x - 1;
+        if (s_last) asm volatile("fence.acq_rel.gpu;" ::: "memory");
     }
     __syncthreads();
     if (s_last) {
