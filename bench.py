@@ -505,8 +505,6 @@ def main():
     h_u = torch.from_numpy(synth.random_uncertainty(K2, E_all, 18)[:, lo:hi].copy()).pin_memory()
     h_rew = torch.empty(K2, E).pin_memory()
     h_obs = torch.empty(K2, E, batch.b_max + 2).pin_memory()
-    d_a = torch.empty(E, 2, device=dev)
-    d_u = torch.empty(E, device=dev)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -516,11 +514,8 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        d_a.copy_(h_acts[k], non_blocking=True)
-        d_u.copy_(h_u[k], non_blocking=True)
-        batch.step_fused(d_a, d_u, reward, obs)
-        h_rew[k].copy_(reward, non_blocking=True)
-        h_obs[k].copy_(obs, non_blocking=True)
+        # the C-ABI call with host buffers: copies in, step, copies out
+        batch.step_host(h_acts[k], h_u[k], h_rew[k], h_obs[k], stream=stream)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)

@@ -102,6 +102,7 @@ EXPORTS = {
                             C.POINTER(P)], C.c_int),
     "aslam_step": ([P, P, P, P], C.c_int),
     "aslam_step_fused": ([P, P, P, P, P, P], C.c_int),
+    "aslam_step_host": ([P, P, P, P, P, P], C.c_int),
     "aslam_reward": ([P, P, P], C.c_int),
     "aslam_reward_terms": ([P, P, P], C.c_int),
     "aslam_observe": ([P, P, P], C.c_int),
@@ -175,6 +176,16 @@ def _dptr(t):
         raise AslamError(1, "expected a CUDA tensor")
     if not t.is_contiguous():
         raise AslamError(1, "expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(t):
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise AslamError(1, "expected a host (CPU) tensor")
+    if not t.is_contiguous() or t.dtype != torch.float32:
+        raise AslamError(1, "expected a contiguous float32 tensor")
     return C.c_void_p(t.data_ptr())
 
 
@@ -324,6 +335,12 @@ class Batch2D:
     def step_fused(self, actions, u=None, reward=None, obs=None, stream=None):
         _check(self.lib.aslam_step_fused(self.handle, _dptr(actions), _dptr(u), _dptr(reward),
                                          _dptr(obs), _stream(stream)), self.handle)
+
+    def step_host(self, actions, u=None, reward=None, obs=None, stream=None):
+        """One step from and to host tensors (page-locked for asynchronous
+        copies); the outputs are valid after the stream is synchronised."""
+        _check(self.lib.aslam_step_host(self.handle, _hptr(actions), _hptr(u), _hptr(reward),
+                                        _hptr(obs), _stream(stream)), self.handle)
 
     def reward(self, out=None, stream=None):
         if out is None:

@@ -37,6 +37,7 @@ struct Offsets {
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
     size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, err, tune_actions;
+    size_t io_in, io_out;        // aslam_step_host staging: [3E] in, [E (b_max + 3)] out
     size_t pose_cov, u_scan;
     size_t win_x, win_odo, win_meas, win_minfo, win_n, slam_pred, slam_odo, csm_pose, csm_match,
         csm_scores, slam_upd_w;
@@ -254,6 +255,8 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.queue = add(16);         // {next item, CTAs finished, sensing CTAs finished}
     o.err = add(4);
     o.tune_actions = add(8 * E);
+    o.io_in = add(12 * E);                                   // actions [E, 2], U [E]
+    o.io_out = add(4 * E * ((size_t)hi.b_max + 3));          // reward [E], obs [E, b_max + 2]
     const bool uq = c->u_mode == ASLAM_U_SCANMATCH || c->u_mode == ASLAM_U_FIXEDLAG;
     const bool sl = c->u_mode == ASLAM_U_FIXEDLAG;
     o.pose_cov = add(uq ? 48 * E : 0);
@@ -826,6 +829,31 @@ aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const floa
 
 aslam_status aslam_step(aslam_batch *b, const float *d_actions, const float *d_u, void *stream) {
     return aslam_step_fused(b, d_actions, d_u, nullptr, nullptr, stream);
+}
+
+aslam_status aslam_step_host(aslam_batch *b, const float *h_actions, const float *h_u,
+                             float *h_reward, float *h_obs, void *stream) {
+    if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
+    if (!h_actions) return fail_b(b, ASLAM_ERR_INVALID_ARG, "h_actions is NULL");
+    const size_t E = (size_t)b->hi.E;
+    const cudaStream_t s = (cudaStream_t)stream;
+    float *d_in = at<float>(b, b->off.io_in);
+    float *d_out = at<float>(b, b->off.io_out);
+    CK(cudaMemcpyAsync(d_in, h_actions, 8 * E, cudaMemcpyHostToDevice, s), "aslam_step_host: actions");
+    const float *d_u = nullptr;
+    if (h_u) {
+        CK(cudaMemcpyAsync(d_in + 2 * E, h_u, 4 * E, cudaMemcpyHostToDevice, s), "aslam_step_host: U");
+        d_u = d_in + 2 * E;
+    }
+    const aslam_status st = aslam_step_fused(b, d_in, d_u, h_reward ? d_out : nullptr,
+                                             h_obs ? d_out + E : nullptr, stream);
+    if (st != ASLAM_OK) return st;
+    if (h_reward)
+        CK(cudaMemcpyAsync(h_reward, d_out, 4 * E, cudaMemcpyDeviceToHost, s), "aslam_step_host: reward");
+    if (h_obs)
+        CK(cudaMemcpyAsync(h_obs, d_out + E, 4 * E * ((size_t)b->hi.b_max + 2), cudaMemcpyDeviceToHost, s),
+           "aslam_step_host: obs");
+    return ASLAM_OK;
 }
 
 aslam_status aslam_reward(aslam_batch *b, float *d_reward, void *stream) {
