@@ -544,8 +544,9 @@ def main():
     if dims == "3d":
         kbytes = {"step3d_kernel": rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env}
     else:
-        kbytes = {"integrate2d_kernel": E * 24 + E * 72,
-                  "sense2d_kernel": gt_step / 8 + Bsum * 8,
+        # the sensing kernel also integrates each env's action (state in
+        # and the start-of-step header out: 96 B per env)
+        kbytes = {"sense2d_kernel": gt_step / 8 + Bsum * 8 + E * 96,
                   "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
         if args.u_mode == "scanmatch":
             # the belief read once per env, the covariance read and written, U written

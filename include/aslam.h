@@ -397,8 +397,8 @@ aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d
  * [ASLAM_MAX_STEP_KERNELS], zero past the last kernel), the number of
  * kernels a step launches to *h_n_kernels and the number of timed steps to
  * *h_n_steps, and releases the events; ASLAM_ERR_STATE without a begin.
- * aslam_kernel_name(b, k) is the name of kernel k ("integrate2d_kernel",
- * "sense2d_kernel", then "uq2d_kernel" with ASLAM_U_SCANMATCH or
+ * aslam_kernel_name(b, k) is the name of kernel k ("sense2d_kernel", which
+ * also integrates the actions, then "uq2d_kernel" with ASLAM_U_SCANMATCH or
  * "slam_predict2d_kernel", "csm2d_kernel", "slam_window2d_kernel" with
  * ASLAM_U_FIXEDLAG, then "update2d_kernel"; 3-D: "step3d_kernel"), NULL
  * past the last.  A static string, owned by the library.

@@ -249,7 +249,8 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     {
         size_t nb = 0;
         const int sb = sense_block(hi.gt_words_max);
-        for (int e = 0; e < hi.E; ++e) nb += (size_t)(hi.B[e] + sb - 1) / sb;
+        // at least one bundle per env: its first bundle integrates the env
+        for (int e = 0; e < hi.E; ++e) nb += std::max<size_t>(1, (size_t)(hi.B[e] + sb - 1) / sb);
         o.bundles = add(8 * std::max<size_t>(nb, 1));
     }
     o.queue = add(16);         // {next item, CTAs finished, sensing CTAs finished}
@@ -748,12 +749,15 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                                                 (double)hi.D[e] * hi.D[e]));
         std::stable_sort(b->order.begin(), b->order.end(),
                          [&](int a, int c2) { return cost[a] > cost[c2]; });
-        // sensing bundles of sense_block() beams, costliest envs first
+        // sensing bundles of sense_block() beams, costliest envs first; an
+        // env without beams still gets one (it integrates the env's action)
         std::vector<int2> bundles;
         p.sense_block = sense_block(hi.gt_words_max);
         for (int q = 0; q < E; ++q) {
             const int e = b->order[q];
-            for (int b0 = 0; b0 < hi.B[e]; b0 += p.sense_block) bundles.push_back(make_int2(e, b0));
+            bundles.push_back(make_int2(e, 0));
+            for (int b0 = p.sense_block; b0 < hi.B[e]; b0 += p.sense_block)
+                bundles.push_back(make_int2(e, b0));
         }
         p.n_bundles = (int)bundles.size();
         p.bundles = at<int2>(b, o.bundles);
@@ -1216,12 +1220,11 @@ aslam_status aslam_profile_end(aslam_batch *b, double *h_ms, int32_t *h_n_kernel
 }
 
 const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
-    static const char *const k2[] = {"integrate2d_kernel", "sense2d_kernel", "update2d_kernel"};
-    static const char *const k2u[] = {"integrate2d_kernel", "sense2d_kernel", "uq2d_kernel",
-                                      "update2d_kernel"};
+    static const char *const k2[] = {"sense2d_kernel", "update2d_kernel"};
+    static const char *const k2u[] = {"sense2d_kernel", "uq2d_kernel", "update2d_kernel"};
     if (!b || k < 0) return nullptr;
     if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
-    static const char *const k2s[] = {"integrate2d_kernel", "sense2d_kernel",
+    static const char *const k2s[] = {"sense2d_kernel",
                                       "slam_predict2d_kernel", "csm2d_kernel",
                                       "slam_window2d_kernel", "update2d_kernel"};
     if (b->p.u_mode == ASLAM_U_SCANMATCH) return k < kStep2DKernels + 1 ? k2u[k] : nullptr;

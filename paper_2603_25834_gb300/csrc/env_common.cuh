@@ -9,19 +9,32 @@ namespace aslam {
 
 struct EnvStart {
     float x, y, th, u_prev;
-    int t, gstep, reset;
+    int t, gstep, reset, ep;
     long long Hq;
+};
+
+// Handed from the 2-D sensing kernel to the kernels after it, one per env:
+// the integrated start of the step, the robot's Q16 cell position, heading
+// and collision cell, and the sums and minima the sensing CTAs reduce into
+// (reset to 0 / r_max by the update kernel once it has read them).
+struct EnvSense {
+    EnvStart start;
+    int Px, Py, col_cell, gt_cells;
+    float c, s, dmin_meas, dmin_true;
+    int upd_cells;               // cells of this step's belief walks (update cost)
 };
 
 // Reset a done env to its next spawn pose, then integrate the action with
 // the Euler unicycle (pre-step heading, heading wrapped to [-pi, pi)).
-__device__ __forceinline__ EnvStart begin_env(const Step2DParams &p, int e, long long ncell) {
+// Reads only: the 2-D step evaluates it in every sensing CTA of the env and
+// commits it (commit_start) in the update kernel.
+__device__ __forceinline__ EnvStart integrate_env(const Step2DParams &p, int e, long long ncell) {
     EnvStart s;
     s.reset = p.done[e] != 0;
+    s.ep = p.ep[e];
     if (s.reset) {
-        const int ep = p.ep[e] + 1;
-        p.ep[e] = ep;
-        const float *sp = p.spawn + ((long long)e * p.n_spawn + (ep % p.n_spawn)) * 3;
+        s.ep += 1;
+        const float *sp = p.spawn + ((long long)e * p.n_spawn + (s.ep % p.n_spawn)) * 3;
         s.x = sp[0];
         s.y = sp[1];
         s.th = sp[2];
@@ -49,11 +62,23 @@ __device__ __forceinline__ EnvStart begin_env(const Step2DParams &p, int e, long
     if (th >= pi_f) th = fsub(th, two_pi_f);
     if (th < -pi_f) th = fadd(th, two_pi_f);
     s.th = th;
+    s.gstep = p.g[e];
+    return s;
+}
+
+// Writes an integrated start into the env state: pose, step, episode.
+__device__ __forceinline__ void commit_start(const Step2DParams &p, int e, const EnvStart &s) {
+    if (s.reset) p.ep[e] = s.ep;
     p.x[e] = s.x;
     p.y[e] = s.y;
     p.th[e] = s.th;
     p.t[e] = s.t;
-    s.gstep = p.g[e];
+}
+
+// integrate_env + commit_start, for a step that runs in one kernel.
+__device__ __forceinline__ EnvStart begin_env(const Step2DParams &p, int e, long long ncell) {
+    const EnvStart s = integrate_env(p, e, ncell);
+    commit_start(p, e, s);
     return s;
 }
 
@@ -66,9 +91,12 @@ struct EnvTotals {
 // Entropy gain, visit grid (Eq. 8-9), reward terms (Eq. 7-17), termination
 // and the per-env outputs.  One thread, in fp32: every term is a product or
 // quotient of a few fp32 inputs (a few ulp each), and the fp64 pipe of
-// sm_103a is slow enough that fp64 here would lengthen the step.
+// sm_103a is slow enough that fp64 here would lengthen the step.  commit:
+// also write the start of the step (integrate_env) into the env state.
 __device__ __forceinline__ void finish_env(const Step2DParams &p, int e, int W, int H,
-                                           const EnvStart &s, int col_cell, const EnvTotals &r) {
+                                           const EnvStart &s, int col_cell, const EnvTotals &r,
+                                           bool commit) {
+    if (commit) commit_start(p, e, s);
     const long long Hq = s.Hq + r.dHq;
     p.Hq[e] = Hq;
     constexpr float kInvLut = 1.0f / 1099511627776.0f;   // 2^-40, exact

@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "aslam_internal.cuh"
+#include "env_common.cuh"
 #include "window_gn.cuh"
 
 namespace aslam {
@@ -42,10 +43,11 @@ __global__ void slam_predict2d_kernel(const Step2DParams p) {
         const float ux = fmul(v, p.dt), uth = fmul(w, p.dt);
         float px, py, pth;
         if (n == 0) {
-            // a fresh window starts from the known pose
-            px = p.x[e];
-            py = p.y[e];
-            pth = p.th[e];
+            // a fresh window starts from the known pose: this step's start
+            const EnvStart &st = reinterpret_cast<const EnvSense *>(p.env_sense)[e].start;
+            px = st.x;
+            py = st.y;
+            pth = st.th;
         } else {
             const float *last = p.win_x + ((long long)e * p.slam_L + n - 1) * 3;
             float s, c;

@@ -1,13 +1,13 @@
-// step2d.cu -- the batched 2-D environment step on sm_103a, in three kernels.
-//
-// integrate2d_kernel: one thread per environment resets a done env to its
-//   next spawn pose and integrates the action (Euler unicycle, Sec. III-C
-//   Eq. 4 / Sec. IV-A robot), then writes the env's sensing header (Q16
-//   origin, heading sin/cos, collision cell, reduction seeds).
+// step2d.cu -- the batched 2-D environment step on sm_103a, in two kernels.
 //
 // sense2d_kernel: one small CTA per bundle of up to `sense_block` beams of
-//   one env.  The env's ground truth is staged in shared memory as one bit
-//   per cell; every thread walks its beam's cells with an exact fixed-point
+//   one env (at least one bundle per env).  Thread 0 of every bundle resets
+//   a done env to its next spawn pose and integrates the action (Euler
+//   unicycle, Sec. III-C Eq. 4 / Sec. IV-A robot) from the state of the last
+//   step, which no kernel of this step writes; bundle 0 publishes the env's
+//   header (start, Q16 origin, heading sin/cos, collision cell) and the
+//   update kernel commits the start to the env state.  The env's ground
+//   truth is staged in shared memory as one bit per cell; every thread walks its beam's cells with an exact fixed-point
 //   traversal (Amanatides-Woo order, exact 64-bit comparisons, ties Y first)
 //   to the first occupied cell (Sec. IV-A LiDAR), draws the range noise, and
 //   records how many cells the belief walk to the measured endpoint has
@@ -45,14 +45,6 @@
 #include "env_common.cuh"
 
 namespace aslam {
-
-// Handed from the sensing kernel to the update kernel, one per env.
-struct EnvSense {
-    EnvStart start;
-    int Px, Py, col_cell, gt_cells;
-    float c, s, dmin_meas, dmin_true;
-    int upd_cells;               // cells of this step's belief walks (update cost)
-};
 
 size_t env_sense_bytes() { return sizeof(EnvSense); }
 
@@ -158,29 +150,6 @@ __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W
     return ry + (int)cx + 1;
 }
 
-// ---------------------------------------------------------------------------
-// Integration kernel: one thread per env
-// ---------------------------------------------------------------------------
-__global__ void integrate2d_kernel(const Step2DParams p) {
-    pdl_trigger();                       // the sensing grid may start staging its maps
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += gridDim.x * blockDim.x) {
-        const int W = p.W[e], H = p.H[e];
-        EnvSense es;
-        es.start = begin_env(p, e, (long long)W * H);
-        es.Px = q16_of(es.start.x, p.res);
-        es.Py = q16_of(es.start.y, p.res);
-        const int ri = es.Px >> 16, rj = es.Py >> 16;
-        const bool inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
-        es.col_cell = !inside || gt_bit(p.gt_bits + p.gtb_off[e], rj * W + ri);
-        det_sincos(es.start.th, es.s, es.c);
-        es.gt_cells = 0;
-        es.upd_cells = 0;
-        es.dmin_meas = p.r_max;      // reduced with atomicMin on the (positive) float bits
-        es.dmin_true = p.r_max;
-        reinterpret_cast<EnvSense *>(p.env_sense)[e] = es;
-    }
-}
-
 // Work order of the update kernel's queue for this step, costliest env first
 // (longest-processing-time-first keeps the persistent CTAs' last envs short).
 // The cost is the env's belief-walk cells, bucketed into 256 classes of the
@@ -272,6 +241,13 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         prefetch_l2(p.belief + p.map_off[e], (unsigned)min(2LL * W * H, 1LL << 30));
     }
     pdl_trigger();                       // the update grid may start its prologue
+    // The env's start of the step, computed alike by every bundle of the env
+    // by the first lane of the last warp while the others stage the ground
+    // truth.  This kernel is an ordinary launch (never a programmatic
+    // dependent), so the last step's state is complete when it starts.
+    const int itid = blockDim.x - 32;
+    EnvStart st0;
+    if (tid == itid) st0 = integrate_env(p, e, (long long)W * H);
     {
         // the env's ground truth, one bit per cell, into shared memory
         const int words = (int)(((long long)W * H + 31) >> 5);
@@ -279,17 +255,39 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
         for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
     }
-    pdl_wait();                          // the integration's EnvSense records are complete
+    __syncthreads();
+    __shared__ EnvSense s_hdr;
+    if (tid == itid) {
+        EnvSense h;
+        h.start = st0;
+        h.Px = q16_of(h.start.x, p.res);
+        h.Py = q16_of(h.start.y, p.res);
+        const int ri = h.Px >> 16, rj = h.Py >> 16;
+        const bool inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
+        h.col_cell = !inside || gt_bit(s_gt, rj * W + ri);
+        det_sincos(h.start.th, h.s, h.c);
+        s_hdr = h;
+        if (bundle.y == 0) {
+            // the header for the kernels after this one; the reduced fields
+            // belong to the atomics of every bundle and are left alone
+            esp->start = h.start;
+            esp->Px = h.Px;
+            esp->Py = h.Py;
+            esp->col_cell = h.col_cell;
+            esp->c = h.c;
+            esp->s = h.s;
+        }
+    }
     __syncthreads();
     int gc = 0, uc = 0;
     float dmin_m = p.r_max, dmin_t = p.r_max;
     if (b < B) {
         const unsigned *gt = s_gt;
-        const int Px = esp->Px, Py = esp->Py;
+        const int Px = s_hdr.Px, Py = s_hdr.Py;
         const int i0 = Px >> 16, j0 = Py >> 16;
         const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
         const long long ray = p.ray_off[e] + b;
-        const Beam bm = beam_setup(p, ray, Px, Py, i0, j0, esp->c, esp->s);
+        const Beam bm = beam_setup(p, ray, Px, Py, i0, j0, s_hdr.c, s_hdr.s);
         bool hit = false;
         float z_true = p.r_max, z = p.r_max;
         int code = -1;
@@ -334,7 +332,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
             gc = cells;
             z = z_true;
             if (hit) {
-                const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)esp->start.gstep, (unsigned)b);
+                const float g = det_gauss(p.key, (unsigned)(p.env_base + e), (unsigned)s_hdr.start.gstep, (unsigned)b);
                 z = measured_range(z_true, g, p.sigma, p.r_min, p.r_max, p.dec_scale);
             }
             const int Tz = hit ? q16_of(z, p.res) : p.Tmax;
@@ -545,7 +543,13 @@ __device__ __forceinline__ void load_env(const Step2DParams &p, int item, EnvSha
         return;
     }
     const int e = p.order[item];
-    const EnvSense es = reinterpret_cast<const EnvSense *>(p.env_sense)[e];
+    EnvSense *esp = reinterpret_cast<EnvSense *>(p.env_sense) + e;
+    const EnvSense es = *esp;
+    // the reduced fields start over for the next step's sensing
+    esp->gt_cells = 0;
+    esp->upd_cells = 0;
+    esp->dmin_meas = p.r_max;        // reduced with atomicMin on the (positive) float bits
+    esp->dmin_true = p.r_max;
     const int W = p.W[e], H = p.H[e];
     sh.e = e;
     sh.W = W;
@@ -592,7 +596,7 @@ __device__ __forceinline__ void finish_pending(const Step2DParams &p, const EnvS
     r.gt_cells = sh.gt_cells;
     r.dmin_meas = sh.dmin_meas;
     r.dmin_true = sh.dmin_true;
-    finish_env(p, sh.e, sh.W, sh.H, sh.start, sh.col_cell, r);
+    finish_env(p, sh.e, sh.W, sh.H, sh.start, sh.col_cell, r, true);
 }
 
 // One persistent CTA per SM slot takes envs from a queue.  The last warp is
@@ -924,6 +928,13 @@ __global__ void init_state_kernel(const Step2DParams p) {
         p.Hq[e] = (long long)p.W[e] * p.H[e] * p.Dd[e] * p.lut[p.clamp_q];
         p.reward[e] = 0.0f;
         if (p.win_n) p.win_n[e] = 0;
+        if (p.env_sense) {
+            EnvSense *es = reinterpret_cast<EnvSense *>(p.env_sense) + e;
+            es->gt_cells = 0;
+            es->upd_cells = 0;
+            es->dmin_meas = p.r_max;
+            es->dmin_true = p.r_max;
+        }
         if (p.pose_cov) {
             double *S = p.pose_cov + 6 * (long long)e;
             S[0] = p.uq_prior[0];
@@ -1023,45 +1034,39 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
                           cudaStream_t s, const cudaEvent_t *ev) {
     cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    integrate2d_kernel<<<(p.E + 127) / 128, 128, 0, s>>>(p);
-    e = cudaGetLastError();
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-    if (e != cudaSuccess) return e;
-    // without per-kernel events the sensing and update kernels are launched
-    // as programmatic dependents of the kernel before them
+    // the first kernel of the step is an ordinary launch; without per-kernel
+    // events the update kernel is a programmatic dependent of the sensing one
     const bool pdl = ev == nullptr;
-    if (p.n_bundles > 0) {
-        const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
-        e = launch_pdl(sense2d_kernel, dim3(p.n_bundles), dim3(p.sense_block), gt_bytes, s, pdl, p);
-    }
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
+    e = launch_pdl(sense2d_kernel, dim3(p.n_bundles), dim3(p.sense_block), gt_bytes, s, false, p);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;
     if (p.u_mode == 2) {
         // SLAM backbone: predict, scan-match, window Gauss-Newton -> U_t
-        e = launch_slam2d(p, s, ev ? ev + 3 : nullptr);
+        e = launch_slam2d(p, s, ev ? ev + 2 : nullptr);
         if (e != cudaSuccess) return e;
         Step2DParams q = p;
         q.u_in = p.u_scan;
         q.upd_w = p.slam_weighted ? p.slam_upd_w : nullptr;
         update2d_kernel<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[6], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], s);
         return e;
     }
     if (p.u_mode == 1) {
         // in-step U_t from the map before this scan; the update's reward reads it
         e = launch_uq2d(p, s);
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
         if (e != cudaSuccess) return e;
         Step2DParams q = p;
         q.u_in = p.u_scan;
         update2d_kernel<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
         return e;
     }
-    e = launch_pdl(update2d_kernel, dim3(grid), dim3(block), smem, s, pdl && p.n_bundles > 0, p);
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+    e = launch_pdl(update2d_kernel, dim3(grid), dim3(block), smem, s, pdl, p);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;
 }
 

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                 t.dmin_meas = fminf(t.dmin_meas, r_dm[q]);
                 t.dmin_true = fminf(t.dmin_true, r_dt[q]);
             }
-            finish_env(p, e, W, H, sh.start, sh.col_cell, t);
+            finish_env(p, e, W, H, sh.start, sh.col_cell, t, false);
         }
         if (p.out_obs) {
             float *o = p.out_obs + (long long)e * (p.b_max + 2);

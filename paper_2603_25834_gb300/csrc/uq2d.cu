@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "aslam_internal.cuh"
+#include "env_common.cuh"
 
 namespace aslam {
 namespace {
@@ -88,7 +89,9 @@ __global__ void __launch_bounds__(512, 3) uq2d_kernel(const Step2DParams p, int 
     float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (!reset) {
         const short *Lq = p.belief + p.map_off[e];
-        const float x = p.x[e], y = p.y[e], th = p.th[e];
+        // the pose at the start of this step (integrated by the sensing kernel)
+        const EnvStart &st = reinterpret_cast<const EnvSense *>(p.env_sense)[e].start;
+        const float x = st.x, y = st.y, th = st.th;
         MapView m{Lq, W, H, 0, 0, W};
         if (staged) {
             // every tap (clamped to the map) is within R cells of the robot's cell

@@ -32,7 +32,7 @@ def test_profile_names_counts_and_no_side_effects(aslam_gpu, dims):
     if dims == 2:
         inp = synth.paper_scale(E=8, W=128, B=90, seed=31)
         cfg = dict(r_max_m=6.0, noise_sigma_m=0.01)
-        names = ["integrate2d_kernel", "sense2d_kernel", "update2d_kernel"]
+        names = ["sense2d_kernel", "update2d_kernel"]
     else:
         inp = synth.voxel_batch(E=4, W=32, H=32, D=8, n_az=32, K=2)
         cfg = dict(r_max_m=4.0, noise_sigma_m=0.01, n_rings=4)
