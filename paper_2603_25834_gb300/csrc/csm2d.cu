@@ -25,9 +25,12 @@
 // outside the map scores 0 for every candidate and is pointed at the centre
 // of the sentinel block; any other endpoint's candidate cells all lie in the
 // bordered map.  So the per-rotation staging stores one shared address per
-// beam and the candidate loop is a load, an add, and nothing else.  The row
-// stride is chosen on the host so that the candidate rows one warp reads
-// fall in distinct shared-memory banks.
+// beam, and each thread sums four horizontally adjacent candidates at once:
+// two aligned words hold their four evidence bytes (a funnel shift by the
+// address's byte offset), added as two pairs of 16-bit lanes (a thread adds
+// at most ceil(1024 / 6) beams of <= 255, so a lane never carries).  The
+// row stride is chosen on the host so that the words one warp reads fall in
+// as few shared-memory banks per bank as it can.
 #include <cmath>
 
 #include "aslam_internal.cuh"
@@ -134,7 +137,11 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
     const int nslice = nt / NC;                  // beam slices per candidate
     const int c = tid % NC, sl = tid / NC;
     const int ci_off = c % side - a.n_xy, cj_off = c / side - a.n_xy;
-    const int c_off = cj_off * ws + ci_off;      // candidate offset in the staged map
+    // staged map: thread (slice sl4, row cj4, group gi4) sums candidates
+    // i = 4 gi4 .. 4 gi4 + 3 (those < side) of row cj4
+    const int G4 = (side + 3) >> 2, NG = side * G4, nslice4 = nt / NG;
+    const int sl4 = tid / NG, g4 = tid % NG, cj4 = g4 / G4, gi4 = g4 % G4;
+    const int c_off4 = (cj4 - a.n_xy) * ws + 4 * gi4 - a.n_xy;
     // centre of the zero sentinel block below the bordered map
     const int sentinel = (H + 2 * brd + a.n_xy) * ws + a.n_xy;
     // the returned beams (range < r_max), compacted in beam order once
@@ -180,27 +187,51 @@ __global__ void __launch_bounds__(kCsmBlock) csm2d_kernel(const Step2DParams p, 
             }
         }
         __syncthreads();
-        int acc = 0;
-        if (sl < nslice) {
-            if (staged) {
-                const unsigned char *mc = s_map + c_off;
+        if (staged) {
+            unsigned lo = 0u, hi = 0u;          // candidates (0, 2) and (1, 3) of the group
+            if (sl4 < nslice4) {
+                const unsigned *words = reinterpret_cast<const unsigned *>(s_map);
                 const int *addr = reinterpret_cast<const int *>(s_cell);
-                for (int q = sl; q < nret; q += nslice) acc += mc[addr[2 * q]];
-            } else {
+                for (int q = sl4; q < nret; q += nslice4) {
+                    const int ad = addr[2 * q] + c_off4;
+                    const unsigned v = __funnelshift_r(words[ad >> 2], words[(ad >> 2) + 1],
+                                                       (unsigned)(ad & 3) << 3);
+                    lo += v & 0x00ff00ffu;
+                    hi += (v >> 8) & 0x00ff00ffu;
+                }
+            }
+            __syncthreads();                      // every address is read: s_cell is free
+            int *part = reinterpret_cast<int *>(s_cell);          // [nslice4][NC]
+            if (sl4 < nslice4) {
+                const int sums[4] = {(int)(lo & 0xffffu), (int)(hi & 0xffffu), (int)(lo >> 16),
+                                     (int)(hi >> 16)};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (4 * gi4 + u < side) part[sl4 * NC + cj4 * side + 4 * gi4 + u] = sums[u];
+            }
+            __syncthreads();
+            if (tid < NC) {
+                int sum = 0;
+                for (int q = 0; q < nslice4; ++q) sum += part[q * NC + tid];
+                s_score[k * NC + tid] = sum;
+            }
+        } else {
+            int acc = 0;
+            if (sl < nslice) {
                 for (int q = sl; q < nret; q += nslice) {
                     const int2 cc = s_cell[q];
                     const int i = cc.x + ci_off, j = cc.y + cj_off;
                     if ((unsigned)i < (unsigned)W && (unsigned)j < (unsigned)H && !empty)
                         acc += (int)evidence(L[(long long)j * W + i]);
                 }
+                s_part[tid] = acc;
             }
-            s_part[tid] = acc;
-        }
-        __syncthreads();
-        if (tid < NC) {
-            int sum = 0;
-            for (int q = 0; q < nslice; ++q) sum += s_part[q * NC + tid];
-            s_score[k * NC + tid] = sum;
+            __syncthreads();
+            if (tid < NC) {
+                int sum = 0;
+                for (int q = 0; q < nslice; ++q) sum += s_part[q * NC + tid];
+                s_score[k * NC + tid] = sum;
+            }
         }
     }
     __syncthreads();
@@ -266,31 +297,35 @@ int csm_max_n() { return kCsmMaxN; }
 
 namespace {
 
-// true when, for every base address, the lanes of each warp that read the
-// same beam (one slice) touch distinct words in distinct banks or share a
-// word: the staged candidate loads then take one shared-memory wavefront.
-// Moving the base by a word rotates every lane's bank by one, so the byte
-// offset of the base within its word is all that matters.
-bool csm_stride_conflict_free(int ws, int n) {
-    const int side = 2 * n + 1, NC = side * side, nslice = kCsmBlock / NC;
-    for (int w0 = 0; w0 < kCsmBlock; w0 += 32)
-        for (int base = 0; base < 4; ++base) {
-            int word_of_bank[32];
-            int slice_of_bank[32];
-            for (int k = 0; k < 32; ++k) word_of_bank[k] = -1;
+// Shared-memory wavefronts of the worst warp for row stride ws (bytes): the
+// lanes of one slice read the same beam, so with row stride ws / 4 words,
+// lane (cj, gi) reads word w0 + cj ws / 4 + gi (and the word after it);
+// lanes of different slices read other beams and are not counted.
+int csm_stride_cost(int ws, int n) {
+    const int side = 2 * n + 1, G4 = (side + 3) / 4, NG = side * G4, nslice = kCsmBlock / NG;
+    const int wsw = ws / 4;
+    int worst = 1;
+    for (int w0 = 0; w0 < kCsmBlock; w0 += 32) {
+        for (int sl = 0; sl < nslice; ++sl) {
+            int words[32], nw = 0;
             for (int t = w0; t < w0 + 32; ++t) {
-                const int sl = t / NC, c = t % NC;
-                if (sl >= nslice) continue;
-                const int a = base + (c / side) * ws + c % side;     // offsets shifted by n
-                const int word = a >> 2, bank = word & 31;
-                if (word_of_bank[bank] >= 0 && slice_of_bank[bank] == sl &&
-                    word_of_bank[bank] != word)
-                    return false;
-                word_of_bank[bank] = word;
-                slice_of_bank[bank] = sl;
+                if (t / NG != sl) continue;
+                const int g = t % NG;
+                words[nw++] = (g / G4) * wsw + g % G4;
+            }
+            for (int bank = 0; bank < 32; ++bank) {
+                int distinct = 0;
+                for (int u = 0; u < nw; ++u) {
+                    if ((words[u] & 31) != bank) continue;
+                    bool seen = false;
+                    for (int v = 0; v < u; ++v) seen = seen || words[v] == words[u];
+                    distinct += !seen;
+                }
+                worst = distinct > worst ? distinct : worst;
             }
         }
-    return true;
+    }
+    return worst;
 }
 
 }  // namespace
@@ -301,18 +336,22 @@ size_t csm_map_layout(const int *W, const int *H, int E, int n, int *ws) {
         wmax = W[e] > wmax ? W[e] : wmax;
         hmax = H[e] > hmax ? H[e] : hmax;
     }
-    // bordered width in words; the first stride within 32 words that keeps
-    // a warp's candidate rows apart in the banks (else the narrowest)
+    // bordered width in words; of the next 8 strides (a wider pad costs
+    // occupancy), the first with the fewest bank conflicts across a warp's
+    // candidate words
     const int w0 = (csm_col0(n) + wmax + 2 * n + 3) / 4;
-    int words = w0;
-    for (int w = w0; w < w0 + 32; ++w)
-        if (csm_stride_conflict_free(4 * w, n)) {
+    int words = w0, best = 1 << 30;
+    for (int w = w0; w < w0 + 8; ++w) {
+        const int c = csm_stride_cost(4 * w, n);
+        if (c < best) {
+            best = c;
             words = w;
-            break;
         }
+    }
     *ws = 4 * words;
-    // bordered map rows plus the sentinel block of 2n + 1 zero rows
-    const size_t bytes = (size_t)(4 * words) * (size_t)(hmax + 4 * n + 2 * n + 1);
+    // bordered map rows plus the sentinel block of 2n + 1 zero rows, and 16
+    // bytes for the word after the last one a candidate group reads
+    const size_t bytes = (size_t)(4 * words) * (size_t)(hmax + 4 * n + 2 * n + 1) + 16;
     return (bytes + 15) & ~(size_t)15;
 }
 
