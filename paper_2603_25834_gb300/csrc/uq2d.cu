@@ -63,23 +63,30 @@ __device__ __forceinline__ double det3d(const double *M) {
            M[2] * (M[3] * M[7] - M[4] * M[6]);
 }
 
-// 3x3 inverse through the adjugate.
+// 3x3 inverse through the adjugate, one reciprocal of the determinant.
 __device__ __forceinline__ void inv3d(const double *M, double *R) {
-    const double d = det3d(M);
-    R[0] = (M[4] * M[8] - M[5] * M[7]) / d;
-    R[1] = (M[2] * M[7] - M[1] * M[8]) / d;
-    R[2] = (M[1] * M[5] - M[2] * M[4]) / d;
-    R[3] = (M[5] * M[6] - M[3] * M[8]) / d;
-    R[4] = (M[0] * M[8] - M[2] * M[6]) / d;
-    R[5] = (M[2] * M[3] - M[0] * M[5]) / d;
-    R[6] = (M[3] * M[7] - M[4] * M[6]) / d;
-    R[7] = (M[1] * M[6] - M[0] * M[7]) / d;
-    R[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+    const double id = 1.0 / det3d(M);
+    R[0] = (M[4] * M[8] - M[5] * M[7]) * id;
+    R[1] = (M[2] * M[7] - M[1] * M[8]) * id;
+    R[2] = (M[1] * M[5] - M[2] * M[4]) * id;
+    R[3] = (M[5] * M[6] - M[3] * M[8]) * id;
+    R[4] = (M[0] * M[8] - M[2] * M[6]) * id;
+    R[5] = (M[2] * M[3] - M[0] * M[5]) * id;
+    R[6] = (M[3] * M[7] - M[4] * M[6]) * id;
+    R[7] = (M[1] * M[6] - M[0] * M[7]) * id;
+    R[8] = (M[0] * M[4] - M[1] * M[3]) * id;
 }
 
 // Three CTAs per SM (at most 42 registers a thread) hide the latency of
-// each beam's sample chain better than fewer, fatter CTAs.
-__global__ void __launch_bounds__(512, 3) uq2d_kernel(const Step2DParams p, int R, bool staged) {
+// each beam's sample chain better than fewer, fatter CTAs.  When the beams
+// fit twice into a CTA (split = 2) two threads share a beam (samples
+// [0, K1) and [K1, K)), halving the chain that sets the time; with more
+// beams, fatter CTAs would cost more waves than the halved chain saves
+// (timed at 360 beams: 97 us one thread per beam, 121 us two).
+constexpr int kUqBlockMax = 512;
+
+__global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams p, int R, bool staged,
+                                                              int split) {
     extern __shared__ __align__(16) short s_win[];
     __shared__ float red[6][32];
     const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -110,13 +117,24 @@ __global__ void __launch_bounds__(512, 3) uq2d_kernel(const Step2DParams p, int 
         det_sincos(th, s, c);
         const float inv_res = 1.0f / p.res, scale = p.logodds_scale;
         const float r_far = (float)p.uq_K * p.uq_ds;
-        for (int b = tid; b < B; b += nt) {
-            const float2 cs = p.beam_cs[p.ray_off[e] + b];
+        // The sweep is linear in (T, dT): the second half runs from T = 1,
+        // dT = 0 and also sums A = sum_k T'_k p_k s_k; with the first half's
+        // (T, dT) at the split, the beam's totals are
+        //   dr = dr_1 + dT_1 A + T_1 dr'_2,   dT = dT_1 Q + T_1 dT'_2,
+        // Q the second half's product of q.
+        const int h = split == 2 ? (tid & 1) : 0;
+        const int K1 = split == 2 ? (p.uq_K + 1) >> 1 : p.uq_K;
+        const int k0 = h ? K1 : 0, k1 = h ? p.uq_K : K1;
+        for (int b0 = 0; b0 < B; b0 += nt / split) {
+            const int b = b0 + tid / split;
+            const bool live = b < B;
+            float2 cs = make_float2(1.f, 0.f);
+            if (live) cs = p.beam_cs[p.ray_off[e] + b];
             const float cp = c * cs.x - s * cs.y, sp = s * cs.x + c * cs.y;
-            float T = 1.f;
+            float T = 1.f, A = 0.f;
             float dT0 = 0.f, dT1 = 0.f, dT2 = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
             Tap t;
-            for (int k = 0; k < p.uq_K; ++k) {
+            for (int k = k0; live && k < k1; ++k) {
                 const float sk = (float)(k + 1) * p.uq_ds;
                 bilinear_q(m, inv_res, scale, x + sk * cp, y + sk * sp, t);
                 // p = sigmoid(l), q = 1 - p, without cancellation (fast exp and
@@ -131,18 +149,37 @@ __global__ void __launch_bounds__(512, 3) uq2d_kernel(const Step2DParams p, int 
                 dr0 += (dT0 * pr + T * d0) * sk;
                 dr1 += (dT1 * pr + T * d1) * sk;
                 dr2 += (dT2 * pr + T * d2) * sk;
+                A += T * pr * sk;
                 dT0 = dT0 * q - T * d0;
                 dT1 = dT1 * q - T * d1;
                 dT2 = dT2 * q - T * d2;
                 T *= q;
             }
-            const float J0 = dr0 + dT0 * r_far, J1 = dr1 + dT1 * r_far, J2 = dr2 + dT2 * r_far;
-            a[0] += J0 * J0;
-            a[1] += J0 * J1;
-            a[2] += J0 * J2;
-            a[3] += J1 * J1;
-            a[4] += J1 * J2;
-            a[5] += J2 * J2;
+            // the second half's sums to its first half (the lane below); one
+            // thread per beam combines with an empty second half
+            float Q2 = 1.f, A2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
+            if (split == 2) {                      // uniform over the CTA
+                Q2 = __shfl_down_sync(0xffffffffu, T, 1);
+                A2 = __shfl_down_sync(0xffffffffu, A, 1);
+                e0 = __shfl_down_sync(0xffffffffu, dT0, 1);
+                e1 = __shfl_down_sync(0xffffffffu, dT1, 1);
+                e2 = __shfl_down_sync(0xffffffffu, dT2, 1);
+                f0 = __shfl_down_sync(0xffffffffu, dr0, 1);
+                f1 = __shfl_down_sync(0xffffffffu, dr1, 1);
+                f2 = __shfl_down_sync(0xffffffffu, dr2, 1);
+            }
+            if (h == 0 && live) {
+                const float g0 = dr0 + dT0 * A2 + T * f0, g1 = dr1 + dT1 * A2 + T * f1;
+                const float g2 = dr2 + dT2 * A2 + T * f2;
+                const float u0 = dT0 * Q2 + T * e0, u1 = dT1 * Q2 + T * e1, u2 = dT2 * Q2 + T * e2;
+                const float J0 = g0 + u0 * r_far, J1 = g1 + u1 * r_far, J2 = g2 + u2 * r_far;
+                a[0] += J0 * J0;
+                a[1] += J0 * J1;
+                a[2] += J0 * J2;
+                a[3] += J1 * J1;
+                a[4] += J1 * J2;
+                a[5] += J2 * J2;
+            }
         }
     }
 #pragma unroll
@@ -193,13 +230,15 @@ constexpr size_t kUqWindowMax = 48 * 1024;     // shared bytes for the staged ma
 }  // namespace
 
 cudaError_t launch_uq2d(const Step2DParams &p, cudaStream_t s) {
-    int block = ((p.b_max + 31) / 32) * 32;
-    block = block < 64 ? 64 : (block > 512 ? 512 : block);
+    // two threads per beam when that still fits one CTA
+    const int split = 2 * p.b_max <= kUqBlockMax ? 2 : 1;
+    int block = ((split * p.b_max + 31) / 32) * 32;
+    block = block < 64 ? 64 : (block > kUqBlockMax ? kUqBlockMax : block);
     // samples reach K*ds from the robot; taps one cell further, plus rounding
     const int R = (int)ceilf(((float)p.uq_K * p.uq_ds) / p.res) + 2;
     const size_t win = 2 * (size_t)(2 * R + 1) * (2 * R + 1);
     const bool staged = win <= kUqWindowMax;
-    uq2d_kernel<<<p.E, block, staged ? win : 0, s>>>(p, R, staged);
+    uq2d_kernel<<<p.E, block, staged ? win : 0, s>>>(p, R, staged, split);
     return cudaGetLastError();
 }
 
