@@ -562,12 +562,23 @@ def main():
                                     if k in kbytes else None)}
                for k, v in kernel_ms.items()}
     traffic = None
+    issue = None
     tf = traffic_file(kern, args.workload)
     if os.path.exists(tf):
         with open(tf) as fh:
             tr = json.load(fh)
         if tr.get("kernel_hash") == kernel_hash(dims) and tr.get("envs") == E:
             traffic = tr.get("dram_bytes_per_launch")
+            if tr.get("warp_inst_per_launch"):
+                # the kernel is issue-bound: its warp instructions (ncu) over the
+                # live launch time, against one instruction per scheduler per clock
+                n_inst = float(tr["warp_inst_per_launch"])
+                mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+                ipeak = 152 * 4 * mhz * 1e6
+                issue = {"warp_inst_per_launch": n_inst, "achieved": n_inst / (k_ms / 1e3),
+                         "peak": ipeak, "unit": "warp-inst/s",
+                         "frac": n_inst / (k_ms / 1e3) / ipeak,
+                         "peak_kind": "152 SMs x 4 schedulers x max SM clock"}
     cpu = None
     if not args.no_cpu_baseline and args.workload == "paper_scale":
         n_s, steps_s = 48, 60
@@ -586,7 +597,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " hbm_gbs (STREAM-style copy)",
-                     "bytes_per_launch": kbytes[kern], "ms_per_launch": k_ms, "kernel": kern},
+                     "bytes_per_launch": kbytes[kern], "ms_per_launch": k_ms, "kernel": kern,
+                     "issue": issue},
         "kernels": kernels,
         "kernel_pass": {"steps": prof_steps,
                         "note": "per-kernel CUDA events in a separate pass; they serialise "

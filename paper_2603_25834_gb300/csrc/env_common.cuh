@@ -29,9 +29,14 @@ struct EnvSense {
 // Reads only: the 2-D step evaluates it in every sensing CTA of the env and
 // commits it (commit_start) in the update kernel.
 __device__ __forceinline__ EnvStart integrate_env(const Step2DParams &p, int e, long long ncell) {
+    // every load that does not depend on the reset flag is issued first
+    const int done = p.done[e], ep = p.ep[e], t0 = p.t[e], g = p.g[e];
+    const float x0 = p.x[e], y0 = p.y[e], th0 = p.th[e], up0 = p.u_prev[e];
+    const long long Hq0 = p.Hq[e];
+    const float a_v = p.actions[2 * e], a_w = p.actions[2 * e + 1];   // 4-byte aligned input
     EnvStart s;
-    s.reset = p.done[e] != 0;
-    s.ep = p.ep[e];
+    s.reset = done != 0;
+    s.ep = ep;
     if (s.reset) {
         s.ep += 1;
         const float *sp = p.spawn + ((long long)e * p.n_spawn + (s.ep % p.n_spawn)) * 3;
@@ -42,18 +47,18 @@ __device__ __forceinline__ EnvStart integrate_env(const Step2DParams &p, int e, 
         s.u_prev = 0.0f;
         s.Hq = ncell * p.lut[p.clamp_q];
     } else {
-        s.x = p.x[e];
-        s.y = p.y[e];
-        s.th = p.th[e];
-        s.t = p.t[e];
-        s.u_prev = p.u_prev[e];
-        s.Hq = p.Hq[e];
+        s.x = x0;
+        s.y = y0;
+        s.th = th0;
+        s.t = t0;
+        s.u_prev = up0;
+        s.Hq = Hq0;
     }
     s.t += 1;
     const float pi_f = (float)3.14159265358979323846;
     const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
-    const float v = fminf(fmaxf(p.actions[2 * e], 0.0f), p.v_max);
-    const float w = fminf(fmaxf(p.actions[2 * e + 1], -p.w_max), p.w_max);
+    const float v = fminf(fmaxf(a_v, 0.0f), p.v_max);
+    const float w = fminf(fmaxf(a_w, -p.w_max), p.w_max);
     float s0, c0;
     det_sincos(s.th, s0, c0);
     s.x = fadd(s.x, fmul(fmul(v, c0), p.dt));
@@ -62,7 +67,7 @@ __device__ __forceinline__ EnvStart integrate_env(const Step2DParams &p, int e, 
     if (th >= pi_f) th = fsub(th, two_pi_f);
     if (th < -pi_f) th = fadd(th, two_pi_f);
     s.th = th;
-    s.gstep = p.g[e];
+    s.gstep = g;
     return s;
 }
 

@@ -7,8 +7,12 @@
 //   * the env's ground truth (1 bit per voxel, 64 KiB for 128x128x32) is
 //     staged in shared memory;
 //   * one thread per beam walks the voxels with an exact fixed-point 3-D
-//     traversal: three 64-bit error terms e_xy, e_xz, e_yz compare the next
-//     face crossings of each axis pair; ties go Z first, then Y, then X;
+//     traversal: three error terms e_xy, e_xz, e_yz compare the next face
+//     crossings of each axis pair; ties go Z first, then Y, then X.  Every
+//     step adds a multiple of 2^16 to them, so the walk carries
+//     floor(e / 2^16) (same sign; a term is ax ay (t_x - t_y) scaled, both
+//     next crossings within one interval, so it stays in [-2^30, 2^30]) and
+//     the voxel index in 32 bits (the ground truth fits shared memory);
 //   * counts go to global 32-bit (hits << 16 | misses) counters plus a
 //     bitmap of touched 8-voxel chunks.  The belief walk runs warp-
 //     synchronously: the 32 lanes of a warp are 32 adjacent azimuths of one
@@ -35,17 +39,16 @@ __device__ __forceinline__ unsigned gt_bit3(const unsigned *bits, long long k) {
 
 struct Walk3 {
     int i, j, k;             // voxel
-    long long flat;
-    long long exy, exz, eyz; // next-crossing comparisons of axis pairs
+    int flat;
+    int exy, exz, eyz;       // floor(e / 2^16) of the axis pairs' crossing comparisons
     int last;                // axis of the last step (0 x, 1 y, 2 z)
 };
 
 struct Ray3 {
     int sx, sy, sz;
     long long ax, ay, az;    // |D| per axis (Q30)
-    long long Ax, Ay, Az;    // |D| * 2^16
     long long nx0, ny0, nz0;
-    long long stride_y, stride_z;
+    int stride_y, stride_z;
 };
 
 // One traversal step; returns false when it leaves the volume.
@@ -57,21 +60,21 @@ __device__ __forceinline__ bool step3(const Ray3 &r, const Env3 &sh, Walk3 &w) {
     if (a == 0) {
         w.i += r.sx;
         w.flat += r.sx;
-        w.exy += r.Ay;
-        w.exz += r.Az;
+        w.exy += (int)r.ay;
+        w.exz += (int)r.az;
         return (unsigned)w.i < (unsigned)sh.W;
     }
     if (a == 1) {
         w.j += r.sy;
         w.flat += r.sy * r.stride_y;
-        w.exy -= r.Ax;
-        w.eyz += r.Az;
+        w.exy -= (int)r.ax;
+        w.eyz += (int)r.az;
         return (unsigned)w.j < (unsigned)sh.H;
     }
     w.k += r.sz;
     w.flat += r.sz * r.stride_z;
-    w.exz -= r.Ax;
-    w.eyz -= r.Ay;
+    w.exz -= (int)r.ax;
+    w.eyz -= (int)r.ay;
     return (unsigned)w.k < (unsigned)sh.Dd;
 }
 
@@ -200,9 +203,6 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                 r.ax = Dx < 0 ? -(long long)Dx : Dx;
                 r.ay = Dy < 0 ? -(long long)Dy : Dy;
                 r.az = Dz < 0 ? -(long long)Dz : Dz;
-                r.Ax = r.ax << 16;
-                r.Ay = r.ay << 16;
-                r.Az = r.az << 16;
                 r.nx0 = Dx > 0 ? ((long long)(i0 + 1) << 16) - sh.Px
                                : (Dx < 0 ? (long long)sh.Px - ((long long)i0 << 16) : 65536);
                 r.ny0 = Dy > 0 ? ((long long)(j0 + 1) << 16) - sh.Py
@@ -210,14 +210,14 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                 r.nz0 = Dz > 0 ? ((long long)(k0 + 1) << 16) - p.Pz
                                : (Dz < 0 ? (long long)p.Pz - ((long long)k0 << 16) : 65536);
                 r.stride_y = W;
-                r.stride_z = (long long)W * H;
+                r.stride_z = W * H;
                 w0.i = i0;
                 w0.j = j0;
                 w0.k = k0;
-                w0.flat = ((long long)k0 * H + j0) * W + i0;
-                w0.exy = r.nx0 * r.ay - r.ny0 * r.ax;
-                w0.exz = r.nx0 * r.az - r.nz0 * r.ax;
-                w0.eyz = r.ny0 * r.az - r.nz0 * r.ay;
+                w0.flat = (k0 * H + j0) * W + i0;
+                w0.exy = (int)((r.nx0 * r.ay - r.ny0 * r.ax) >> 16);
+                w0.exz = (int)((r.nx0 * r.az - r.nz0 * r.ax) >> 16);
+                w0.eyz = (int)((r.ny0 * r.az - r.nz0 * r.ay) >> 16);
                 w0.last = -1;
                 if (in0) {
                     // ground truth up to the first occupied voxel
