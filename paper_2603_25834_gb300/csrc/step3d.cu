@@ -78,12 +78,6 @@ __device__ __forceinline__ bool step3(const Ray3 &r, const Env3 &sh, Walk3 &w) {
     return (unsigned)w.k < (unsigned)sh.Dd;
 }
 
-__device__ __forceinline__ void count_plain(const Step2DParams &p, const Env3 &sh, long long k,
-                                            unsigned inc) {
-    atomicAdd(&p.far_cnt[sh.map_off + k], inc);
-    atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
-}
-
 __device__ __forceinline__ long long apply_cell3(const Step2DParams &p, short &L, unsigned h,
                                                  unsigned m) {
     const int l0 = L;
@@ -266,10 +260,14 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                 dmin_m = fminf(dmin_m, z);
                 dmin_t = fminf(dmin_t, z_true);
             }
-            // belief walk, warp-synchronous: lanes in the same voxel share one atomic
+            // belief walk, warp-synchronous: lanes in the same voxel share one
+            // atomic.  The touched-chunk bit is set only by a leader that has
+            // just entered its 8-voxel chunk: the chunk of its previous voxel
+            // was marked by the leader that counted that voxel one step
+            // earlier (and a walk's first voxel always marks).
             bool active = valid && in0;
             Walk3 w = w0;
-            int s = 0;
+            int s = 0, prev_chunk = -1;
             for (;;) {
                 const unsigned act = __ballot_sync(0xffffffffu, active);
                 if (!act) break;
@@ -278,10 +276,14 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                     const bool is_hit = last && hit;
                     const unsigned peers = __match_any_sync(act, w.flat);
                     const unsigned hits = __ballot_sync(act, is_hit) & peers;
+                    const int chunk = w.flat >> 3;
                     if (lane == __ffs(peers) - 1) {
                         const unsigned nh = __popc(hits), nm = __popc(peers) - nh;
-                        count_plain(p, sh, w.flat, (nh << 16) | nm);
+                        atomicAdd(&p.far_cnt[sh.map_off + w.flat], (nh << 16) | nm);
+                        if (chunk != prev_chunk)
+                            atomicOr(&p.far_bits[(sh.map_off + w.flat) >> 8], 1u << (chunk & 31));
                     }
+                    prev_chunk = chunk;
                     ++rc;
                     ++s;
                     if (last) active = false;
