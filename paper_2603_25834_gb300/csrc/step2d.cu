@@ -246,8 +246,17 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     // truth.  This kernel is an ordinary launch (never a programmatic
     // dependent), so the last step's state is complete when it starts.
     const int itid = blockDim.x - 32;
-    EnvStart st0;
-    if (tid == itid) st0 = integrate_env(p, e, (long long)W * H);
+    __shared__ EnvSense s_hdr;
+    if (tid == itid) {
+        // the walkers need the origin and heading only; the collision cell
+        // (from the staged ground truth) waits for the barrier below
+        EnvSense h;
+        h.start = integrate_env(p, e, (long long)W * H);
+        h.Px = q16_of(h.start.x, p.res);
+        h.Py = q16_of(h.start.y, p.res);
+        det_sincos(h.start.th, h.s, h.c);
+        s_hdr = h;
+    }
     {
         // the env's ground truth, one bit per cell, into shared memory
         const int words = (int)(((long long)W * H + 31) >> 5);
@@ -256,29 +265,18 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
     }
     __syncthreads();
-    __shared__ EnvSense s_hdr;
-    if (tid == itid) {
-        EnvSense h;
-        h.start = st0;
-        h.Px = q16_of(h.start.x, p.res);
-        h.Py = q16_of(h.start.y, p.res);
-        const int ri = h.Px >> 16, rj = h.Py >> 16;
+    if (tid == itid && bundle.y == 0) {
+        // the header for the kernels after this one; the reduced fields
+        // belong to the atomics of every bundle and are left alone
+        const int ri = s_hdr.Px >> 16, rj = s_hdr.Py >> 16;
         const bool inside = (unsigned)ri < (unsigned)W && (unsigned)rj < (unsigned)H;
-        h.col_cell = !inside || gt_bit(s_gt, rj * W + ri);
-        det_sincos(h.start.th, h.s, h.c);
-        s_hdr = h;
-        if (bundle.y == 0) {
-            // the header for the kernels after this one; the reduced fields
-            // belong to the atomics of every bundle and are left alone
-            esp->start = h.start;
-            esp->Px = h.Px;
-            esp->Py = h.Py;
-            esp->col_cell = h.col_cell;
-            esp->c = h.c;
-            esp->s = h.s;
-        }
+        esp->start = s_hdr.start;
+        esp->Px = s_hdr.Px;
+        esp->Py = s_hdr.Py;
+        esp->col_cell = !inside || gt_bit(s_gt, rj * W + ri);
+        esp->c = s_hdr.c;
+        esp->s = s_hdr.s;
     }
-    __syncthreads();
     int gc = 0, uc = 0;
     float dmin_m = p.r_max, dmin_t = p.r_max;
     if (b < B) {
