@@ -994,13 +994,13 @@ cudaError_t step2d_set_smem(size_t smem) {
                                 kSenseSmemMax);
 }
 
-// Beams per sensing CTA: 128, more for larger maps so that the ground truth
-// staged per CTA stays at <= 256 bytes per thread.
+// Beams per sensing CTA: 128, 256 once the largest map's ground truth
+// would exceed 128 bytes per thread (every bundle stages its env's grid).
+// Timed: 256^2 maps 64 / 128 / 192 / 256 beams -> 62.5 / 59.5 / 66 / 66.8 us;
+// the uneven batch (maps up to 512^2) 128 / 192 / 256 -> 356 / 282 / 254 us.
 int sense_block(int gt_words_max) {
-    // 128 beams per bundle: a 360-beam scan stages its ground truth three
-    // times instead of six (measured faster than 64 and 256 at 256^2 maps)
     int t = 128;
-    while (t < 256 && 4LL * gt_words_max > 256LL * t) t *= 2;
+    while (t < 256 && 4LL * gt_words_max > 128LL * t) t *= 2;
     return t;
 }
 
