@@ -57,7 +57,7 @@ __device__ __forceinline__ void odo_factor(const double *xa, const double *xb, c
     Jb[6] = 0.0; Jb[7] = 0.0; Jb[8] = 1.0;
 }
 
-// Per-warp workspace of window_gn_warp (shared memory).
+// Per-window workspace of window_gn_half (shared memory).
 struct WgnShared {
     double x[kMaxWindow][3];     // estimates (fp64 between passes)
     double D[kMaxWindow][9];     // diagonal blocks of the normal matrix
