@@ -16,8 +16,8 @@
 //   * counts go to global 32-bit (hits << 16 | misses) counters plus a
 //     bitmap of touched 8-voxel chunks.  The belief walk runs warp-
 //     synchronously: the 32 lanes of a warp are 32 adjacent azimuths of one
-//     ring, which cross the same voxels near the sensor, so lanes in the same
-//     voxel are merged (__match_any_sync) into one atomic;
+//     ring, which cross the same voxels near the sensor, so adjacent lanes
+//     in the same voxel are merged into one atomic;
 //   * the CTA then applies the touched chunks and sums the entropy change.
 #include "aslam_internal.cuh"
 #include "env_common.cuh"
@@ -271,14 +271,23 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
             for (;;) {
                 const unsigned act = __ballot_sync(0xffffffffu, active);
                 if (!act) break;
+                // adjacent lanes (adjacent azimuths) in the same voxel form a
+                // run; the run's first lane adds the whole run in one atomic
+                const int vox = active ? w.flat : -1 - lane;          // inactive: unique
+                const int pvox = __shfl_up_sync(0xffffffffu, vox, 1);
+                const bool start = active && (lane == 0 || pvox != vox);
+                const unsigned starts = __ballot_sync(0xffffffffu, start);
+                const bool last = active && s == Ku;
+                const unsigned hits = __ballot_sync(0xffffffffu, last && hit);
                 if (active) {
-                    const bool last = s == Ku;
-                    const bool is_hit = last && hit;
-                    const unsigned peers = __match_any_sync(act, w.flat);
-                    const unsigned hits = __ballot_sync(act, is_hit) & peers;
                     const int chunk = w.flat >> 3;
-                    if (lane == __ffs(peers) - 1) {
-                        const unsigned nh = __popc(hits), nm = __popc(peers) - nh;
+                    if (start) {
+                        // the run: this lane up to the next start or inactive lane
+                        const unsigned above = lane == 31 ? 0u : ~((2u << lane) - 1u);
+                        const unsigned stop = (starts | ~act) & above;
+                        const unsigned upto = stop ? (stop & (0u - stop)) - 1u : 0xffffffffu;
+                        const unsigned run = upto & ~((1u << lane) - 1u);
+                        const unsigned nh = __popc(hits & run), nm = __popc(run) - nh;
                         atomicAdd(&p.far_cnt[sh.map_off + w.flat], (nh << 16) | nm);
                         if (chunk != prev_chunk)
                             atomicOr(&p.far_bits[(sh.map_off + w.flat) >> 8], 1u << (chunk & 31));
