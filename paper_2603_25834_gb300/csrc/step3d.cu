@@ -6,8 +6,9 @@
 // voxel world.  One persistent CTA per environment:
 //   * the env's ground truth (1 bit per voxel, 64 KiB for 128x128x32) is
 //     staged in shared memory;
-//   * one thread per beam walks the voxels with an exact fixed-point 3-D
-//     traversal: three error terms e_xy, e_xz, e_yz compare the next face
+//   * warps take groups of 32 adjacent azimuths of one ring from a block-
+//     wide counter, long rings first; one thread per beam walks the voxels
+//     with an exact fixed-point 3-D traversal: three error terms e_xy, e_xz, e_yz compare the next face
 //     crossings of each axis pair; ties go Z first, then Y, then X.  Every
 //     step adds a multiple of 2^16 to them, so the walk carries
 //     floor(e / 2^16) (same sign; a term is ax ay (t_x - t_y) scaled, both
@@ -87,13 +88,25 @@ __device__ __forceinline__ long long apply_cell3(const Step2DParams &p, short &L
     return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
 }
 
+// Range (in voxels) at which a ring's beams leave the slab between the floor
+// and the top of the volume, at most r_max.
+__device__ __forceinline__ float ring_reach(const Step2DParams &p, int Dd, int ring) {
+    const float rmax_v = p.r_max / p.res;
+    const float zs = (float)p.Pz * (1.0f / 65536.0f);
+    const float se = p.elev_cs[ring].y;
+    if (se < 0.0f) return fminf(rmax_v, zs / -se);
+    if (se > 0.0f) return fminf(rmax_v, ((float)Dd - zs) / se);
+    return rmax_v;
+}
+
 __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     unsigned *s_gt = smem;
     __shared__ Env3 sh;
     __shared__ long long r_dh[32], r_rc[32], r_gc[32];
     __shared__ float r_dm[32], r_dt[32];
-    __shared__ int s_next;
+    __shared__ int s_next, s_grp;
+    __shared__ short s_ring[256];   // rings, longest expected walk first
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -139,6 +152,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
             sh.col_cell = !inside ||
                           gt_bit3(p.gt_bits + sh.gtb_off, ((long long)sh.rk * H + sh.rj) * W + sh.ri);
             det_sincos(sh.start.th, sh.s, sh.c);
+            s_grp = 0;
             s_next = (int)atomicAdd(p.queue, 1u);
         }
         __syncthreads();
@@ -159,28 +173,46 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
             if (debug)
                 for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
         }
+        // Rings in decreasing order of the range at which they leave the
+        // slab between the floor and the top of the volume (r_max at most):
+        // the warps take the long rings first, so that the groups still in
+        // flight when the work runs out are short ones.  The order only
+        // schedules; every count is an integer sum.
+        for (int r = tid; r < p.n_rings; r += nt) {
+            const float key = ring_reach(p, sh.Dd, r);
+            int rank = 0;
+            for (int q = 0; q < p.n_rings; ++q) {
+                const float kq = ring_reach(p, sh.Dd, q);
+                rank += kq > key || (kq == key && q < r);
+            }
+            s_ring[rank] = (short)r;
+        }
         __syncthreads();
 
         // ---- beams -------------------------------------------------------------
         long long rc = 0, gc = 0;
         float dmin_m = p.r_max, dmin_t = p.r_max;
         const int W = sh.W, H = sh.H;
-        const int rounds = (sh.B + nt - 1) / nt;
-        for (int q = 0; q < rounds; ++q) {
-            // every lane runs the same number of rounds: the warp-synchronous
-            // belief walk below needs whole warps.  A warp keeps 32 adjacent
-            // azimuths, but the sector it takes rotates from round to round, so
-            // that warps facing near walls and warps facing open space even out
-            // before the CTA's barrier.
-            const int b = (q * nwarps + (warp + 5 * q) % nwarps) * 32 + lane;
-            const bool valid = b < sh.B;
+        // Work is taken a group of 32 adjacent azimuths of one ring at a time,
+        // from a block-wide counter: whole warps, as the warp-synchronous
+        // belief walk below needs, and balanced across the warps before the
+        // CTA's barrier however the walk lengths vary.
+        const int A = sh.A, gpr = (A + 31) >> 5, ngroups = p.n_rings * gpr;
+        for (;;) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&s_grp, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= ngroups) break;
+            const int ring = s_ring[g / gpr];
+            const int a = (g % gpr) * 32 + lane;
+            const bool valid = a < A;
+            const int b = ring * A + a;
             Ray3 r;
             Walk3 w0;
             bool hit = false, in0 = false;
             float z_true = p.r_max, z = p.r_max;
             int Ku = -1;
             if (valid) {
-                const int ring = b / sh.A;
                 const float2 cs = p.beam_cs[sh.ray_off + b];
                 const float2 el = p.elev_cs[ring];
                 const float hx = fsub(fmul(sh.c, cs.x), fmul(sh.s, cs.y));
