@@ -88,6 +88,17 @@ __device__ __forceinline__ long long apply_cell3(const Step2DParams &p, short &L
     return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
 }
 
+// Global reductions without a returned value (relaxed, device scope, like
+// atomicAdd / atomicOr): the walking warp never waits for the L2, even when
+// the counter's sector has to come from DRAM.  The CTA's barrier before the
+// apply phase orders them before the apply's loads.
+__device__ __forceinline__ void red_add(unsigned *a, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(unsigned *a, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
 // Range (in voxels) at which a ring's beams leave the slab between the floor
 // and the top of the volume, at most r_max.
 __device__ __forceinline__ float ring_reach(const Step2DParams &p, int Dd, int ring) {
@@ -320,9 +331,9 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                         const unsigned upto = stop ? (stop & (0u - stop)) - 1u : 0xffffffffu;
                         const unsigned run = upto & ~((1u << lane) - 1u);
                         const unsigned nh = __popc(hits & run), nm = __popc(run) - nh;
-                        atomicAdd(&p.far_cnt[sh.map_off + w.flat], (nh << 16) | nm);
+                        red_add(&p.far_cnt[sh.map_off + w.flat], (nh << 16) | nm);
                         if (chunk != prev_chunk)
-                            atomicOr(&p.far_bits[(sh.map_off + w.flat) >> 8], 1u << (chunk & 31));
+                            red_or(&p.far_bits[(sh.map_off + w.flat) >> 8], 1u << (chunk & 31));
                     }
                     prev_chunk = chunk;
                     ++rc;
