@@ -21,6 +21,17 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 
+// Global reductions without a returned value (relaxed, device scope, the
+// ordering of atomicAdd / atomicOr): the issuing warp never waits for the
+// L2, even when the counter's sector has to come from DRAM.  A later
+// barrier of the CTA orders them before its own loads of the counters.
+__device__ __forceinline__ void red_add(unsigned *a, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(unsigned *a, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
 // Maclaurin series of sin and cos truncated after x^9 / x^10: on
 // |r| <= pi/4 the first omitted term is below 2^-26 relative.
 __device__ __forceinline__ void poly_sincos(float r, float &s, float &c) {

@@ -133,7 +133,7 @@ __global__ void scan_rays_kernel(const ScanParams p) {
         long long ee = e0;
         for (int st = 0;; ++st) {
             const bool last = st == Ku;
-            atomicAdd(&p.cnt[off + (long long)j * W + i], (last && hit) ? 0x10000u : 1u);
+            red_add(&p.cnt[off + (long long)j * W + i], (last && hit) ? 0x10000u : 1u);
             if (last) break;
             if (ee < 0) { i += sx; ee += dA; } else { j += sy; ee -= dB; }
             if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) break;

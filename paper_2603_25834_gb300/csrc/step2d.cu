@@ -422,8 +422,8 @@ __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared
         atomicAdd(&s_win[q >> 2], inc << ((q & 3) << 3));
         return;
     }
-    atomicAdd(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
-    atomicOr(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
+    red_add(&p.far_cnt[sh.map_off + k], is_hit ? 0x10000u : 1u);
+    red_or(&p.far_bits[(sh.map_off + k) >> 8], 1u << ((k >> 3) & 31));
 }
 
 // Is the m-th x-crossing (m >= 1) strictly earlier than the n-th

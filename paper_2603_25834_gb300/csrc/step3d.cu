@@ -88,17 +88,6 @@ __device__ __forceinline__ long long apply_cell3(const Step2DParams &p, short &L
     return __ldg(&p.lut[l1 + p.clamp_q]) - __ldg(&p.lut[l0 + p.clamp_q]);
 }
 
-// Global reductions without a returned value (relaxed, device scope, like
-// atomicAdd / atomicOr): the walking warp never waits for the L2, even when
-// the counter's sector has to come from DRAM.  The CTA's barrier before the
-// apply phase orders them before the apply's loads.
-__device__ __forceinline__ void red_add(unsigned *a, unsigned v) {
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ void red_or(unsigned *a, unsigned v) {
-    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
-}
-
 // Range (in voxels) at which a ring's beams leave the slab between the floor
 // and the top of the volume, at most r_max.
 __device__ __forceinline__ float ring_reach(const Step2DParams &p, int Dd, int ring) {
