@@ -302,16 +302,40 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                 const int ady = (int)bm.ady, nadx = -(int)bm.adx;
                 int st = 0, kx = 0;
                 bool lastx = false;
-                for (; st < nsteps; ++st) {
-                    lastx = eh < 0;
-                    k += lastx ? bm.sx : syW;
-                    eh += lastx ? ady : nadx;
-                    kx += lastx;
-                    if (gt_bit(gt, k)) {
+                // two steps per iteration: both cells' bits are loaded
+                // together, and one branch tests them
+                for (; st + 1 < nsteps; st += 2) {
+                    const bool x1 = eh < 0;
+                    const int k1 = k + (x1 ? bm.sx : syW);
+                    const int e1 = eh + (x1 ? ady : nadx);
+                    const bool x2 = e1 < 0;
+                    const int k2 = k1 + (x2 ? bm.sx : syW);
+                    const unsigned b1 = gt_bit(gt, k1), b2 = gt_bit(gt, k2);
+                    if (b1 | b2) {
                         hit = true;
-                        ++st;
+                        if (b1) {
+                            k = k1;
+                            lastx = x1;
+                            kx += x1;
+                            st += 1;
+                        } else {
+                            k = k2;
+                            lastx = x2;
+                            kx += x1 + x2;
+                            st += 2;
+                        }
                         break;
                     }
+                    k = k2;
+                    eh = e1 + (x2 ? ady : nadx);
+                    kx += x1 + x2;
+                }
+                if (!hit && st < nsteps) {
+                    lastx = eh < 0;
+                    k += lastx ? bm.sx : syW;
+                    kx += lastx;
+                    ++st;
+                    hit = gt_bit(gt, k) != 0;
                 }
                 cells = st + 1;                 // the start cell and every step taken
                 if (hit) {
