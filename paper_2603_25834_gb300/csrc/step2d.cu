@@ -302,39 +302,56 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                 const int ady = (int)bm.ady, nadx = -(int)bm.adx;
                 int st = 0, kx = 0;
                 bool lastx = false;
-                // two steps per iteration: both cells' bits are loaded
+                // four steps per iteration: the four cells' bits are loaded
                 // together, and one branch tests them
-                for (; st + 1 < nsteps; st += 2) {
+                for (; st + 3 < nsteps; st += 4) {
                     const bool x1 = eh < 0;
                     const int k1 = k + (x1 ? bm.sx : syW);
                     const int e1 = eh + (x1 ? ady : nadx);
                     const bool x2 = e1 < 0;
                     const int k2 = k1 + (x2 ? bm.sx : syW);
+                    const int e2 = e1 + (x2 ? ady : nadx);
+                    const bool x3 = e2 < 0;
+                    const int k3 = k2 + (x3 ? bm.sx : syW);
+                    const int e3 = e2 + (x3 ? ady : nadx);
+                    const bool x4 = e3 < 0;
+                    const int k4 = k3 + (x4 ? bm.sx : syW);
                     const unsigned b1 = gt_bit(gt, k1), b2 = gt_bit(gt, k2);
-                    if (b1 | b2) {
+                    const unsigned b3 = gt_bit(gt, k3), b4 = gt_bit(gt, k4);
+                    if (b1 | b2 | b3 | b4) {
                         hit = true;
                         if (b1) {
                             k = k1;
                             lastx = x1;
                             kx += x1;
                             st += 1;
-                        } else {
+                        } else if (b2) {
                             k = k2;
                             lastx = x2;
                             kx += x1 + x2;
                             st += 2;
+                        } else if (b3) {
+                            k = k3;
+                            lastx = x3;
+                            kx += x1 + x2 + x3;
+                            st += 3;
+                        } else {
+                            k = k4;
+                            lastx = x4;
+                            kx += x1 + x2 + x3 + x4;
+                            st += 4;
                         }
                         break;
                     }
-                    k = k2;
-                    eh = e1 + (x2 ? ady : nadx);
-                    kx += x1 + x2;
+                    k = k4;
+                    eh = e3 + (x4 ? ady : nadx);
+                    kx += x1 + x2 + x3 + x4;
                 }
-                if (!hit && st < nsteps) {
+                for (; !hit && st < nsteps; ++st) {
                     lastx = eh < 0;
                     k += lastx ? bm.sx : syW;
+                    eh += lastx ? ady : nadx;
                     kx += lastx;
-                    ++st;
                     hit = gt_bit(gt, k) != 0;
                 }
                 cells = st + 1;                 // the start cell and every step taken
