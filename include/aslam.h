@@ -501,9 +501,11 @@ aslam_status aslam_gn_correct(const aslam_soft_config *cfg, const float *d_logod
  *   d_ranges   device float [n_envs, B] measured ranges (output).
  * Limits: n_envs <= 2048, total cells <= 4194304, B <= 1024; larger requests
  * return ASLAM_ERR_INVALID_ARG.  The first call on a device looks up the
- * array's device address with that device current: make it before any
- * stream capture.  All calls share the array (each clears what it uses
- * first), so calls that overlap on the GPU race: serialise them.
+ * array's device address with that device current.  Every call copies its
+ * small tables from host memory, so a call made while `stream` is being
+ * captured into a CUDA graph returns ASLAM_ERR_UNSUPPORTED.  All calls share
+ * the array (each clears what it uses first), so calls that overlap on the
+ * GPU race: serialise them.
  */
 aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const uint8_t *d_gt,
                                        const int64_t *h_gt_off, const float *d_pose,

@@ -457,6 +457,26 @@ def scan_update_noalloc(inputs, gt, pose, step, belief, ranges, stream=None, **c
     h = np.ascontiguousarray(inputs.map_h, dtype=np.int32)
     b = np.ascontiguousarray(inputs.n_beams, dtype=np.int32)
     off = np.ascontiguousarray(inputs.map_off, dtype=np.int64)
+    # The C side cannot see device buffer sizes: every tensor is checked here
+    # against the sizes the kernels will index, so a wrong buffer is an
+    # exception instead of an out-of-bounds access.
+    cells = int(off[-1])
+    B = int(b[0]) if E > 0 else 0
+    want = [("gt", gt, torch.uint8, cells), ("belief", belief, torch.int16, cells),
+            ("pose", pose, torch.float32, 3 * E), ("step", step, torch.int32, E),
+            ("ranges", ranges, torch.float32, E * B)]
+    dev = gt.device if isinstance(gt, torch.Tensor) else None
+    for name, t, dt, n in want:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise AslamError(1, "%s must be a CUDA tensor" % name)
+        if t.dtype != dt:
+            raise AslamError(1, "%s must be %s, got %s" % (name, dt, t.dtype))
+        if t.numel() != n:
+            raise AslamError(1, "%s must have %d elements, got %d" % (name, n, t.numel()))
+        if not t.is_contiguous():
+            raise AslamError(1, "%s must be contiguous" % name)
+        if t.device != dev:
+            raise AslamError(1, "every tensor must be on %s (%s is on %s)" % (dev, name, t.device))
     c.n_envs = E
     c.res_m = float(inputs.res)
     c.h_map_w = w.ctypes.data_as(P)
@@ -464,8 +484,10 @@ def scan_update_noalloc(inputs, gt, pose, step, belief, ranges, stream=None, **c
     c.h_n_beams = b.ctypes.data_as(P)
     for k, v in cfg.items():
         setattr(c, k, float(v) if k in _FLOAT_KEYS else int(v))
-    _check(lib.aslam_scan_update_noalloc(C.byref(c), _dptr(gt), off.ctypes.data_as(P), _dptr(pose),
-                                         _dptr(step), _dptr(belief), _dptr(ranges), _stream(stream)))
+    with torch.cuda.device(dev):
+        _check(lib.aslam_scan_update_noalloc(C.byref(c), _dptr(gt), off.ctypes.data_as(P),
+                                             _dptr(pose), _dptr(step), _dptr(belief),
+                                             _dptr(ranges), _stream(stream)))
 
 
 def fixed_lag_gn(x, odo, meas, meas_info, prior, prior_info, iters=3,

@@ -189,7 +189,7 @@ struct Step2DParams {
     float *csm_pose, *csm_match;                      // [E, 3]
     long long *csm_scores;                            // [E, 3]
     float *slam_upd_w;           // [E] this step's scan weight (u_mode 2)
-    const float *upd_w;          // per-env update weight, or null (unweighted)                // global index of env 0 in the noise counter
+    const float *upd_w;          // per-env update weight, or null (unweighted)
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *R8, *Dd;
     int *order;                  // work order of the update queue (2-D: costliest first each step)

@@ -19,9 +19,12 @@
 //     it needs first, but calls that overlap on the GPU (different streams,
 //     or host threads racing) corrupt each other -- serialise them;
 //   * the first call on each device looks the array's device address up
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture.
+//     (cudaGetSymbolAddress) with that device current;
+//   * every call copies its tables from host memory (some of it on the
+//     call's own stack) with cudaMemcpyAsync, so a call made while `stream`
+//     is being captured is rejected with ASLAM_ERR_UNSUPPORTED.
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -217,11 +220,25 @@ extern "C" aslam_status aslam_scan_update_noalloc(const aslam_config *cfg, const
         return na_fail(ASLAM_ERR_INVALID_ARG, "res_m / r_max_m out of range");
     if (cfg->l_clamp_q < 1 || cfg->l_clamp_q > 32767 || !(cfg->noise_sigma_m >= 0.0f))
         return na_fail(ASLAM_ERR_INVALID_ARG, "l_clamp_q or noise_sigma_m out of range");
+    // hits * l_hit_q + misses * l_miss_q stays inside a 32-bit int for up to
+    // 2^15 beams per cell only with increments of at most 16 bits
+    if (std::abs(cfg->l_hit_q) > 32767 || std::abs(cfg->l_miss_q) > 32767)
+        return na_fail(ASLAM_ERR_INVALID_ARG, "|l_hit_q|, |l_miss_q| must be <= 32767");
+    if (cfg->range_decimals < -1 || cfg->range_decimals > 6 || !(cfg->r_min_m >= 0.0f) ||
+        !(cfg->r_min_m <= cfg->r_max_m))
+        return na_fail(ASLAM_ERR_INVALID_ARG, "range_decimals or r_min_m out of range");
 
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t qe = cudaStreamIsCapturing(s, &cap);
+    if (qe != cudaSuccess)
+        return na_fail(ASLAM_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(qe));
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(ASLAM_ERR_UNSUPPORTED,
+                       "stream is being captured: this call copies host tables and cannot be captured");
     unsigned char *base = nullptr;
     aslam_status st = scratch_ptr(&base);
     if (st != ASLAM_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
 
     // Beam directions, as the batched step builds them (host fp64 -> fp32).
     float2 tab[ASLAM_MAX_BEAMS];
