@@ -7,11 +7,19 @@ noise sigma = 0.01 m, int16 log-odds, 1000 steps of random (v, w) actions
 and a synthetic uncertainty signal U_t (composite reward, Eq. 7-17).
 
 A "step" is one call of the whole path (action integration, raycast, log-odds
-update, reward, observation) for all envs: three kernel launches (integrate,
-sense, update; one for the 3-D variant).  Inputs (all steps' actions and U_t)
-are resident in HBM before timing; L2 is flushed (256 MiB write) between
-timed steps, each step is timed with its own CUDA event pair on the
-launching stream, and the library's own events time each kernel.
+update, reward, observation) for all envs: two kernel launches (sensing,
+which also integrates the actions, then the persistent update; one for the
+3-D variant).  Inputs (all steps' actions and U_t) are resident in HBM
+before timing; L2 is flushed (256 MiB write) between timed steps, each step
+is timed with its own CUDA event pair on the launching stream, and the
+library's own events time each kernel in a separate pass.
+
+The default line also carries `batched_4096`: the batched uneven form
+(4096 envs, map sides {128,256,384,512}, beams {180,360,720}), autotuned,
+timed both as plain launches and as replays of the captured CUDA graph, with
+its step's algorithmic bytes against the measured HBM peak; and
+`cpu_baseline`: the oracle on one thread and with a step's envs spread over
+every host core.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -130,21 +138,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(inputs, n_envs, steps, seed_actions=2026):
-    """Env-steps/s of the CPU oracle on the first n_envs envs (single thread)."""
+def oracle_rate(inputs, n_envs, steps, threads=1, seed_actions=2026):
+    """Env-steps/s of the CPU oracle on the first n_envs envs, its step's
+    independent envs spread over `threads` host threads (OpenMP)."""
     import oracle
     from paper_2603_25834_gb300 import synth
-    sub = synth.subset(inputs, list(range(n_envs)))
-    ob = oracle.OracleBatch2D(sub, r_max=12.0, sigma=0.01)
-    acts = synth.random_actions(steps, n_envs, seed_actions)
-    u = synth.random_uncertainty(steps, n_envs, seed_actions + 1)
-    t0 = time.perf_counter()
-    rc = 0
-    for s in range(steps):
-        o = ob.step(acts[s], u[s])
-        rc += int(o["ray_cells"].sum())
-    dt = time.perf_counter() - t0
-    return n_envs * steps / dt, rc / dt, dt
+    used = oracle.set_threads(threads)
+    try:
+        sub = synth.subset(inputs, list(range(n_envs)))
+        ob = oracle.OracleBatch2D(sub, r_max=12.0, sigma=0.01)
+        acts = synth.random_actions(steps, n_envs, seed_actions)
+        u = synth.random_uncertainty(steps, n_envs, seed_actions + 1)
+        t0 = time.perf_counter()
+        rc = 0
+        for s in range(steps):
+            o = ob.step(acts[s], u[s])
+            rc += int(o["ray_cells"].sum())
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return n_envs * steps / dt, rc / dt, dt, used
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
@@ -152,10 +172,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2603_25834_gb300 import synth
-    # bounded sample: a few envs of the same workload per step
-    n_sample = 4
-    inp = synth.paper_scale(E=n_sample)
     import oracle
+    # bounded sample of the same workload: four envs per host core per step,
+    # the step's envs spread over every core (OpenMP)
+    cores = host_cores()
+    used = oracle.set_threads(cores)
+    n_sample = 4 * used
+    inp = synth.paper_scale(E=n_sample)
     ob = oracle.OracleBatch2D(inp, r_max=12.0, sigma=0.01)
     total = args.warmup + args.steps
     acts = synth.random_actions(total, n_sample, 2026)
@@ -167,6 +190,7 @@ def run_reference(args):
     for s in range(args.warmup, total):
         rc += int(ob.step(acts[s], u[s])["ray_cells"].sum())
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     val = n_sample * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
@@ -174,13 +198,171 @@ def run_reference(args):
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16+f32", "data": "synthetic", "config": WORKLOAD,
         "ray_cells_per_s": rc / dt,
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d of the 750 envs per step, %d steps, single thread"
-                                   % (n_sample, args.steps)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": "%d of the 750 envs per step (4 per core), %d steps, the envs "
+                                   "of a step spread over %d threads" % (n_sample, args.steps, used)},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def timed_steps(batch, acts, uu, W, K, reward, obs, flush, stream, dev, counters=None,
+                clocks=None):
+    """K steps (after W untimed ones), each timed with its own CUDA event pair
+    on the launching stream, L2 flushed before each; returns the summed ms.
+    `counters` (ray_cells, gt_cells device views and accumulators) sums the
+    exact cell counts of every timed step on the device."""
+    for s in range(W):
+        batch.step_fused(acts[s], uu[s], reward, obs)
+    starts = [torch_event() for _ in range(K)]
+    ends = [torch_event() for _ in range(K)]
+    torch_sync(dev)
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.1)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        batch.step_fused(acts[W + k], uu[W + k], reward, obs)
+        ends[k].record(stream)
+        if counters is not None:
+            rc, gc, rc_acc, gc_acc = counters
+            rc_acc += rc.sum()
+            gc_acc += gc.sum()
+    torch_sync(dev)
+    clk = clocks.stop() if clocks is not None else None
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), clk
+
+
+def graph_steps(batch, acts, uu, W, n, reward, obs, flush, dev):
+    """Capture one step into a CUDA graph and time n replays (inputs copied
+    into the captured buffers before each, outside the timed region)."""
+    import torch
+    gstream = torch.cuda.Stream(dev)
+    abuf = acts[0].clone()
+    ubuf = uu[0].clone()
+    with torch.cuda.stream(gstream):
+        batch.capture_graph(abuf, ubuf, reward, obs, stream=gstream)
+    torch_sync(dev)
+    tot = 0.0
+    with torch.cuda.stream(gstream):
+        for k in range(n):
+            abuf.copy_(acts[W + k])
+            ubuf.copy_(uu[W + k])
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch_event(), torch_event()
+            e0.record(gstream)
+            batch.graph_step(stream=gstream)
+            e1.record(gstream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+    torch_sync(dev)
+    return tot / n
+
+
+def kernel_split(batch, acts, uu, W, n, reward, obs, flush, dev):
+    """Per-kernel device time from the library's own events (a separate pass:
+    the events between kernels serialise them)."""
+    batch.profile_begin(n)
+    for k in range(n):
+        flush.fill_(k & 0xFF)
+        batch.step_fused(acts[W + k], uu[W + k], reward, obs)
+    torch_sync(dev)
+    return batch.profile_end()
+
+
+def torch_event():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def torch_sync(dev):
+    import torch
+    torch.cuda.synchronize(dev)
+
+
+def step_kernel_bytes(E, b_max, Bsum, rc_step, gt_step):
+    """Algorithmic bytes of one 2-D step per kernel and in total (per-unit
+    figures x units of one launch): each cell an update walk visits is an
+    int16 read + write (4 B); each ground-truth cell a sensing walk visits is
+    1 bit of the packed world (1/8 B); per beam a 4 B range and a 4 B walk
+    code written by the sensing and read by the update; per env the
+    observation row (b_max + 2) x 4 B and 24 B of pose, action and reward,
+    and 96 B of integration state and the start-of-step header."""
+    io_env = E * (b_max + 2) * 4 + E * 24
+    kb = {"sense2d_kernel": gt_step / 8 + Bsum * 8 + E * 96,
+          "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
+    step = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
+    return kb, step
+
+
+def batched_record(args, world, rank, dev, peak):
+    """The batched uneven form at its full size (4096 envs per GPU, map sides
+    {128, 256, 384, 512}, beams {180, 360, 720}): the persistent update launch
+    and the captured CUDA graph of the whole step, autotuned, each timed over
+    K steps; the step's ray-cell bytes against the HBM peak."""
+    import torch
+    from paper_2603_25834_gb300 import aslam, shard, synth
+    E_all = 4096 * world
+    side, nb = synth.uneven_shapes(E_all)
+    lo, hi = shard.env_range(shard.env_cost(side, side, nb), world, rank)
+    inp = synth.uneven(E=E_all, envs=range(lo, hi))
+    E = hi - lo
+    batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE, r_max_m=12.0,
+                          noise_sigma_m=0.01, env_base=lo)
+    tuned = batch.autotune()
+    K, W = args.steps, args.warmup
+    acts = torch.from_numpy(synth.random_actions(K + W, E_all, 7)[:, lo:hi].copy()).to(dev)
+    uu = torch.from_numpy(synth.random_uncertainty(K + W, E_all, 8)[:, lo:hi].copy()).to(dev)
+    reward = torch.empty(E, device=dev)
+    obs = torch.empty(E, batch.b_max + 2, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = batch.state()
+    rc_acc = torch.zeros((), dtype=torch.int64, device=dev)
+    gc_acc = torch.zeros((), dtype=torch.int64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    plain_ms, _ = timed_steps(batch, acts, uu, W, K, reward, obs, flush, stream, dev,
+                              counters=(st["ray_cells"], st["gt_cells"], rc_acc, gc_acc))
+    plain_ms = shard.max_over_ranks(plain_ms, dev) / K
+    rc_step = int(rc_acc.item()) / K
+    gt_step = int(gc_acc.item()) / K
+    Kg = min(K, 200)
+    g_ms = shard.max_over_ranks(graph_steps(batch, acts, uu, W, Kg, reward, obs, flush, dev), dev)
+    kms, ns = kernel_split(batch, acts, uu, W, min(K, 100), reward, obs, flush, dev)
+    kb, step_b = step_kernel_bytes(E, batch.b_max, int(batch.ray_off[-1]), rc_step, gt_step)
+    batch.sync_status()
+    rc_all = shard.sum_over_ranks(rc_step, dev)
+    step_all = shard.sum_over_ranks(step_b, dev)
+    kernels = {k: {"ms_per_launch": v / ns,
+                   "achieved_gbs": kb[k] / (v / ns / 1e3) / 1e9 if k in kb else None,
+                   "frac": kb[k] / (v / ns / 1e3) / 1e9 / peak if k in kb else None}
+               for k, v in kms.items()}
+    del batch
+    return {
+        "workload": "uneven: %d envs per GPU, sides {128,256,384,512} @0.05 m, beams "
+                    "{180,360,720}, 12 m, sigma 0.01 m, composite reward" % E,
+        "envs": E_all, "mean_beams": float(nb.mean()),
+        "mean_cells": float((side.astype(np.int64) ** 2).mean()),
+        "autotuned": {"threads_per_cta": tuned[0], "window_cells": tuned[1]},
+        "ray_cells_per_step": rc_all, "bytes_per_step": step_all,
+        "graph": {"ms_per_step": g_ms, "value": E_all / (g_ms / 1e3), "unit": UNIT,
+                  "ray_cells_per_s": rc_all / (g_ms / 1e3),
+                  "achieved_gbs": step_all / (g_ms / 1e3) / 1e9,
+                  "frac": step_all / (g_ms / 1e3) / 1e9 / peak, "steps": Kg},
+        "plain": {"ms_per_step": plain_ms, "value": E_all / (plain_ms / 1e3), "unit": UNIT,
+                  "ray_cells_per_s": rc_all / (plain_ms / 1e3),
+                  "achieved_gbs": step_all / (plain_ms / 1e3) / 1e9,
+                  "frac": step_all / (plain_ms / 1e3) / 1e9 / peak, "steps": K},
+        "kernels": kernels,
+        "frac_target": 0.5,
+        "note": "frac = the step's algorithmic bytes (4 B per ray cell, 1/8 B per ground-truth "
+                "cell, ranges, observation, pose/action/reward) / step time / measured hbm_gbs",
+        "l2": "flushed (256 MiB write) between timed steps",
+    }
 
 
 def bench_diff(args):
@@ -330,6 +512,8 @@ def main():
     ap.add_argument("--envs", type=int, default=750)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 4096-env batched record of the default workload")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default/tuned)")
     ap.add_argument("--window", type=int, default=0, help="shared window side (0: default/tuned)")
@@ -438,66 +622,23 @@ def main():
     rc_acc = torch.zeros((), dtype=torch.int64, device=dev)
     gc_acc = torch.zeros((), dtype=torch.int64, device=dev)
     st = batch.state()
-    for s in range(W):
-        batch.step_fused(acts[s], uu[s], reward, obs)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     clocks = ClockSampler(dev.index)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    time.sleep(0.1)
-    for k in range(K):
-        flush.fill_(k & 0xFF)
-        starts[k].record(stream)
-        batch.step_fused(acts[W + k], uu[W + k], reward, obs)
-        ends[k].record(stream)
-        rc_acc += st["ray_cells"].sum()
-        gc_acc += st["gt_cells"].sum()
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
+    total_ms, clk = timed_steps(batch, acts, uu, W, K, reward, obs, flush, stream, dev,
+                                counters=(st["ray_cells"], st["gt_cells"], rc_acc, gc_acc),
+                                clocks=clocks)
     if world > 1:
         dist.barrier()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    # Per-kernel split from a separate pass: the library records CUDA events
-    # between its kernels on the launching stream, which serialises them
-    # (no programmatic dependent launch), so the timed loop above runs
-    # without them.
-    Kp = min(K, 100)
-    batch.profile_begin(Kp)
-    for k in range(Kp):
-        flush.fill_(k & 0xFF)
-        batch.step_fused(acts[W + k], uu[W + k], reward, obs)
-    torch.cuda.synchronize(dev)
-    kernel_ms, prof_steps = batch.profile_end()
+    kernel_ms, prof_steps = kernel_split(batch, acts, uu, W, min(K, 100), reward, obs, flush, dev)
     ray_cells = int(rc_acc.item())
     gt_cells = int(gc_acc.item())
     total_ms_max = shard.max_over_ranks(total_ms, dev)
     batch.sync_status()
 
     # ---- graph-captured replay of the same step (reported beside) ----
-    gstream = torch.cuda.Stream(dev)
-    abuf = acts[0].clone()
-    ubuf = uu[0].clone()
-    with torch.cuda.stream(gstream):
-        batch.capture_graph(abuf, ubuf, reward, obs, stream=gstream)
-    torch.cuda.synchronize(dev)
     gk = min(K, 200)
-    g_ms = 0.0
-    with torch.cuda.stream(gstream):
-        for k in range(gk):
-            abuf.copy_(acts[W + k])
-            ubuf.copy_(uu[W + k])
-            flush.fill_(k & 0xFF)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(gstream)
-            batch.graph_step(stream=gstream)
-            e1.record(gstream)
-            e1.synchronize()
-            g_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize(dev)
+    g_ms = graph_steps(batch, acts, uu, W, gk, reward, obs, flush, dev)
 
     # ---- end to end through the public API with host buffers ----
     K2 = min(args.e2e_steps, K)
@@ -511,8 +652,7 @@ def main():
     e2e_ms = 0.0
     for k in range(K2):
         flush.fill_(k & 0xFF)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = torch_event(), torch_event()
         e0.record(stream)
         # the C-ABI call with host buffers: copies in, step, copies out
         batch.step_host(h_acts[k], h_u[k], h_rew[k], h_obs[k], stream=stream)
@@ -523,6 +663,14 @@ def main():
     h2d = shard.sum_over_ranks(E * 2 * 4 + E * 4, dev)
     d2h = shard.sum_over_ranks(E * 4 + E * (batch.b_max + 2) * 4, dev)
     ray_cells_all = shard.sum_over_ranks(ray_cells, dev)
+    b_max, Bsum, n_cells = batch.b_max, int(batch.ray_off[-1]), int(batch.map_off[-1])
+    del batch
+    peak, peak_kind = measured_peaks()
+
+    # ---- the batched uneven form at 4096 envs per GPU, beside the headline ----
+    batched = None
+    if args.workload == "paper_scale" and not args.no_batched and args.u_mode == "caller":
+        batched = batched_record(args, world, rank, dev, peak)
 
     if rank != 0:
         if world > 1:
@@ -531,28 +679,17 @@ def main():
 
     value = E_all * K / (total_ms_max / 1e3)
     ms_step = total_ms_max / K
-    # Algorithmic bytes per launch (per-unit figures x units of one launch):
-    # each cell an update walk visits is an int16 read + write (4 B); each
-    # ground-truth cell a sensing walk visits is 1 bit of the packed world
-    # (1/8 B); per beam a 4 B range and a 4 B walk code written by the
-    # sensing and read by the update; per env the observation row
-    # (b_max + 2) x 4 B and 24 B of pose, action and reward.
-    Bsum = int(batch.ray_off[-1])
     rc_step, gt_step = ray_cells / K, gt_cells / K
-    io_env = E * (batch.b_max + 2) * 4 + E * 24
     dims = "3d" if args.workload == "3d" else "2d"
     if dims == "3d":
+        io_env = E * (b_max + 2) * 4 + E * 24
         kbytes = {"step3d_kernel": rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env}
+        step_bytes = kbytes["step3d_kernel"]
     else:
-        # the sensing kernel also integrates each env's action (state in
-        # and the start-of-step header out: 96 B per env)
-        kbytes = {"sense2d_kernel": gt_step / 8 + Bsum * 8 + E * 96,
-                  "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
+        kbytes, step_bytes = step_kernel_bytes(E, b_max, Bsum, rc_step, gt_step)
         if args.u_mode == "scanmatch":
             # the belief read once per env, the covariance read and written, U written
-            kbytes["uq2d_kernel"] = 2 * int(batch.map_off[-1]) + E * (96 + 4)
-    step_bytes = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
-    peak, peak_kind = measured_peaks()
+            kbytes["uq2d_kernel"] = 2 * n_cells + E * (96 + 4)
     kern = max((k for k in kernel_ms if k in kbytes), key=kernel_ms.get)
     k_ms = kernel_ms[kern] / prof_steps
     achieved = kbytes[kern] / (k_ms / 1e3) / 1e9
@@ -570,8 +707,8 @@ def main():
         if tr.get("kernel_hash") == kernel_hash(dims) and tr.get("envs") == E:
             traffic = tr.get("dram_bytes_per_launch")
             if tr.get("warp_inst_per_launch"):
-                # the kernel is issue-bound: its warp instructions (ncu) over the
-                # live launch time, against one instruction per scheduler per clock
+                # the kernel's warp instructions (ncu) over the live launch
+                # time, against one instruction per scheduler per clock
                 n_inst = float(tr["warp_inst_per_launch"])
                 mhz = (clk or {}).get("sm_max_mhz") or 2070.0
                 ipeak = 152 * 4 * mhz * 1e6
@@ -581,11 +718,21 @@ def main():
                          "peak_kind": "152 SMs x 4 schedulers x max SM clock"}
     cpu = None
     if not args.no_cpu_baseline and args.workload == "paper_scale":
+        # the oracle on a bounded sample of the same workload: one thread, and
+        # the step's envs spread over every host core (OpenMP)
         n_s, steps_s = 48, 60
-        rate, rcs, dt = oracle_rate(inp, n_s, steps_s)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d of the %d envs x %d steps (%.1f s), single thread; "
-                         "oracle ray-cells/s %.3g" % (n_s, E, steps_s, dt, rcs)}
+        rate1, rcs1, dt1, _ = oracle_rate(inp, n_s, steps_s, threads=1)
+        cores = host_cores()
+        n_m, steps_m = min(E, 16 * cores), 30
+        rate_m, rcs_m, dt_m, used = oracle_rate(inp, n_m, steps_m, threads=cores)
+        cpu = {"value": rate_m, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": "first %d of the %d envs x %d steps (%.1f s), the envs of a step spread "
+                         "over %d threads; oracle ray-cells/s %.3g" % (n_m, E, steps_m, dt_m, used,
+                                                                       rcs_m),
+               "nproc": cores,
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": "first %d envs x %d steps (%.1f s); oracle ray-cells/s "
+                                           "%.3g" % (n_s, steps_s, dt1, rcs1)}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -606,11 +753,12 @@ def main():
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved": step_bytes / (ms_step / 1e3) / 1e9,
                           "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak},
+        "batched_4096": batched,
         "cpu_baseline": cpu,
         "e2e": {"value": E_all * K2 / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "graph": {"value": E_all * gk / (g_ms / 1e3), "unit": UNIT, "steps": gk,
-                  "ms_per_step": g_ms / gk},
+                  "ms_per_step": g_ms},
         "gpu_launches": K * len(kernel_ms),
         "clocks": clk,
     }

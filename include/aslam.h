@@ -50,7 +50,7 @@ typedef enum {
     ASLAM_ERR_INVALID_ARG = 1,   /* a size, pointer or value is out of range */
     ASLAM_ERR_CUDA = 2,          /* a CUDA runtime call failed */
     ASLAM_ERR_WORKSPACE = 3,     /* workspace missing, misaligned or too small */
-    ASLAM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    ASLAM_ERR_TIMEOUT = 4,       /* reserved: no kernel of this build waits on another */
     ASLAM_ERR_STATE = 5,         /* call not valid in the batch's current state */
     ASLAM_ERR_UNSUPPORTED = 6,   /* valid request this build does not support */
     ASLAM_ERR_DEVICE = 7         /* a device-side check failed (sticky error word) */
@@ -58,7 +58,12 @@ typedef enum {
 
 /* Config flags. */
 #define ASLAM_FLAG_DEBUG   0x1   /* keep per-beam true ranges/hit flags and per-cell counts */
-#define ASLAM_FLAG_CHECKS  0x2   /* extra device-side consistency checks */
+/* Device-side consistency checks: every grid index of the 2-D sensing and
+ * update walks is checked before the access (a failed check skips it), and
+ * non-finite actions or U_t are reported.  A failed check sets the batch's
+ * sticky error word (aslam_sync_status -> ASLAM_ERR_DEVICE); no kernel traps.
+ * Results are unchanged when every check passes; the checked walks are slower. */
+#define ASLAM_FLAG_CHECKS  0x2
 
 /* Reward selection (aslam_reward). */
 #define ASLAM_REWARD_ENTROPY   0  /* H_{t-1} - H_t of the robot's map, nats */
@@ -272,8 +277,9 @@ aslam_status aslam_reset(aslam_batch *b, const uint8_t *d_mask, void *stream);
 /* Borrowed device pointers to the batch state (host call, no sync). */
 aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *out);
 
-/* Synchronise `stream` and return ASLAM_ERR_DEVICE / ASLAM_ERR_TIMEOUT if a
- * device-side check has fired since create (the word stays set). */
+/* Synchronise `stream` and return ASLAM_ERR_DEVICE if a device-side check
+ * has fired since create (ASLAM_FLAG_CHECKS, or a singular fixed-lag window
+ * of ASLAM_U_FIXEDLAG); the word stays set. */
 aslam_status aslam_sync_status(aslam_batch *b, void *stream);
 
 /*

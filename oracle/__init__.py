@@ -39,9 +39,23 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(out) >= newest:
             return out
     tmp = out + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"])
+    # OpenMP only spreads orc_step2d's independent envs over threads (the
+    # all-cores CPU baseline); without it the same code runs serially
+    r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", *srcs, "-o", tmp, "-lm"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.check_call(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"])
     os.replace(tmp, out)
     return out
+
+
+def set_threads(n: int) -> int:
+    """Threads orc_step2d spreads its envs over; returns the count in effect
+    (1 when the oracle was built without OpenMP)."""
+    L = lib()
+    n = max(1, int(n)) if L.orc_openmp() else 1
+    L.orc_set_threads(n)
+    return n
 
 
 def lib():
@@ -139,6 +153,8 @@ def _declare(L):
     L.orc_philox4x32_10.argtypes = [P, P, P]
     L.orc_gauss.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
     L.orc_gauss.restype = C.c_float
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_openmp.restype = C.c_int
     L.orc_walk2d.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                              C.c_int32, C.c_int32, P, P, P, C.c_int, C.POINTER(C.c_int)]
     L.orc_walk2d.restype = C.c_int

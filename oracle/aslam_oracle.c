@@ -643,11 +643,37 @@ static double orc_slam_backbone(const orc_cfg *cfg, orc_state *st, int e, float 
     return cbrt(orc_det3(cov)) / scale;
 }
 
+/* Threads of orc_step2d's loop over environments (1 unless the CPU
+ * baseline asks for more; built without OpenMP the loop is serial).  The
+ * environments of a step are independent, so the thread count changes no
+ * result. */
+static int orc_threads = 1;
+
+void orc_set_threads(int n)
+{
+    orc_threads = n < 1 ? 1 : n;
+}
+
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const float *u_in,
                orc_out *out)
 {
     const float pi_f = (float)3.14159265358979323846;
     const float two_pi_f = (float)(2.0 * 3.14159265358979323846);
+    for (int e = 0; e < cfg->n_envs; ++e)
+        if (cfg->n_beams[e] > 4096)
+            return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_threads)
+#endif
     for (int e = 0; e < cfg->n_envs; ++e) {
         const int32_t W = cfg->map_w[e], H = cfg->map_h[e], B = cfg->n_beams[e];
         const int64_t off = cfg->map_off[e], ncell = (int64_t)W * H;
@@ -678,8 +704,6 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
 
         /* Sensing and per-step hit/miss counts. */
         float cb_tab[4096], sb_tab[4096];
-        if (B > 4096)
-            return -1;
         orc_beam_dirs(B, cfg->fov, cb_tab, sb_tab);
         float s1, c1;
         orc_sincosf(th, &s1, &c1);

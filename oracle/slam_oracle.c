@@ -46,7 +46,7 @@ void orc_csm(const int16_t *belief, int32_t W, int32_t H, float res, float r_max
     orc_beam_dirs(B, fov, cb, sb);
     const int side = 2 * n + 1, nk = 2 * m + 1;
     int64_t best = -1, best_q = 0;
-    static int64_t score[17 * 17 * 17];
+    int64_t score[17 * 17 * 17];
     int nret = 0;
     for (int b = 0; b < B; ++b)
         if (z[b] < r_max)

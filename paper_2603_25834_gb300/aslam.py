@@ -21,7 +21,7 @@ P = C.c_void_p
 
 ASLAM_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace error",
-          4: "device wait timed out", 5: "invalid state", 6: "unsupported",
+          4: "reserved", 5: "invalid state", 6: "unsupported",
           7: "device-side check failed"}
 FLAG_DEBUG = 0x1
 FLAG_CHECKS = 0x2

@@ -105,6 +105,23 @@ bool validate(const aslam_config *c, std::string *msg) {
         if (c->dims == 2 && (long long)c->h_map_w[e] * c->h_map_h[e] > 1600LL * 1024)
             return fail("2-D map larger than 1638400 cells");
     }
+    {
+        // every real-valued field must be finite (NaN fails every comparison
+        // below, but +-Inf would pass the sign checks)
+        const double vals[] = {c->res_m, c->r_max_m, c->fov_rad, c->noise_sigma_m, c->dt_s,
+                               c->v_max, c->w_max, c->d_crash, c->d_full, c->visit_cell_m,
+                               c->logodds_scale, c->lam_col, c->lam_explore, c->lam_abs,
+                               c->lam_delta, c->kappa, c->u_hi, c->r_min_m, c->sensor_z_m,
+                               c->elev_min_rad, c->elev_max_rad, c->uq_step_m,
+                               c->uq_range_sigma_m, c->uq_u_scale, c->csm_dth_rad,
+                               c->uq_odo_sigma[0], c->uq_odo_sigma[1], c->uq_odo_sigma[2],
+                               c->uq_prior_sigma[0], c->uq_prior_sigma[1], c->uq_prior_sigma[2],
+                               c->slam_meas_info[0], c->slam_meas_info[1], c->slam_meas_info[2],
+                               c->slam_prior_info[0], c->slam_prior_info[1],
+                               c->slam_prior_info[2]};
+        for (double v : vals)
+            if (!std::isfinite(v)) return fail("a real-valued config field is NaN or infinite");
+    }
     if (!(c->res_m > 0.0f) || !(c->r_max_m > 0.0f)) return fail("res_m and r_max_m must be > 0");
     if ((double)c->r_max_m / c->res_m > 16384.0) return fail("r_max_m / res_m must be <= 16384 cells");
     if (!(c->dt_s >= 0.0f) || !(c->v_max >= 0.0f) || !(c->w_max >= 0.0f))
@@ -924,7 +941,6 @@ aslam_status aslam_sync_status(aslam_batch *b, void *stream) {
     unsigned h = 0;
     CK(cudaMemcpyAsync(&h, b->p.err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status read");
     CK(cudaStreamSynchronize((cudaStream_t)stream), "status synchronize");
-    if (h & kErrTimeout) return fail_b(b, ASLAM_ERR_TIMEOUT, "a bounded device wait gave up");
     if (h & kErrChecks) return fail_b(b, ASLAM_ERR_DEVICE, "a device-side check failed");
     return ASLAM_OK;
 }
@@ -1246,7 +1262,7 @@ const char *aslam_status_string(aslam_status s) {
         case ASLAM_ERR_INVALID_ARG: return "invalid argument";
         case ASLAM_ERR_CUDA: return "CUDA error";
         case ASLAM_ERR_WORKSPACE: return "workspace error";
-        case ASLAM_ERR_TIMEOUT: return "device wait timed out";
+        case ASLAM_ERR_TIMEOUT: return "reserved (no device waits in this build)";
         case ASLAM_ERR_STATE: return "invalid state";
         case ASLAM_ERR_UNSUPPORTED: return "unsupported";
         case ASLAM_ERR_DEVICE: return "device-side check failed";

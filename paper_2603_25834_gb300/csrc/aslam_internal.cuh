@@ -228,9 +228,10 @@ struct Step2DParams {
 constexpr int kTerms = ASLAM_N_TERMS;
 constexpr double kLutScale = 1099511627776.0;   // 2^40
 
-// Error bits of the sticky device word.
+// Error bit of the sticky device word (a failed ASLAM_FLAG_CHECKS check or a
+// singular fixed-lag window).  No kernel waits on another, so there is no
+// timeout bit.
 constexpr unsigned kErrChecks = 1u;
-constexpr unsigned kErrTimeout = 2u;
 
 // Records the calling thread's last error message (aslam_last_error(NULL)).
 void set_thread_error(const char *msg);

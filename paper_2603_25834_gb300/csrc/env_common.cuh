@@ -34,6 +34,11 @@ __device__ __forceinline__ EnvStart integrate_env(const Step2DParams &p, int e, 
     const float x0 = p.x[e], y0 = p.y[e], th0 = p.th[e], up0 = p.u_prev[e];
     const long long Hq0 = p.Hq[e];
     const float a_v = p.actions[2 * e], a_w = p.actions[2 * e + 1];   // 4-byte aligned input
+    // ASLAM_FLAG_CHECKS: a non-finite action is a caller error.  The clamps
+    // below still give it a defined value (fmaxf / fminf return the non-NaN
+    // operand: NaN -> 0 and -w_max; +-Inf -> the bounds), so the step goes on.
+    if ((p.flags & ASLAM_FLAG_CHECKS) && !(isfinite(a_v) && isfinite(a_w)))
+        atomicOr(p.err, kErrChecks);
     EnvStart s;
     s.reset = done != 0;
     s.ep = ep;
@@ -123,6 +128,9 @@ __device__ __forceinline__ void finish_env(const Step2DParams &p, int e, int W, 
     *vc = s.t;
     const float Up = s.u_prev;
     const float U = p.u_in ? p.u_in[e] : 0.0f;
+    // ASLAM_FLAG_CHECKS: a non-finite U_t (a caller input, or the in-step
+    // estimate of a degenerate window) makes the reward non-finite
+    if ((p.flags & ASLAM_FLAG_CHECKS) && !isfinite(U)) atomicOr(p.err, kErrChecks);
     const float dU = fsub(Up, U);                  // exact sign
     float cg = fminf(fmaxf(fdiv(fsub(p.u_hi, Up), p.u_hi), 0.0f), 1.0f);
     cg = fmul(cg, cg);

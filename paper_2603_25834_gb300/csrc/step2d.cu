@@ -225,6 +225,10 @@ __device__ void order_envs_by_cost(const Step2DParams &p, unsigned *s_hist, int 
 // ---------------------------------------------------------------------------
 // Sensing kernel: one small CTA per bundle of beams of one env
 // ---------------------------------------------------------------------------
+// kChecks (ASLAM_FLAG_CHECKS): every ground-truth index of the walk is
+// checked against the env's grid before it is read; a failed check records
+// kErrChecks in the sticky error word and ends that beam's walk.
+template <bool kChecks>
 __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned s_gt[];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -254,7 +258,11 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     }
     {
         // the env's ground truth, one bit per cell, into shared memory
-        const int words = (int)(((long long)W * H + 31) >> 5);
+        int words = (int)(((long long)W * H + 31) >> 5);
+        if (kChecks && ((words + 3) & ~3) > p.gt_words_max) {
+            if (tid == 0) atomicOr(p.err, kErrChecks);    // the grid exceeds the staged words
+            words = 0;
+        }
         const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + p.gtb_off[e]);
         uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
         for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
@@ -303,8 +311,9 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                 int st = 0, kx = 0;
                 bool lastx = false;
                 // four steps per iteration: the four cells' bits are loaded
-                // together, and one branch tests them
-                for (; st + 3 < nsteps; st += 4) {
+                // together, and one branch tests them (with checks, every step
+                // goes through the one-cell loop below)
+                for (; !kChecks && st + 3 < nsteps; st += 4) {
                     const bool x1 = eh < 0;
                     const int k1 = k + (x1 ? bm.sx : syW);
                     const int e1 = eh + (x1 ? ady : nadx);
@@ -352,6 +361,10 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
                     k += lastx ? bm.sx : syW;
                     eh += lastx ? ady : nadx;
                     kx += lastx;
+                    if (kChecks && (unsigned)k >= (unsigned)(W * H)) {
+                        atomicOr(p.err, kErrChecks);
+                        break;
+                    }
                     hit = gt_bit(gt, k) != 0;
                 }
                 cells = st + 1;                 // the start cell and every step taken
@@ -440,11 +453,17 @@ struct EnvShared {
 };
 
 // Adds one hit or miss of cell (i, j) (flat k) to its counter.  kNear:
-// the cell may lie in the 32-bit block around the robot.
-template <bool kPartial, bool kNear>
+// the cell may lie in the 32-bit block around the robot.  kChecks: a cell
+// outside the env's grid records kErrChecks and is skipped.
+template <bool kPartial, bool kNear, bool kChecks>
 __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared &sh, int i,
                                           int j, int k, bool is_hit, unsigned *s_win,
                                           unsigned *s_near) {
+    if (kChecks && ((unsigned)i >= (unsigned)sh.W || (unsigned)j >= (unsigned)sh.H ||
+                    k != j * sh.W + i)) {
+        atomicOr(p.err, kErrChecks);
+        return;
+    }
     if (kNear) {
         const int ni = i - sh.ri + sh.R8 - 1, nj = j - sh.rj + sh.R8 - 1;
         if ((unsigned)ni < (unsigned)sh.NB && (unsigned)nj < (unsigned)sh.NB) {
@@ -492,7 +511,7 @@ __device__ __forceinline__ int x_steps_after(const Beam &b, int s) {
 
 // Walks cells s0 .. min(s0 + chunk, n) - 1 of beam b, where n = cells of its
 // belief walk (all in the map; the last one takes the hit of a returned beam).
-template <bool kPartial, bool kNear>
+template <bool kPartial, bool kNear, bool kChecks>
 __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared &sh, int b,
                                           int code, int s0, unsigned *s_win, unsigned *s_near) {
     const Beam bm = beam_setup(p, sh.ray_off + b, sh.Px, sh.Py, sh.ri, sh.rj, sh.c, sh.s);
@@ -509,7 +528,7 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
     const bool hit_end = hit && s_end == last;
     const int n_miss = s_end - s0 + (hit_end ? 0 : 1);   // the hit cell is added last
     for (int c = 0; c < n_miss; ++c) {
-        add_count<kPartial, kNear>(p, sh, i, j, k, false, s_win, s_near);
+        add_count<kPartial, kNear, kChecks>(p, sh, i, j, k, false, s_win, s_near);
         if (eh < 0) {
             i += bm.sx;
             k += bm.sx;
@@ -520,7 +539,7 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
             eh -= adx;
         }
     }
-    if (hit_end) add_count<kPartial, kNear>(p, sh, i, j, k, true, s_win, s_near);
+    if (hit_end) add_count<kPartial, kNear, kChecks>(p, sh, i, j, k, true, s_win, s_near);
     return s_end - s0 + 1;
 }
 
@@ -641,6 +660,7 @@ __device__ __forceinline__ void finish_pending(const Step2DParams &p, const EnvS
 // the control warp: while the others walk env n it finishes env n-1 (reward,
 // termination, outputs) and loads env n+1's parameters into the other half
 // of a two-slot shared buffer, so neither serial step delays the CTA.
+template <bool kChecks>
 __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     long long *s_lut = reinterpret_cast<long long *>(smem);           // [clamp_q + 1]
@@ -774,8 +794,8 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                     // first chunk of a beam: may touch the 32-bit block near the robot
                     const int b = s_beam[q];
                     const int code = p.ray_code[sh.ray_off + b];
-                    rc += sh.partial ? walk_chunk<true, true>(p, sh, b, code, 0, s_win, s_near)
-                                     : walk_chunk<false, true>(p, sh, b, code, 0, s_win, s_near);
+                    rc += sh.partial ? walk_chunk<true, true, kChecks>(p, sh, b, code, 0, s_win, s_near)
+                                     : walk_chunk<false, true, kChecks>(p, sh, b, code, 0, s_win, s_near);
                 } else {
                     // later chunks start >= chunk >= 2*R8 steps out: after s steps a walk
                     // is >= s/2 cells (Chebyshev) from the robot, outside the near block
@@ -789,8 +809,8 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                     const int b = lo;
                     const int code = p.ray_code[sh.ray_off + b];
                     const int s0 = (qq - s_pref[b] + 1) * p.chunk;
-                    rc += sh.partial ? walk_chunk<true, false>(p, sh, b, code, s0, s_win, s_near)
-                                     : walk_chunk<false, false>(p, sh, b, code, s0, s_win, s_near);
+                    rc += sh.partial ? walk_chunk<true, false, kChecks>(p, sh, b, code, s0, s_win, s_near)
+                                     : walk_chunk<false, false, kChecks>(p, sh, b, code, s0, s_win, s_near);
                 }
             }
         }
@@ -1021,17 +1041,26 @@ __global__ void detmath_kernel(const float *x, const float *u, int n, float *s, 
 }  // namespace
 
 size_t update2d_static_smem() {
-    cudaFuncAttributes a;
-    return cudaFuncGetAttributes(&a, update2d_kernel) == cudaSuccess ? a.sharedSizeBytes
-                                                                      : (size_t)16384;
+    cudaFuncAttributes a, b;
+    if (cudaFuncGetAttributes(&a, update2d_kernel<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&b, update2d_kernel<true>) != cudaSuccess)
+        return (size_t)16384;
+    return a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes;
 }
 
 cudaError_t step2d_set_smem(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(update2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sense2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSenseSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(update2d_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(update2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sense2d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSenseSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sense2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSenseSmemMax);
+    return e;
 }
 
 // Beams per sensing CTA: 128, 256 once the largest map's ground truth
@@ -1045,7 +1074,13 @@ int sense_block(int gt_words_max) {
 }
 
 cudaError_t step2d_occupancy(int block, size_t smem, int *ctas_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, update2d_kernel, block, smem);
+    // the checked variant uses at least the registers of the plain one
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, update2d_kernel<false>, block, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, update2d_kernel<true>, block, smem);
+    *ctas_per_sm = a < b ? a : b;
+    return e;
 }
 
 // Integration (one thread per env), sensing (one CTA per bundle of
@@ -1075,8 +1110,11 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     // the first kernel of the step is an ordinary launch; without per-kernel
     // events the update kernel is a programmatic dependent of the sensing one
     const bool pdl = ev == nullptr;
+    const bool checks = (p.flags & ASLAM_FLAG_CHECKS) != 0;
+    auto sense = checks ? sense2d_kernel<true> : sense2d_kernel<false>;
+    auto update = checks ? update2d_kernel<true> : update2d_kernel<false>;
     const size_t gt_bytes = 4 * (size_t)p.gt_words_max;
-    e = launch_pdl(sense2d_kernel, dim3(p.n_bundles), dim3(p.sense_block), gt_bytes, s, false, p);
+    e = launch_pdl(sense, dim3(p.n_bundles), dim3(p.sense_block), gt_bytes, s, false, p);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;
     if (p.u_mode == 2) {
@@ -1086,7 +1124,7 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
         Step2DParams q = p;
         q.u_in = p.u_scan;
         q.upd_w = p.slam_weighted ? p.slam_upd_w : nullptr;
-        update2d_kernel<<<grid, block, smem, s>>>(q);
+        update<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], s);
         return e;
@@ -1098,12 +1136,12 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
         if (e != cudaSuccess) return e;
         Step2DParams q = p;
         q.u_in = p.u_scan;
-        update2d_kernel<<<grid, block, smem, s>>>(q);
+        update<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
         return e;
     }
-    e = launch_pdl(update2d_kernel, dim3(grid), dim3(block), smem, s, pdl, p);
+    e = launch_pdl(update, dim3(grid), dim3(block), smem, s, pdl, p);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;
 }

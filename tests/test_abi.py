@@ -112,3 +112,27 @@ def test_status_strings(lib):
         assert lib.aslam_status_string(s)
     assert lib.aslam_graph_step(None, None) == 1
     assert lib.aslam_step(None, None, None, None) == 1
+
+
+@pytest.mark.parametrize("field", ["res_m", "r_max_m", "noise_sigma_m", "dt_s", "v_max",
+                                   "w_max", "lam_col", "lam_abs", "kappa", "d_crash",
+                                   "visit_cell_m", "uq_u_scale", "sensor_z_m"])
+@pytest.mark.parametrize("value", [float("nan"), float("inf"), float("-inf")])
+def test_nonfinite_config_values_are_rejected(lib, field, value):
+    """Fault injection on the host: a NaN or infinite constant never reaches a
+    kernel (fields whose sign checks +Inf would pass included)."""
+    from paper_2603_25834_gb300 import aslam
+    c, keep = small_config(aslam, **{field: value})
+    n = C.c_size_t()
+    assert lib.aslam_workspace_bytes(C.byref(c), C.byref(n)) == 1
+    assert b"NaN or infinite" in lib.aslam_last_error(None)
+
+
+def test_timeout_status_is_reserved(lib):
+    """No kernel of this build waits on another: the status exists in the ABI
+    (value 4) with its string, but no call returns it."""
+    assert lib.aslam_status_string(4)
+    assert b"reserved" in lib.aslam_status_string(4)
+    for f in os.listdir(os.path.join(ROOT, "paper_2603_25834_gb300", "csrc")):
+        src = open(os.path.join(ROOT, "paper_2603_25834_gb300", "csrc", f)).read()
+        assert "return ASLAM_ERR_TIMEOUT" not in src and "kErrTimeout" not in src, f

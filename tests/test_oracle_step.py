@@ -289,3 +289,46 @@ def test_observation_layout_and_padding(orc):
     assert np.all(o["obs"][1, 3:6] == np.float32(5.0))
     assert o["obs"][0, 6] == np.float32(0.2) and o["obs"][0, 7] == np.float32(0.25)
     assert o["obs"][1, 6] == np.float32(-0.4) and o["obs"][1, 7] == np.float32(0.5)
+
+
+def test_threads_over_envs_change_no_result(orc):
+    """The CPU baseline spreads the step's independent envs over threads:
+    every output and state must equal the serial step's (the fixed-lag mode
+    included, whose scan matcher keeps its scores per call)."""
+    inp = synth.uneven(E=12, sides=(64, 96), beams=(45, 90), seed=31)
+    acts = synth.random_actions(4, 12, 5)
+    u = synth.random_uncertainty(4, 12, 6)
+    runs = []
+    for th in (1, 4):
+        orc.set_threads(th)
+        try:
+            for mode in (0, 2):
+                ob = orc.OracleBatch2D(inp, r_max=4.0, sigma=0.01, u_mode=mode)
+                outs = [ob.step(acts[s], u[s], counts=True) for s in range(4)]
+                runs.append((th, mode, ob.belief.copy(), ob.x.copy(), outs[-1]))
+        finally:
+            orc.set_threads(1)
+    for (t1, m1, b1, x1, o1), (t4, m4, b4, x4, o4) in zip(runs[:2], runs[2:]):
+        assert m1 == m4
+        np.testing.assert_array_equal(b1, b4)
+        np.testing.assert_array_equal(x1, x4)
+        for k in ("z", "terms", "obs", "cnt_h", "cnt_m", "ray_cells"):
+            np.testing.assert_array_equal(o1[k], o4[k])
+
+
+def test_nonfinite_actions_take_the_clamp_bounds(orc):
+    """Host-side fault injection: Eq. 4 bounds the action, and the clamp takes
+    a NaN to the non-NaN bound (C99 fmax/fmin return the other operand):
+    v = NaN -> 0, w = NaN -> -w_max; +-Inf -> the nearer bound."""
+    occ = bordered(200, 200)
+    b = one_env(orc, occ, 4, 0.1, (5.0, 5.0, 0.0), r_max=2.0)
+    b.step(np.array([[np.nan, 0.0]], np.float32))
+    assert b.x[0] == np.float32(5.0) and b.y[0] == np.float32(5.0) and b.th[0] == 0.0
+    b.step(np.array([[0.0, np.nan]], np.float32))
+    assert b.x[0] == np.float32(5.0) and b.th[0] == pytest.approx(-0.1, abs=1e-7)
+    b = one_env(orc, occ, 4, 0.1, (5.0, 5.0, 0.0), r_max=2.0)
+    b.step(np.array([[np.inf, np.inf]], np.float32))
+    assert b.x[0] == pytest.approx(5.05, abs=1e-6) and b.th[0] == pytest.approx(0.1, abs=1e-7)
+    b.step(np.array([[-np.inf, -np.inf]], np.float32))
+    assert b.x[0] == pytest.approx(5.05, abs=1e-6) and b.th[0] == pytest.approx(0.0, abs=1e-7)
+    assert np.all(np.isfinite(b.belief)) and int(np.abs(b.belief).max()) <= 3584
