@@ -643,6 +643,28 @@ static double orc_slam_backbone(const orc_cfg *cfg, orc_state *st, int e, float 
     return cbrt(orc_det3(cov)) / scale;
 }
 
+/* Inverse-sensor counts of one beam (Sec. III-D log-odds grid): the ray from
+ * the Q16 origin (Px, Py) along the Q30 direction (Dx, Dy) is walked up to
+ * its measured range z (r_max for a beam without a return); every cell it
+ * crosses gets a miss, except the last, which gets the hit of a returned
+ * beam unless the walk left the map before reaching it.  Returns the number
+ * of cells counted. */
+static int64_t orc_count_beam(const orc_cfg *cfg, int32_t Px, int32_t Py, int32_t Dx, int32_t Dy,
+                              float z, int hit, int32_t W, int32_t H, int64_t *cells,
+                              int64_t *en, int64_t *ea, int cap, int32_t *hc, int32_t *mc)
+{
+    const int32_t Tz = orc_q16_of_range(hit ? z : cfg->r_max, cfg->res);
+    int left;
+    const int nc = orc_walk2d(Px, Py, Dx, Dy, Tz, W, H, cells, en, ea, cap, &left);
+    for (int k = 0; k < nc; ++k) {
+        if (k == nc - 1 && !left && hit)
+            hc[cells[k]] += 1;
+        else
+            mc[cells[k]] += 1;
+    }
+    return nc;
+}
+
 /* Threads of orc_step2d's loop over environments (1 unless the CPU
  * baseline asks for more; built without OpenMP the loop is serial).  The
  * environments of a step are independent, so the thread count changes no
@@ -738,15 +760,12 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
                 z = orc_measured_range(z_true, g, cfg->sigma, cfg->r_min, cfg->r_max,
                                        cfg->dec_scale);
             }
-            int32_t Tz = hit ? orc_q16_of_range(z, cfg->res) : Tmax;
-            nc = orc_walk2d(Px, Py, Dx, Dy, Tz, W, H, cells, en, ea, cap, &left);
-            for (int k = 0; k < nc; ++k) {
-                if (k == nc - 1 && !left && hit)
-                    hc[cells[k]] += 1;
-                else
-                    mc[cells[k]] += 1;
-            }
-            ray_cells += nc;
+            /* The scan is integrated where the robot is believed to be: the
+             * sensing pose here; with the fixed-lag backbone (u_mode 2) the
+             * optimised pose, once it is known (below). */
+            if (cfg->u_mode != 2)
+                ray_cells += orc_count_beam(cfg, Px, Py, Dx, Dy, z, hit, W, H, cells, en, ea,
+                                            cap, hc, mc);
             out->z[(int64_t)e * cfg->b_max + b] = z;
             out->z_true[(int64_t)e * cfg->b_max + b] = z_true;
             out->hit[(int64_t)e * cfg->b_max + b] = (uint8_t)hit;
@@ -758,7 +777,6 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
             out->z_true[(int64_t)e * cfg->b_max + b] = cfg->r_max;
             out->hit[(int64_t)e * cfg->b_max + b] = 0;
         }
-        free(cells);
 
         /* In-step uncertainty from the map before this scan (u_mode 1 and 2). */
         float u_scan = 0.0f, upd_w = -1.0f;
@@ -771,6 +789,24 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
             upd_w = -1.0f;
         if (st->slam_upd_w)
             st->slam_upd_w[e] = upd_w;
+        if (cfg->u_mode == 2) {
+            /* Sec. III-D: "after optimization, the aligned scan is integrated
+             * into the occupancy grid": every beam of this scan, with its
+             * measured range, walked from the window's newest optimised pose
+             * (its heading rotating the beams). */
+            const float *xe = st->win_x + ((int64_t)e * cfg->slam_window + st->win_n[e] - 1) * 3;
+            float se, ce;
+            orc_sincosf(xe[2], &se, &ce);
+            for (int b = 0; b < B; ++b) {
+                int32_t Px, Py, Dx, Dy;
+                orc_ray_setup(xe[0], xe[1], ce, se, cb_tab[b], sb_tab[b], cfg->res, &Px, &Py,
+                              &Dx, &Dy);
+                const int64_t r = (int64_t)e * cfg->b_max + b;
+                ray_cells += orc_count_beam(cfg, Px, Py, Dx, Dy, out->z[r], out->hit[r], W, H,
+                                            cells, en, ea, cap, hc, mc);
+            }
+        }
+        free(cells);
 
         /* Map update: per-step sum of increments, then one clamp per cell. */
         int16_t *L = st->belief + off;

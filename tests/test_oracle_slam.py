@@ -65,3 +65,36 @@ def test_first_scan_has_full_weight(orc):
         w.step(acts[s])
         np.testing.assert_array_equal(w.slam_upd_w, w.slam_match[:, 0])
         assert np.all(w.slam_upd_w < 1.0)
+
+
+def test_aligned_scan_is_integrated_at_the_optimised_pose(orc):
+    """Sec. III-D: "after optimization, the aligned scan is integrated into the
+    occupancy grid".  Each step's per-cell counts must equal an exact-rational
+    recount of that step's measured ranges walked from the window's newest
+    optimised pose -- not from the simulator's true pose, from which the
+    recount differs whenever the two poses differ."""
+    from tests.test_oracle_step import bordered, recount_at
+    occ = bordered(48, 40)
+    occ[10:14, 20:30] = 1
+    occ[25:36, 8:11] = 1
+    occ[28:31, 30:44] = 1
+    spawn = np.tile(np.float32([1.21, 1.03, 0.3]), (1, 2, 1))
+    inp = synth.custom_2d([occ], [40], 0.05, spawn)
+    import oracle
+    b = oracle.OracleBatch2D(inp, r_max=1.5, sigma=0.02, u_mode=2, slam_window=4)
+    acts = synth.random_actions(10, 1, 21, v_max=0.3)
+    discriminated = 0
+    for s in range(10):
+        o = b.step(acts[s], counts=True)
+        if b.done[0]:
+            break
+        n = int(b.win_n[0])
+        est = b.win_x[0, n - 1]
+        h, m = recount_at(orc, b, o, est)
+        np.testing.assert_array_equal(o["cnt_h"], h, err_msg="hits step %d" % s)
+        np.testing.assert_array_equal(o["cnt_m"], m, err_msg="misses step %d" % s)
+        assert o["ray_cells"][0] == int((h + m).sum())
+        ht, mt = recount_at(orc, b, o, (b.x[0], b.y[0], b.th[0]))
+        if not (np.array_equal(ht, h) and np.array_equal(mt, m)):
+            discriminated += 1
+    assert discriminated >= 3

@@ -116,14 +116,20 @@ def test_many_beams_through_one_cell_sum_then_clamp(orc):
 
 def recount(orc, b, o, e=0):
     """Exact-rational recount of one step's per-cell hit/miss counts."""
+    return recount_at(orc, b, o, (b.x[e], b.y[e], b.th[e]), e)
+
+
+def recount_at(orc, b, o, pose, e=0):
+    """Exact-rational recount of env e's per-cell hit/miss counts for the
+    step's measured ranges walked from `pose` (x, y, th)."""
     W, H, B = int(b.map_w[e]), int(b.map_h[e]), int(b.n_beams[e])
     res = np.float32(b.inp.res)
-    s, c = orc.sincosf(float(b.th[e]))
+    s, c = orc.sincosf(float(pose[2]))
     cb, sb = orc.beam_dirs(B, b.p["fov"])
     h = np.zeros(W * H, np.int64)
     m = np.zeros(W * H, np.int64)
     for k in range(B):
-        Px, Py, Dx, Dy = orc.ray_setup(float(b.x[e]), float(b.y[e]), c, s, float(cb[k]),
+        Px, Py, Dx, Dy = orc.ray_setup(float(pose[0]), float(pose[1]), c, s, float(cb[k]),
                                        float(sb[k]), float(res))
         z = np.float32(o["z"][e, k])
         Tz = int(np.rint(np.float32(np.float32(z / res) * np.float32(65536.0))))
