@@ -165,9 +165,12 @@ typedef struct {
      * window restarts at its reset; its first scan adds no pose factor.  With
      * slam_weighted_update = 1 the scan's log-odds increments are scaled by
      * the normalised match score s (1 for an episode's first scan):
-     * L' = clamp(L + rint(s * (h*HIT + m*MISS))) (fp32).  The map is built
-     * at the true pose; the estimate feeds U_t, the reward and the
-     * observation. */
+     * L' = clamp(L + rint(s * (h*HIT + m*MISS))) (fp32).  After the
+     * optimisation the aligned scan is integrated: every beam's measured
+     * range is walked from the window's newest optimised pose (its heading
+     * rotating the beams), not from the sensing pose; ray_cells counts those
+     * walks.  The sensing pose stays the robot's state (motion, collision,
+     * visit grid). */
     int32_t slam_window;           /* 1 .. 16 (default 8) */
     int32_t slam_iters;            /* 0 .. 20 (default 3) */
     int32_t csm_n_xy, csm_n_th;    /* 0 .. 8 (default 5, 5) */
@@ -405,8 +408,9 @@ aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d
  * *h_n_steps, and releases the events; ASLAM_ERR_STATE without a begin.
  * aslam_kernel_name(b, k) is the name of kernel k ("sense2d_kernel", which
  * also integrates the actions, then "uq2d_kernel" with ASLAM_U_SCANMATCH or
- * "slam_predict2d_kernel", "csm2d_kernel", "slam_window2d_kernel" with
- * ASLAM_U_FIXEDLAG, then "update2d_kernel"; 3-D: "step3d_kernel"), NULL
+ * "slam_predict2d_kernel", "csm2d_kernel", "slam_window2d_kernel",
+ * "slam_replan2d_kernel" with ASLAM_U_FIXEDLAG, then "update2d_kernel"; 3-D:
+ * "step3d_kernel"), NULL
  * past the last.  A static string, owned by the library.
  */
 #define ASLAM_MAX_STEP_KERNELS 8

@@ -361,7 +361,7 @@ namespace {
 
 int step_kernels(const aslam_batch *b) {
     if (b->hi.dims == 3) return kStep3DKernels;
-    return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : b->p.u_mode == ASLAM_U_FIXEDLAG ? 3 : 0);
+    return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : b->p.u_mode == ASLAM_U_FIXEDLAG ? 4 : 0);
 }
 
 void release_profile(aslam_batch *b) {
@@ -1242,9 +1242,10 @@ const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
     if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
     static const char *const k2s[] = {"sense2d_kernel",
                                       "slam_predict2d_kernel", "csm2d_kernel",
-                                      "slam_window2d_kernel", "update2d_kernel"};
+                                      "slam_window2d_kernel", "slam_replan2d_kernel",
+                                      "update2d_kernel"};
     if (b->p.u_mode == ASLAM_U_SCANMATCH) return k < kStep2DKernels + 1 ? k2u[k] : nullptr;
-    if (b->p.u_mode == ASLAM_U_FIXEDLAG) return k < kStep2DKernels + 3 ? k2s[k] : nullptr;
+    if (b->p.u_mode == ASLAM_U_FIXEDLAG) return k < kStep2DKernels + 4 ? k2s[k] : nullptr;
     return k < kStep2DKernels ? k2[k] : nullptr;
 }
 

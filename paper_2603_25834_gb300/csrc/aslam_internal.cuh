@@ -242,7 +242,7 @@ float range_scale(int d);
 // Launchers (defined next to their kernels).
 // `ev` (optional) receives an event record before the first kernel and
 // after each kernel of the step: 4 events for 2-D, 2 for 3-D.
-constexpr int kStep2DKernels = 2, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1, +3 with u_mode 2
+constexpr int kStep2DKernels = 2, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1, +4 with u_mode 2
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);

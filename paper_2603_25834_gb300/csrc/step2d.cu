@@ -52,6 +52,13 @@ namespace {
 
 constexpr int kSenseSmemMax = 200 * 1024;   // ground truth of up to 1.6 M cells
 
+// Walk code of a beam (sensing -> update): the index of the last cell of its
+// belief walk, whether that cell takes a hit, and whether the beam returned
+// at all (its range is a measurement, not r_max); -1: the walk has no cells.
+constexpr int kCodeCells = 0x1fffffff;
+constexpr int kCodeRet = 1 << 29;
+constexpr int kCodeHit = 1 << 30;
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialization may start once every CTA of the kernel before it has called
 // pdl_trigger (so all of those CTAs already hold their resources); it runs
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
             // belief walk: cells 0..Ku, cut at the map border; the endpoint
             // gets the hit only when it is in the map
             const int ncells = min(Ku + 1, nm);
-            code = (ncells - 1) | ((hit && Ku < nm) ? (1 << 30) : 0);
+            code = (ncells - 1) | ((hit && Ku < nm) ? kCodeHit : 0) | (hit ? kCodeRet : 0);
             uc = ncells;
         }
         p.ray_code[ray] = code;
@@ -515,8 +522,8 @@ template <bool kPartial, bool kNear, bool kChecks>
 __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared &sh, int b,
                                           int code, int s0, unsigned *s_win, unsigned *s_near) {
     const Beam bm = beam_setup(p, sh.ray_off + b, sh.Px, sh.Py, sh.ri, sh.rj, sh.c, sh.s);
-    const int last = code & 0x3fffffff;              // index of the last cell
-    const bool hit = (code >> 30) & 1;
+    const int last = code & kCodeCells;              // index of the last cell
+    const bool hit = (code & kCodeHit) != 0;
     const int kx = s0 ? x_steps_after(bm, s0) : 0, ky = s0 - kx;
     const int W = sh.W;
     int i = sh.ri + bm.sx * kx, j = sh.rj + bm.sy * ky;
@@ -734,7 +741,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         for (int b0 = 0; b0 < B; b0 += nt) {
             const int b = b0 + tid;
             const int code = b < B ? p.ray_code[sh.ray_off + b] : -1;
-            int vl = code < 0 ? 0 : (code & 0x3fffffff) / p.chunk;    // later chunks
+            int vl = code < 0 ? 0 : (code & kCodeCells) / p.chunk;    // later chunks
             int vf = code < 0 ? 0 : 1;                                  // a first chunk
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -943,6 +950,58 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     }
 }
 
+// The fixed-lag backbone integrates the aligned scan (Sec. III-D: after the
+// optimisation the aligned scan is integrated into the grid): every beam's
+// measured range is walked from the window's newest optimised pose instead of
+// the sensing pose.  One CTA per env re-plans each beam's walk code from that
+// pose (the same exact geometry as the sensing kernel, and the beam's return
+// flag from its sensing code), then replaces the walk origin and heading in
+// the env's header; the update kernel walks from there.  The sensing pose
+// stays in the header's start (state, visit grid, collision cell).
+__global__ void __launch_bounds__(128) slam_replan2d_kernel(const Step2DParams p) {
+    const int e = blockIdx.x;
+    __shared__ int s_P[2];
+    __shared__ float s_cs[2];
+    if (threadIdx.x == 0) {
+        const int n = p.win_n[e];                    // >= 1 after the window kernel
+        const float *xe = p.win_x + ((long long)e * p.slam_L + n - 1) * 3;
+        float sn, cs;
+        det_sincos(xe[2], sn, cs);
+        s_P[0] = q16_of(xe[0], p.res);
+        s_P[1] = q16_of(xe[1], p.res);
+        s_cs[0] = cs;
+        s_cs[1] = sn;
+    }
+    __syncthreads();
+    const int Px = s_P[0], Py = s_P[1];
+    const float c = s_cs[0], sn = s_cs[1];
+    const int W = p.W[e], H = p.H[e], B = p.B[e];
+    const int i0 = Px >> 16, j0 = Py >> 16;
+    const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const long long ray = p.ray_off[e] + b;
+        const int c0 = p.ray_code[ray];
+        const bool ret = c0 >= 0 && (c0 & kCodeRet) != 0;
+        int code = -1;
+        if (in0) {
+            const Beam bm = beam_setup(p, ray, Px, Py, i0, j0, c, sn);
+            const int nm = cells_in_map(bm, i0, j0, W, H);
+            const int Tz = ret ? q16_of(p.z[ray], p.res) : p.Tmax;
+            const int Ku = crossings_le(bm.nx0, bm.adx, Tz) + crossings_le(bm.ny0, bm.ady, Tz);
+            const int ncells = min(Ku + 1, nm);
+            code = (ncells - 1) | ((ret && Ku < nm) ? kCodeHit : 0) | (ret ? kCodeRet : 0);
+        }
+        p.ray_code[ray] = code;
+    }
+    if (threadIdx.x == 0) {
+        EnvSense *esp = reinterpret_cast<EnvSense *>(p.env_sense) + e;
+        esp->Px = Px;
+        esp->Py = Py;
+        esp->c = c;
+        esp->s = sn;
+    }
+}
+
 // Bridged uncertainty (Sec. III-G, Eq. 22): U = alpha U_new + (1 - alpha) U_old.
 __global__ void bridge_u_kernel(const float *u_old, const float *u_new, float alpha, int E,
                                 float *u_out, float *obs, int row, int col) {
@@ -1118,15 +1177,20 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e != cudaSuccess) return e;
     if (p.u_mode == 2) {
-        // SLAM backbone: predict, scan-match, window Gauss-Newton -> U_t
+        // SLAM backbone: predict, scan-match, window Gauss-Newton -> U_t;
+        // the scan is then integrated at the optimised pose
         e = launch_slam2d(p, s, ev ? ev + 2 : nullptr);
+        if (e != cudaSuccess) return e;
+        slam_replan2d_kernel<<<p.E, 128, 0, s>>>(p);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], s);
         if (e != cudaSuccess) return e;
         Step2DParams q = p;
         q.u_in = p.u_scan;
         q.upd_w = p.slam_weighted ? p.slam_upd_w : nullptr;
         update<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[6], s);
         return e;
     }
     if (p.u_mode == 1) {

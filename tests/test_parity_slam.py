@@ -1,11 +1,12 @@
 """GPU parity of the SLAM backbone inside the 2-D step (u_mode
 ASLAM_U_FIXEDLAG; Sec. III-D) through the C ABI against the oracle.
 
-Bit-exact: ranges, maps (also with the confidence-weighted update), counts,
-poses, the scan matches (integer scores, matched poses, score_norm, margin,
-w).  The window estimates come from two fp64 solvers (block elimination on
-the GPU, a dense Gauss-Jordan inverse in the oracle) rounded to fp32: within
-4 fp32 ulps.  U_t and the covariance: 1e-6 relative; the reward terms that
+Bit-exact: ranges, maps integrated at the window's optimised pose (also with
+the confidence-weighted update), counts, poses, the scan matches (integer
+scores, matched poses, score_norm, margin, w).  The window estimates come
+from two fp64 solvers (block elimination on the GPU, a dense Gauss-Jordan
+inverse in the oracle) rounded to fp32: within 4 fp32 ulps, and maps are
+bit-exact wherever the newest estimate (the integration origin) is.  U_t and the covariance: 1e-6 relative; the reward terms that
 read U (I, R_explore*, R_abs, R_delta*, R_t): the usual tolerance plus
 |dR/dU| * 1e-6 U (|dR/dU| as bounded in test_parity_uq)."""
 import numpy as np
@@ -28,38 +29,55 @@ def run_slam(aslam, orc, inp, steps, seed, weighted, e_sample=None, act_v_max=0.
                            slam_weighted=weighted, **orc_params(cfg))
     acts = synth.random_actions(steps, inp.n_envs, seed, v_max=act_v_max)
     u_prev = np.zeros(len(envs))
+    # The scan is integrated at the window's newest optimised pose (Sec.
+    # III-D).  Both sides solve the window in fp64 with different solvers and
+    # round it to fp32, so the estimates agree to a few ulps and, in all but
+    # rare cases, exactly.  Where the newest pose is bit-identical the
+    # integration origins are too, and the maps must be bit-exact; an env
+    # whose estimate differs by a rounding is compared from then on only
+    # where its map does not matter (ranges, true poses, window within 4
+    # ulps), and such envs must stay rare.
+    diverged = set()
+    env_steps = 0
     for s in range(steps):
         gb.step(torch.from_numpy(acts[s]).cuda())
         torch.cuda.synchronize()
         o = ob.step(acts[s][envs], counts=e_sample is None)
-        compare_step(gb, ob, o, e_map=None if e_sample is None else envs,
-                     check_counts=e_sample is None, tag="slam step %d" % s,
-                     skip_terms=(2, 4, 5, 6, 7))
         st = gb.state()
-        np.testing.assert_array_equal(st["slam_scores"].cpu().numpy()[envs], ob.slam_scores)
-        np.testing.assert_array_equal(st["slam_match"].cpu().numpy()[envs], ob.slam_match)
-        np.testing.assert_array_equal(st["slam_match_pose"].cpu().numpy()[envs], ob.slam_pose)
-        np.testing.assert_array_equal(st["slam_count"].cpu().numpy()[envs], ob.win_n)
         win = st["slam_window"].cpu().numpy()[envs]
+        cnt = st["slam_count"].cpu().numpy()[envs]
+        np.testing.assert_array_equal(cnt, ob.win_n)
         for le in range(len(envs)):
             n = int(ob.win_n[le])
             ref = ob.win_x[le, :n]
             tol = 4 * np.spacing(np.abs(ref)) + 1e-12
             assert np.all(np.abs(win[le, :n] - ref) <= tol), (s, le)
+            if not np.array_equal(win[le, n - 1], ob.win_x[le, n - 1]):
+                diverged.add(le)
+            env_steps += 1
+        compare_step(gb, ob, o, e_map=None if e_sample is None else envs,
+                     check_counts=e_sample is None, tag="slam step %d" % s,
+                     skip_terms=(2, 4, 5, 6, 7), skip_maps=diverged)
+        keep = [le for le in range(len(envs)) if le not in diverged]
+        ge = [envs[le] for le in keep]
+        np.testing.assert_array_equal(st["slam_scores"].cpu().numpy()[ge], ob.slam_scores[keep])
+        np.testing.assert_array_equal(st["slam_match"].cpu().numpy()[ge], ob.slam_match[keep])
+        np.testing.assert_array_equal(st["slam_match_pose"].cpu().numpy()[ge], ob.slam_pose[keep])
         u_gpu = st["u_prev"].cpu().numpy()[envs].astype(np.float64)
         u_orc = ob.u_prev.astype(np.float64)
-        np.testing.assert_allclose(u_gpu, u_orc, rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(u_gpu[keep], u_orc[keep], rtol=1e-6, atol=1e-12)
         cov = st["pose_cov"].cpu().numpy()[envs]
         scale = np.abs(ob.sigma).max(axis=1, keepdims=True)
-        rel = np.abs(cov - ob.sigma) / scale
-        assert rel.max() <= 1e-6, (s, rel.max(), cov.tolist(), ob.sigma.tolist())
+        rel = (np.abs(cov - ob.sigma) / scale)[keep]
+        assert rel.max(initial=0) <= 1e-6, (s, rel.max(), cov.tolist(), ob.sigma.tolist())
         terms = st["terms"].cpu().numpy()[envs].astype(np.float64)
-        for le in range(len(envs)):
+        for le in keep:
             tol = reward_bound(u_prev[le], u_orc[le]) * 1e-4
             for k in (2, 4, 5, 6, 7):
                 ref = o["terms"][le, k]
                 assert abs(terms[le, k] - ref) <= REL * abs(ref) + ABS + tol, (s, le, k)
         u_prev = u_orc
+    assert len(diverged) <= max(1, len(envs) // 4), (sorted(diverged), env_steps)
     gb.sync_status()
     return gb, ob
 
