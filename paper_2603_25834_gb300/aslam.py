@@ -66,7 +66,7 @@ class AslamConfig(C.Structure):
         ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
         ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth_rad", C.c_float),
         ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
-        ("slam_weighted_update", C.c_int32),
+        ("slam_weighted_update", C.c_int32), ("step_kernels", C.c_int32),
     ]
 
 
@@ -407,6 +407,15 @@ class Batch2D:
     def profile_begin(self, max_steps):
         """Time each kernel of the next max_steps steps with CUDA events."""
         _check(self.lib.aslam_profile_begin(self.handle, int(max_steps)), self.handle)
+
+    def kernel_names(self):
+        """Names of the kernels one step of this batch launches, in order."""
+        out = []
+        while True:
+            n = self.lib.aslam_kernel_name(self.handle, len(out))
+            if not n:
+                return out
+            out.append(n.decode())
 
     def profile_end(self):
         """{kernel name: summed device ms} and the number of timed steps."""
