@@ -377,6 +377,8 @@ __global__ void __launch_bounds__(1024, 1) fused2d_kernel(const Step2DParams p) 
     __shared__ int s_tq[32 * 64];                // per-warp rings of touched chunks
     __shared__ unsigned s_hist[256];
     __shared__ int s_last;
+    __shared__ unsigned s_bkt[32];                // beam-order classes
+    __shared__ short s_perm[ASLAM_MAX_BEAMS];     // the env's beams, longest expected first
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -432,6 +434,31 @@ __global__ void __launch_bounds__(1024, 1) fused2d_kernel(const Step2DParams p) 
             if (debug)
                 for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
         }
+        if (control) {
+            // Beam order of the walk: longest expected walk first, by the
+            // beam's range of the last step in 32 classes (a counting sort),
+            // so that each warp walks beams of similar length.  Only the
+            // schedule changes: every count is an integer sum.
+            const float kscale = 32.0f / p.r_max;
+            auto cls = [&](int b) {
+                const float zp = p.z[sh.ray_off + b];
+                return 31 - min(max((int)(zp * kscale), 0), 31);
+            };
+            s_bkt[lane] = 0u;
+            __syncwarp();
+            for (int b = lane; b < B; b += 32) atomicAdd(&s_bkt[cls(b)], 1u);
+            __syncwarp();
+            const unsigned c = s_bkt[lane];
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            s_bkt[lane] = incl - c;
+            __syncwarp();
+            for (int b = lane; b < B; b += 32) s_perm[atomicAdd(&s_bkt[cls(b)], 1u)] = (short)b;
+        }
         __syncthreads();
 
         // ---- sense + count (control warp: finish n-1, load n+1) -------------
@@ -450,7 +477,8 @@ __global__ void __launch_bounds__(1024, 1) fused2d_kernel(const Step2DParams p) 
                 load_env(p, (int)atomicAdd(p.queue, 1u), shb[(it + 1) & 1]);
             }
         } else {
-            for (int b = tid; b < B; b += nwalk) {
+            for (int q = tid; q < B; q += nwalk) {
+                const int b = s_perm[q];
                 if (sh.partial)
                     sense_and_count<true, kChecks>(p, sh, b, s_gt, s_win, s_near, debug, acc);
                 else
