@@ -294,9 +294,6 @@ def step_kernel_bytes(E, b_max, Bsum, rc_step, gt_step):
     kb = {"sense2d_kernel": gt_step / 8 + Bsum * 8 + E * 96,
           "update2d_kernel": rc_step * 4 + Bsum * 4 + io_env}
     step = rc_step * 4 + gt_step / 8 + Bsum * 4 + io_env
-    # the one-kernel step does all of it in one launch (no walk codes between
-    # two kernels)
-    kb["fused2d_kernel"] = step
     return kb, step
 
 

@@ -179,12 +179,6 @@ typedef struct {
     float slam_meas_info[3];       /* > 0 (default 4e4 m^-2, 4e4 m^-2, 1e6 rad^-2) */
     float slam_prior_info[3];      /* > 0 (default 1e4) */
     int32_t slam_weighted_update;  /* 0 (default) or 1 */
-    /* Kernels of a 2-D step with u_mode = ASLAM_U_CALLER.  0 (default) or 1:
-     * one persistent kernel, in which each beam's sensing walk also counts
-     * its map update; 2: a sensing kernel, then an update kernel that walks
-     * every beam again (the form the in-step u_modes always use).  Both give
-     * identical results. */
-    int32_t step_kernels;
 } aslam_config;
 
 #define ASLAM_U_CALLER    0
@@ -412,8 +406,7 @@ aslam_status aslam_bridge_u(aslam_batch *b, const float *d_u_old, const float *d
  * [ASLAM_MAX_STEP_KERNELS], zero past the last kernel), the number of
  * kernels a step launches to *h_n_kernels and the number of timed steps to
  * *h_n_steps, and releases the events; ASLAM_ERR_STATE without a begin.
- * aslam_kernel_name(b, k) is the name of kernel k ("fused2d_kernel" alone for
- * the one-kernel step; else "sense2d_kernel", which
+ * aslam_kernel_name(b, k) is the name of kernel k ("sense2d_kernel", which
  * also integrates the actions, then "uq2d_kernel" with ASLAM_U_SCANMATCH or
  * "slam_predict2d_kernel", "csm2d_kernel", "slam_window2d_kernel",
  * "slam_replan2d_kernel" with ASLAM_U_FIXEDLAG, then "update2d_kernel"; 3-D:

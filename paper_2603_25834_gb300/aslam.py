@@ -66,7 +66,7 @@ class AslamConfig(C.Structure):
         ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
         ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth_rad", C.c_float),
         ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
-        ("slam_weighted_update", C.c_int32), ("step_kernels", C.c_int32),
+        ("slam_weighted_update", C.c_int32),
     ]
 
 

@@ -36,7 +36,7 @@ struct Offsets {
     size_t x, y, th, u_prev, t, g, ep, done, Hq;
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
-    size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, order_hist, err, tune_actions;
+    size_t far_cnt, far_bits, ray_code, env_sense, bundles, queue, err, tune_actions;
     size_t io_in, io_out;        // aslam_step_host staging: [3E] in, [E (b_max + 3)] out
     size_t pose_cov, u_scan;
     size_t win_x, win_odo, win_meas, win_minfo, win_n, slam_pred, slam_odo, csm_pose, csm_match,
@@ -155,7 +155,6 @@ bool validate(const aslam_config *c, std::string *msg) {
             if (!(c->uq_odo_sigma[i] > 0.0f) || !(c->uq_prior_sigma[i] > 0.0f))
                 return fail("uq_odo_sigma and uq_prior_sigma must be > 0");
     }
-    if (c->step_kernels < 0 || c->step_kernels > 2) return fail("step_kernels must be 0, 1 or 2");
     if (c->l_clamp_q < 1 || c->l_clamp_q > 8192) return fail("l_clamp_q out of [1, 8192]");
     if (std::abs(c->l_hit_q) > 32767 || std::abs(c->l_miss_q) > 32767)
         return fail("|l_hit_q|, |l_miss_q| must be <= 32767");
@@ -272,7 +271,6 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
         o.bundles = add(8 * std::max<size_t>(nb, 1));
     }
     o.queue = add(16);         // {next item, CTAs finished, sensing CTAs finished}
-    o.order_hist = add(4 * 256);
     o.err = add(4);
     o.tune_actions = add(8 * E);
     o.io_in = add(12 * E);                                   // actions [E, 2], U [E]
@@ -363,7 +361,6 @@ namespace {
 
 int step_kernels(const aslam_batch *b) {
     if (b->hi.dims == 3) return kStep3DKernels;
-    if (b->p.fused) return 1;
     return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : b->p.u_mode == ASLAM_U_FIXEDLAG ? 4 : 0);
 }
 
@@ -410,15 +407,9 @@ int near_words(const HostInfo &hi) {
 int pref_words(const HostInfo &hi) { return 2 * (int)pad_to((size_t)hi.b_max + 1, 4); }
 int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }
 
-// Largest counter window side that fits the shared memory of the step's
-// update kernel: next to the entropy table and the near block, the update
-// kernel keeps its chunk tables, the one-kernel step the staged ground truth.
-int auto_window(const HostInfo &hi, int smem_optin, int clamp_q, bool fused) {
-    long long budget_words =
-        fused ? (smem_optin - (long long)fused2d_static_smem()) / 4 - hi.gt_words_max -
-                    near_words(hi) - lut_words(clamp_q)
-              : (smem_optin - (long long)update2d_static_smem()) / 4 - pref_words(hi) -
-                    near_words(hi) - lut_words(clamp_q);
+int auto_window(const HostInfo &hi, int smem_optin, int clamp_q) {
+    long long budget_words = (smem_optin - (long long)update2d_static_smem()) / 4 -
+                             pref_words(hi) - near_words(hi) - lut_words(clamp_q);
     int S = (int)std::floor(std::sqrt(4.0 * (double)budget_words));
     S &= ~7;
     return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
@@ -444,21 +435,13 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     int ww = 0;
     std::string msg;
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
-    const bool fused = b->p.fused != 0;
-    const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) +
-                             (fused ? (size_t)b->hi.gt_words_max : (size_t)pref_words(b->hi)) + ww +
+    const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) + pref_words(b->hi) + ww +
                              near_words(b->hi));
-    const size_t stat = fused ? fused2d_static_smem() : update2d_static_smem();
-    if (smem + stat > (size_t)b->smem_optin)
+    if (smem + update2d_static_smem() > (size_t)b->smem_optin)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
+    CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
     int per_sm = 0;
-    if (fused) {
-        CK(fused2d_set_smem(smem), "cudaFuncSetAttribute");
-        CK(fused2d_occupancy(block, smem, &per_sm), "occupancy");
-    } else {
-        CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
-        CK(step2d_occupancy(block, smem, &per_sm), "occupancy");
-    }
+    CK(step2d_occupancy(block, smem, &per_sm), "occupancy");
     if (per_sm < 1) return fail_b(b, ASLAM_ERR_INVALID_ARG, "launch configuration does not fit an SM");
     b->block = block;
     b->window = S;
@@ -485,7 +468,6 @@ aslam_status reset_all(aslam_batch *b, cudaStream_t s) {
     CK(cudaMemsetAsync(b->p.far_cnt, 0, 4 * cells, s), "memset far counters");
     CK(cudaMemsetAsync(b->p.far_bits, 0, cells / 64, s), "memset far bitmap");
     CK(cudaMemsetAsync(b->p.queue, 0, 16, s), "memset queue");
-    CK(cudaMemsetAsync(b->p.order_hist, 0, 4 * 256, s), "memset order histogram");
     if (b->p.dbg_counts) CK(cudaMemsetAsync(b->p.dbg_counts, 0, 4 * cells, s), "memset debug");
     CK(launch_init_state(b->p, s), "init state");
     return ASLAM_OK;
@@ -547,7 +529,6 @@ aslam_status aslam_config_init(aslam_config *c) {
     c->slam_meas_info[2] = 1e6f;                             // sigma 1 mrad
     for (int q = 0; q < 3; ++q) c->slam_prior_info[q] = 1e4f;
     c->slam_weighted_update = 0;
-    c->step_kernels = 0;
     return ASLAM_OK;
 }
 
@@ -739,20 +720,6 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         // of update2d at 750 paper-scale envs)
         p.chunk = std::max(16, 2 * hi.r8_max);
         p.queue = at<unsigned>(b, o.queue);
-        p.order_hist = at<unsigned>(b, o.order_hist);
-        p.fused = hi.dims == 2 && cfg->u_mode == ASLAM_U_CALLER && cfg->step_kernels != 2;
-        {
-            // cost classes of the one-kernel step's queue: the largest possible
-            // update walk of an env (beams x cells of one walk) in 256 classes
-            long long cmax = 1;
-            const long long rcells = (long long)std::ceil((double)cfg->r_max_m / cfg->res_m) + 2;
-            for (int e = 0; e < E; ++e)
-                cmax = std::max(cmax, (long long)std::max(hi.B[e], 1) *
-                                          std::min(rcells, (long long)hi.W[e] + hi.H[e]));
-            int sh = 0;
-            while ((cmax >> sh) > 255) ++sh;
-            p.cost_shift = sh;
-        }
         p.err = at<unsigned>(b, o.err);
 
         // Host-built tables: beam directions, entropy table, work order.
@@ -841,7 +808,6 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                                  cudaMemcpyDeviceToDevice, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.err, 0, 4, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.queue, 0, 16, s);
-        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(p.order_hist, 0, 4 * 256, s);
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(at<void>(b, o.tune_actions), 0, 8 * (size_t)E, s);
         if (e1 == cudaSuccess)
             e1 = launch_pack_gt(d_gt, at<long long>(b, o.src_off), p.W, p.H, p.Dd, p.gtb_off,
@@ -850,7 +816,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         st = reset_all(b, s);
         if (st != ASLAM_OK) break;
         const int S = cfg->window_cells ? cfg->window_cells
-                                         : auto_window(hi, b->smem_optin, cfg->l_clamp_q, p.fused != 0);
+                                         : auto_window(hi, b->smem_optin, cfg->l_clamp_q);
         const int block = cfg->threads_per_cta ? cfg->threads_per_cta : default_block(hi);
         st = configure_launch(b, block, S);
         if (st != ASLAM_OK) break;
@@ -1019,7 +985,7 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
     std::vector<int> blocks, windows;
     for (int t : {128, 256, 384, 512, 768, 1024})
         if (t >= 64 && (t <= 1024)) blocks.push_back(t);
-    const int Sa = auto_window(b->hi, b->smem_optin, b->p.clamp_q, b->p.fused != 0);
+    const int Sa = auto_window(b->hi, b->smem_optin, b->p.clamp_q);
     for (int S : {Sa, 320, 256, 224, 192, 160, 128})
         if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
     if (b->hi.dims == 3) {
@@ -1276,7 +1242,6 @@ const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
     static const char *const k2u[] = {"sense2d_kernel", "uq2d_kernel", "update2d_kernel"};
     if (!b || k < 0) return nullptr;
     if (b->hi.dims == 3) return k == 0 ? "step3d_kernel" : nullptr;
-    if (b->p.fused) return k == 0 ? "fused2d_kernel" : nullptr;
     static const char *const k2s[] = {"sense2d_kernel",
                                       "slam_predict2d_kernel", "csm2d_kernel",
                                       "slam_window2d_kernel", "slam_replan2d_kernel",

@@ -223,10 +223,6 @@ struct Step2DParams {
     const float *actions, *u_in;
     float *out_reward, *out_obs;
     unsigned *queue, *err;
-    // one-kernel step (fused2d_kernel): used when 1
-    int fused;
-    int cost_shift;              // queue cost classes of 2^cost_shift update-walk cells
-    unsigned *order_hist;        // [256] envs per cost class, filled during the step
 };
 
 constexpr int kTerms = ASLAM_N_TERMS;
@@ -251,11 +247,6 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);
 size_t update2d_static_smem();                   // static shared bytes of the update kernel
-size_t fused2d_static_smem();                    // ... of the one-kernel step
-cudaError_t fused2d_set_smem(size_t smem);
-cudaError_t fused2d_occupancy(int block, size_t smem, int *ctas_per_sm);
-cudaError_t launch_fused2d(const Step2DParams &p, int grid, int block, size_t smem, cudaStream_t s,
-                           const cudaEvent_t *ev = nullptr);
 size_t step3d_static_smem();                     // ... of the voxel step kernel
 size_t env_sense_bytes();
 int sense_block(int gt_words_max);

@@ -991,7 +991,6 @@ cudaError_t launch_pdl(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaSt
 
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev) {
-    if (p.fused) return launch_fused2d(p, grid, block, smem, s, ev);
     cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
     if (e != cudaSuccess) return e;
     // the first kernel of the step is an ordinary launch; without per-kernel

@@ -230,38 +230,3 @@ def test_env_base_shard_draws_the_global_noise(aslam_gpu, orc):
     with pytest.raises(aslam_gpu.AslamError):
         aslam_gpu.Batch2D(part, env_base=-1, r_max_m=6.0)
 
-
-@pytest.mark.parametrize("case", ["paper750", "uneven-window", "noise"])
-def test_one_kernel_step_matches_two_kernel_step(aslam_gpu, case):
-    """The one-kernel step (each beam's sensing walk also counts its update)
-    and the two-kernel step (sensing, then a re-walk of every beam) give
-    bit-identical ranges, maps, counts and reward terms step after step."""
-    aslam = aslam_gpu
-    if case == "paper750":
-        inp, kw, cfg, steps = synth.paper_scale(E=750), {}, dict(noise_sigma_m=0.01), 4
-    elif case == "uneven-window":
-        inp, kw, cfg, steps = synth.uneven(E=48, seed=515), dict(window_cells=160), \
-            dict(noise_sigma_m=0.01), 4
-    else:
-        inp, kw, cfg, steps = synth.paper_scale(E=16, seed=516), {}, dict(noise_sigma_m=0.3), 5
-    E = inp.n_envs
-    one = aslam.Batch2D(inp, flags=aslam.FLAG_DEBUG, r_max_m=12.0, reward_mode=1, **kw, **cfg)
-    two = aslam.Batch2D(inp, flags=aslam.FLAG_DEBUG, r_max_m=12.0, reward_mode=1, step_kernels=2,
-                        **kw, **cfg)
-    assert one.kernel_names() == ["fused2d_kernel"]
-    assert two.kernel_names() == ["sense2d_kernel", "update2d_kernel"]
-    acts = synth.random_actions(steps, E, 808)
-    u = synth.random_uncertainty(steps, E, 809)
-    for s in range(steps):
-        a = torch.from_numpy(acts[s]).cuda()
-        uu = torch.from_numpy(u[s]).cuda()
-        one.step(a, uu)
-        two.step(a, uu)
-        torch.cuda.synchronize()
-        x, y = one.state(), two.state()
-        for k in ("z", "z_true", "hit", "belief", "counts", "ray_cells", "gt_cells", "terms",
-                  "x", "y", "th", "t", "done"):
-            assert torch.equal(x[k], y[k]), (case, s, k)
-        assert torch.equal(one.observe(), two.observe())
-    one.sync_status()
-    two.sync_status()

@@ -27,15 +27,11 @@ def _run(aslam, inp, acts, profile, **cfg):
     return belief, out
 
 
-@pytest.mark.parametrize("dims", [2, "2-two-kernels", 3])
+@pytest.mark.parametrize("dims", [2, 3])
 def test_profile_names_counts_and_no_side_effects(aslam_gpu, dims):
     if dims == 2:
         inp = synth.paper_scale(E=8, W=128, B=90, seed=31)
         cfg = dict(r_max_m=6.0, noise_sigma_m=0.01)
-        names = ["fused2d_kernel"]
-    elif dims == "2-two-kernels":
-        inp = synth.paper_scale(E=8, W=128, B=90, seed=31)
-        cfg = dict(r_max_m=6.0, noise_sigma_m=0.01, step_kernels=2)
         names = ["sense2d_kernel", "update2d_kernel"]
     else:
         inp = synth.voxel_batch(E=4, W=32, H=32, D=8, n_az=32, K=2)
