@@ -53,6 +53,7 @@ WORKLOAD = dict(workload="paper_scale: 750 envs x 256^2 cells @0.05 m, 360 beams
                 reward="composite Eq. 7-17", steps_of_actions="random (v,w)",
                 l2="flushed (256 MiB write) between timed steps")
 KERNEL_SOURCES = {"2d": ["paper_2603_25834_gb300/csrc/step2d.cu",
+                         "paper_2603_25834_gb300/csrc/walk2d.cuh",
                          "paper_2603_25834_gb300/csrc/aslam_internal.cuh",
                          "paper_2603_25834_gb300/csrc/env_common.cuh"],
                   "3d": ["paper_2603_25834_gb300/csrc/step3d.cu",

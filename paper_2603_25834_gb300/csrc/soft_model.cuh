@@ -1,0 +1,139 @@
+// soft_model.cuh -- the soft expected-range model of one beam (Sec. III-D scan
+// residuals, the range model the scan-to-map Gauss-Newton differentiates),
+// evaluated in fp32 to within about 1e-5 of the range:
+//
+//   samples s_k = (k+1)*ds, k < K, at q_k = (x, y) + s_k (cos phi, sin phi);
+//   l_k = bilinear log-odds at q_k on cell centres (clamp to edge);
+//   p_k = sigmoid(l_k);  T_0 = 1, T_{k+1} = T_k (1 - p_k);
+//   r = sum_k T_k p_k s_k + T_K K ds.
+//
+// Where fp32 loses the accuracy:
+//   * the bilinear fraction of q_k: formed as x/res + s_k cos(phi)/res in
+//     fp32 it carries one ulp of the map coordinate (7.6e-6 cells at 128
+//     cells), and a log-odds step of 6 per cell turns that into 5e-5 in l.
+//     Here the origin's coordinate u0 = x/res - 1/2 is split in fp64 into an
+//     integer cell and a fraction once per beam, the per-sample step
+//     ds cos(phi)/res is a double-float (hi + lo) pair, and each sample's
+//     fraction is formed with the error-free TwoProd (FMA) and TwoSum of
+//     Dekker and Knuth: its error is one rounding of a number below 1;
+//   * the direction: phi = th + beta rounded to fp32 moves a sample at
+//     3.2 m by ~3e-7 m; cos/sin of th (fp64, once per env) and of beta
+//     (fp64, once per beam) are combined by a double-float rotation;
+//   * the sigmoid: exp and the reciprocal are the correctly rounded library
+//     forms (a few ulp), not the approximate intrinsics;
+//   * the sums: the range is summed with Kahan's compensation and the
+//     transmittance product is carried as a double-float, so 64 samples add
+//     no more than a few ulp.
+// The forward-mode tangents (d/dx, d/dy, d/dth) reuse the same samples in
+// plain fp32.
+#pragma once
+
+#include "aslam_internal.cuh"
+
+namespace aslam {
+
+// A double-float: the unevaluated sum hi + lo of two fp32 numbers.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_of(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// (a.hi + a.lo) (b.hi + b.lo) to about 2^-44 relative: TwoProd of the high
+// parts with one FMA, the cross terms added to its error.
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    const float l = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    const float s = __fadd_rn(p, l);
+    return {s, __fsub_rn(l, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    const float l = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s.hi, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, s.hi))};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+
+// The geometry of one beam in the bilinear frame (u = x/res - 1/2, the
+// coordinate whose integer part is the lower-left tap's column).
+struct SoftRay {
+    int iu, iv;       // integer parts of the origin's u0, v0
+    float fu, fv;     // their fractions, in [0, 1)
+    DF du, dv;        // per-sample steps ds cos(phi)/res, ds sin(phi)/res
+    float cp, sp;     // cos(phi), sin(phi) in fp32 (the th tangent)
+};
+
+// (ct, st) = cos/sin of the heading and (cb, sb) = cos/sin of the beam's
+// angle, each a double-float of its fp64 value; dsr = ds/res.
+__device__ __forceinline__ SoftRay soft_ray(double u0, double v0, DF ct, DF st, DF cb, DF sb,
+                                            DF dsr) {
+    SoftRay r;
+    const double fu = floor(u0), fv = floor(v0);
+    r.iu = (int)fu;
+    r.iv = (int)fv;
+    r.fu = __double2float_rn(u0 - fu);
+    r.fv = __double2float_rn(v0 - fv);
+    if (r.fu >= 1.0f) { r.fu = 0.0f; r.iu += 1; }     // a fraction that rounds up to 1
+    if (r.fv >= 1.0f) { r.fv = 0.0f; r.iv += 1; }
+    const DF cphi = df_add(df_mul(ct, cb), df_neg(df_mul(st, sb)));
+    const DF sphi = df_add(df_mul(st, cb), df_mul(ct, sb));
+    r.du = df_mul(dsr, cphi);
+    r.dv = df_mul(dsr, sphi);
+    r.cp = cphi.hi;
+    r.sp = sphi.hi;
+    return r;
+}
+
+// Cell and fraction of the m-th sample along one axis: f0 + m * (d.hi +
+// d.lo) with m an exact integer; the fraction is one rounding of a number
+// in [0, 1).
+__device__ __forceinline__ void sample_coord(int i0, float f0, DF d, float m, int &cell,
+                                             float &frac) {
+    const float p = __fmul_rn(m, d.hi);
+    const float pe = __fmaf_rn(m, d.hi, -p);
+    const DF s = two_sum(f0, p);
+    const float lo = __fadd_rn(s.lo, __fmaf_rn(m, d.lo, pe));
+    const float fl = floorf(s.hi);
+    float fr = __fadd_rn(__fsub_rn(s.hi, fl), lo);     // s.hi - fl is exact
+    int c = (int)fl;
+    if (fr < 0.0f) {
+        fr = __fadd_rn(fr, 1.0f);
+        c -= 1;
+    } else if (fr >= 1.0f) {
+        fr = __fsub_rn(fr, 1.0f);
+        c += 1;
+    }
+    cell = i0 + c;
+    frac = fr;
+}
+
+// p = sigmoid(l) and q = 1 - p, each without cancellation, from the
+// correctly rounded exp and reciprocal.
+__device__ __forceinline__ void sigmoid_pq_accurate(float l, float &pr, float &q) {
+    const float e = expf(-fabsf(l));
+    const float inv = __frcp_rn(__fadd_rn(1.0f, e));
+    if (l >= 0.f) {
+        pr = inv;
+        q = __fmul_rn(e, inv);
+    } else {
+        pr = __fmul_rn(e, inv);
+        q = inv;
+    }
+}
+
+}  // namespace aslam

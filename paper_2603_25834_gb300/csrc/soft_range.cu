@@ -23,16 +23,60 @@
 #include <string>
 
 #include "aslam_internal.cuh"
+#include "soft_model.cuh"
 
 namespace aslam {
 namespace {
 
 struct SoftParams {
     int E, W, H, B, K;
-    float res, inv_res, ds, r_far, dbeta, beta0, mu, sigma2;
+    float res, inv_res, ds, r_far, mu, sigma2;
+    int full_turn;         // beam b at 2 pi b / B; else at -fov/2 + b fov / (B - 1)
+    double fov, dsr;       // field of view; ds / res
     const float *L;        // [E, H, W]
     const float *pose;     // [E, 3]
 };
+
+// Angle of beam b, in fp64 (the definition of the beam layout).
+__device__ __forceinline__ double soft_beam_angle(const SoftParams &p, int b) {
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    if (p.full_turn) return (two_pi * (double)b) / (double)p.B;
+    if (p.B == 1) return 0.0;
+    return -0.5 * p.fov + ((double)b * p.fov) / (double)(p.B - 1);
+}
+
+// cos/sin of every beam's angle as double-floats, once per CTA.
+__device__ __forceinline__ void stage_beams(const SoftParams &p, DF *s_cb, DF *s_sb) {
+    for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
+        double sb, cb;
+        sincos(soft_beam_angle(p, b), &sb, &cb);
+        s_cb[b] = df_of(cb);
+        s_sb[b] = df_of(sb);
+    }
+}
+
+// The pose's part of every beam's geometry, in fp64 by one thread: the
+// bilinear-frame origin u0 = x/res - 1/2, v0 = y/res - 1/2 and cos/sin of
+// the heading.
+struct SoftPose {
+    double u0, v0;
+    DF ct, st;
+};
+
+__device__ __forceinline__ SoftPose soft_pose(const SoftParams &p, float x, float y, float th) {
+    SoftPose q;
+    q.u0 = (double)x / (double)p.res - 0.5;
+    q.v0 = (double)y / (double)p.res - 0.5;
+    double s, c;
+    sincos((double)th, &s, &c);
+    q.ct = df_of(c);
+    q.st = df_of(s);
+    return q;
+}
+
+__device__ __forceinline__ SoftRay ray_of(const SoftParams &p, const SoftPose &q, DF cb, DF sb) {
+    return soft_ray(q.u0, q.v0, q.ct, q.st, cb, sb, df_of(p.dsr));
+}
 
 struct Sample {
     float l, gx, gy;       // log-odds and its gradient (per metre)
@@ -40,12 +84,15 @@ struct Sample {
     float w[4];
 };
 
-__device__ __forceinline__ void bilinear(const SoftParams &p, const float *L, float px, float py,
-                                         Sample &s) {
-    const float u = px * p.inv_res - 0.5f, v = py * p.inv_res - 0.5f;
-    const float fu = floorf(u), fv = floorf(v);
-    const float ax = u - fu, ay = v - fv;
-    const int i0 = (int)fu, j0 = (int)fv;
+// Bilinear log-odds of sample k of a ray: lower-left tap (i0, j0) with
+// fractions (ax, ay), taps clamped to the map.
+__device__ __forceinline__ void soft_sample(const SoftParams &p, const float *L, const SoftRay &ry,
+                                            int k, Sample &s) {
+    const float m = (float)(k + 1);
+    int i0, j0;
+    float ax, ay;
+    sample_coord(ry.iu, ry.fu, ry.du, m, i0, ax);
+    sample_coord(ry.iv, ry.fv, ry.dv, m, j0, ay);
     const int ia = min(max(i0, 0), p.W - 1), ib = min(max(i0 + 1, 0), p.W - 1);
     const int ja = min(max(j0, 0), p.H - 1), jb = min(max(j0 + 1, 0), p.H - 1);
     s.idx[0] = ja * p.W + ia;
@@ -63,50 +110,47 @@ __device__ __forceinline__ void bilinear(const SoftParams &p, const float *L, fl
     s.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * p.inv_res;
 }
 
-// p = sigmoid(l) and q = 1 - p, each without cancellation (fast exp and
-// divide: a few ulp, far inside the ranges' tolerance).
-__device__ __forceinline__ void sigmoid_pq(float l, float &pr, float &q) {
-    const float e = __expf(-fabsf(l));
-    const float inv = __fdividef(1.0f, 1.0f + e);
-    if (l >= 0.f) {
-        pr = inv;
-        q = e * inv;
-    } else {
-        pr = e * inv;
-        q = inv;
-    }
+// Kahan step: (r, c) <- r + y with the running compensation c.
+__device__ __forceinline__ void kahan_add(float &r, float &c, float y) {
+    const float yc = __fsub_rn(y, c);
+    const float t = __fadd_rn(r, yc);
+    c = __fsub_rn(__fsub_rn(t, r), yc);
+    r = t;
 }
 
-__device__ __forceinline__ void beam_dir(const SoftParams &p, float th, int b, float &c, float &s) {
-    sincosf(th + (p.beta0 + (float)b * p.dbeta), &s, &c);
+// Transmittance times one more factor q, as a double-float.
+__device__ __forceinline__ DF trans_mul(DF T, float q) {
+    const float p = __fmul_rn(T.hi, q);
+    const float l = __fmaf_rn(T.lo, q, __fmaf_rn(T.hi, q, -p));
+    const float h = __fadd_rn(p, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, p))};
 }
 
 // Forward-mode soft range: value and d/d(x, y, th).
-__device__ __forceinline__ float soft_range_tangent(const SoftParams &p, const float *L, float x,
-                                                   float y, float th, int b, float J[3]) {
-    float cp, sp;
-    beam_dir(p, th, b, cp, sp);
-    float T = 1.f, r = 0.f;
+__device__ __forceinline__ float soft_range_tangent(const SoftParams &p, const float *L,
+                                                   const SoftRay &ry, float J[3]) {
+    DF T = {1.f, 0.f};
+    float r = 0.f, rc = 0.f;
     float dT0 = 0.f, dT1 = 0.f, dT2 = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
     Sample sm;
     for (int k = 0; k < p.K; ++k) {
         const float s = (float)(k + 1) * p.ds;
-        bilinear(p, L, x + s * cp, y + s * sp, sm);
+        soft_sample(p, L, ry, k, sm);
         float pr, q;
-        sigmoid_pq(sm.l, pr, q);
+        sigmoid_pq_accurate(sm.l, pr, q);
         const float dpl = pr * q;
         const float d0 = dpl * sm.gx, d1 = dpl * sm.gy;
-        const float d2 = dpl * (sm.gx * (-s * sp) + sm.gy * (s * cp));
-        r += T * pr * s;
-        dr0 += (dT0 * pr + T * d0) * s;
-        dr1 += (dT1 * pr + T * d1) * s;
-        dr2 += (dT2 * pr + T * d2) * s;
-        dT0 = dT0 * q - T * d0;
-        dT1 = dT1 * q - T * d1;
-        dT2 = dT2 * q - T * d2;
-        T *= q;
+        const float d2 = dpl * (sm.gx * (-s * ry.sp) + sm.gy * (s * ry.cp));
+        kahan_add(r, rc, __fmul_rn(__fmul_rn(T.hi, pr), s));
+        dr0 += (dT0 * pr + T.hi * d0) * s;
+        dr1 += (dT1 * pr + T.hi * d1) * s;
+        dr2 += (dT2 * pr + T.hi * d2) * s;
+        dT0 = dT0 * q - T.hi * d0;
+        dT1 = dT1 * q - T.hi * d1;
+        dT2 = dT2 * q - T.hi * d2;
+        T = trans_mul(T, q);
     }
-    r += T * p.r_far;
+    kahan_add(r, rc, __fmaf_rn(T.hi, p.r_far, T.lo * p.r_far));
     J[0] = dr0 + dT0 * p.r_far;
     J[1] = dr1 + dT1 * p.r_far;
     J[2] = dr2 + dT2 * p.r_far;
@@ -114,33 +158,42 @@ __device__ __forceinline__ float soft_range_tangent(const SoftParams &p, const f
 }
 
 __global__ void soft_fwd_kernel(const SoftParams p, float *ranges) {
+    __shared__ DF s_cb[ASLAM_MAX_BEAMS], s_sb[ASLAM_MAX_BEAMS];
+    __shared__ SoftPose s_q;
     const int e = blockIdx.x;
     const float *L = p.L + (long long)e * p.W * p.H;
-    const float x = p.pose[3 * e], y = p.pose[3 * e + 1], th = p.pose[3 * e + 2];
+    stage_beams(p, s_cb, s_sb);
+    if (threadIdx.x == 0) s_q = soft_pose(p, p.pose[3 * e], p.pose[3 * e + 1], p.pose[3 * e + 2]);
+    __syncthreads();
     for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
-        float cp, sp;
-        beam_dir(p, th, b, cp, sp);
-        float T = 1.f, r = 0.f;
+        const SoftRay ry = ray_of(p, s_q, s_cb[b], s_sb[b]);
+        DF T = {1.f, 0.f};
+        float r = 0.f, rc = 0.f;
         Sample sm;
         for (int k = 0; k < p.K; ++k) {
             const float s = (float)(k + 1) * p.ds;
-            bilinear(p, L, x + s * cp, y + s * sp, sm);
+            soft_sample(p, L, ry, k, sm);
             float pr, q;
-            sigmoid_pq(sm.l, pr, q);
-            r += T * pr * s;
-            T *= q;
+            sigmoid_pq_accurate(sm.l, pr, q);
+            kahan_add(r, rc, __fmul_rn(__fmul_rn(T.hi, pr), s));
+            T = trans_mul(T, q);
         }
-        ranges[(long long)e * p.B + b] = r + T * p.r_far;
+        kahan_add(r, rc, __fmaf_rn(T.hi, p.r_far, T.lo * p.r_far));
+        ranges[(long long)e * p.B + b] = r;
     }
 }
 
 __global__ void soft_jac_kernel(const SoftParams p, float *ranges, float *jac) {
+    __shared__ DF s_cb[ASLAM_MAX_BEAMS], s_sb[ASLAM_MAX_BEAMS];
+    __shared__ SoftPose s_q;
     const int e = blockIdx.x;
     const float *L = p.L + (long long)e * p.W * p.H;
-    const float x = p.pose[3 * e], y = p.pose[3 * e + 1], th = p.pose[3 * e + 2];
+    stage_beams(p, s_cb, s_sb);
+    if (threadIdx.x == 0) s_q = soft_pose(p, p.pose[3 * e], p.pose[3 * e + 1], p.pose[3 * e + 2]);
+    __syncthreads();
     for (int b = threadIdx.x; b < p.B; b += blockDim.x) {
         float J[3];
-        const float r = soft_range_tangent(p, L, x, y, th, b, J);
+        const float r = soft_range_tangent(p, L, ray_of(p, s_q, s_cb[b], s_sb[b]), J);
         const long long o = (long long)e * p.B + b;
         if (ranges) ranges[o] = r;
         jac[3 * o] = J[0];
@@ -171,40 +224,64 @@ __device__ __forceinline__ void block_sum(float (&v)[N], float (*red)[32]) {
     __syncthreads();
 }
 
+template <int N>
+__device__ __forceinline__ void block_sum_d(double (&v)[N], double (*red)[32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double a = v[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[q][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double a = 0.0;
+            for (int w = 0; w < nw; ++w) a += red[q][w];
+            v[q] = a;
+        }
+    }
+    __syncthreads();
+}
+
 // Adjoint: one CTA per env; shared memory holds T_k for every thread's beam.
 __global__ void soft_bwd_kernel(const SoftParams p, const float *grad_r, float *grad_pose,
                                 float *grad_L) {
     extern __shared__ float s_T[];            // [K][blockDim]
     __shared__ float red[3][32];
+    __shared__ DF s_cb[ASLAM_MAX_BEAMS], s_sb[ASLAM_MAX_BEAMS];
+    __shared__ SoftPose s_q;
     const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const float *L = p.L + (long long)e * p.W * p.H;
     float *gL = grad_L ? grad_L + (long long)e * p.W * p.H : nullptr;
-    const float x = p.pose[3 * e], y = p.pose[3 * e + 1], th = p.pose[3 * e + 2];
+    stage_beams(p, s_cb, s_sb);
+    if (tid == 0) s_q = soft_pose(p, p.pose[3 * e], p.pose[3 * e + 1], p.pose[3 * e + 2]);
+    __syncthreads();
     float acc[3] = {0.f, 0.f, 0.f};
     for (int b0 = 0; b0 < p.B; b0 += nt) {
         const int b = b0 + tid;
         if (b < p.B) {
             const float g = grad_r[(long long)e * p.B + b];
-            float cp, sp;
-            beam_dir(p, th, b, cp, sp);
+            const SoftRay ry = ray_of(p, s_q, s_cb[b], s_sb[b]);
             Sample sm;
             // forward sweep: transmittance before each sample
-            float T = 1.f;
+            DF T = {1.f, 0.f};
             for (int k = 0; k < p.K; ++k) {
-                s_T[k * nt + tid] = T;
-                const float s = (float)(k + 1) * p.ds;
-                bilinear(p, L, x + s * cp, y + s * sp, sm);
+                s_T[k * nt + tid] = T.hi;
+                soft_sample(p, L, ry, k, sm);
                 float pr, q;
-                sigmoid_pq(sm.l, pr, q);
-                T *= q;
+                sigmoid_pq_accurate(sm.l, pr, q);
+                T = trans_mul(T, q);
             }
             // reverse sweep
             float R = p.r_far;
             for (int k = p.K - 1; k >= 0; --k) {
                 const float s = (float)(k + 1) * p.ds;
-                bilinear(p, L, x + s * cp, y + s * sp, sm);
+                soft_sample(p, L, ry, k, sm);
                 float pr, q;
-                sigmoid_pq(sm.l, pr, q);
+                sigmoid_pq_accurate(sm.l, pr, q);
                 const float dl = g * s_T[k * nt + tid] * (s - R) * pr * q;
                 if (gL) {
 #pragma unroll
@@ -213,7 +290,7 @@ __global__ void soft_bwd_kernel(const SoftParams p, const float *grad_r, float *
                 }
                 acc[0] += dl * sm.gx;
                 acc[1] += dl * sm.gy;
-                acc[2] += dl * (sm.gx * (-s * sp) + sm.gy * (s * cp));
+                acc[2] += dl * (sm.gx * (-s * ry.sp) + sm.gy * (s * ry.cp));
                 R = pr * s + q * R;
             }
         }
@@ -231,35 +308,39 @@ __device__ __forceinline__ double det3(const double *A) {
            A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
-// One thread per beam; three CTAs per SM hide the latency of the sample chains.
-__global__ void __launch_bounds__(512, 3) gn_kernel(const SoftParams p, const float *z, int iters,
-                                                    float *pose_out,
-                          float *cov, float *u_out) {
-    __shared__ float red[9][32];
+// One thread per beam (the normal equations summed in fp64); two CTAs per SM.
+__global__ void __launch_bounds__(512, 2) gn_kernel(const SoftParams p, const float *z, int iters,
+                                                    float *pose_out, float *cov, float *u_out) {
+    __shared__ double red[9][32];
     __shared__ float s_pose[3];
+    __shared__ DF s_cb[ASLAM_MAX_BEAMS], s_sb[ASLAM_MAX_BEAMS];
+    __shared__ SoftPose s_q;
     const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const float *L = p.L + (long long)e * p.W * p.H;
+    stage_beams(p, s_cb, s_sb);
     if (tid < 3) s_pose[tid] = p.pose[3 * e + tid];
     __syncthreads();
     for (int it = 0; it <= iters; ++it) {
-        const float x = s_pose[0], y = s_pose[1], th = s_pose[2];
+        if (tid == 0) s_q = soft_pose(p, s_pose[0], s_pose[1], s_pose[2]);
+        __syncthreads();
         // normal equations: A (xx, xy, xt, yy, yt, tt) and g = J^T e
-        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        double v[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int b = tid; b < p.B; b += nt) {
             float J[3];
-            const float r = soft_range_tangent(p, L, x, y, th, b, J);
-            const float res = r - z[(long long)e * p.B + b];
-            v[0] += J[0] * J[0];
-            v[1] += J[0] * J[1];
-            v[2] += J[0] * J[2];
-            v[3] += J[1] * J[1];
-            v[4] += J[1] * J[2];
-            v[5] += J[2] * J[2];
-            v[6] += J[0] * res;
-            v[7] += J[1] * res;
-            v[8] += J[2] * res;
+            const float r = soft_range_tangent(p, L, ray_of(p, s_q, s_cb[b], s_sb[b]), J);
+            const double res = (double)r - (double)z[(long long)e * p.B + b];
+            const double J0 = J[0], J1 = J[1], J2 = J[2];
+            v[0] += J0 * J0;
+            v[1] += J0 * J1;
+            v[2] += J0 * J2;
+            v[3] += J1 * J1;
+            v[4] += J1 * J2;
+            v[5] += J2 * J2;
+            v[6] += J0 * res;
+            v[7] += J1 * res;
+            v[8] += J2 * res;
         }
-        block_sum<9>(v, red);
+        block_sum_d<9>(v, red);
         if (tid == 0) {
             double A[9] = {v[0] + (double)p.mu, v[1], v[2], v[1], v[3] + (double)p.mu, v[4],
                            v[2], v[4], v[5] + (double)p.mu};
@@ -270,9 +351,9 @@ __global__ void __launch_bounds__(512, 3) gn_kernel(const SoftParams p, const fl
                 for (int col = 0; col < 3; ++col) {
                     double M[9];
                     for (int q = 0; q < 9; ++q) M[q] = A[q];
-                    M[col] = -(double)v[6];
-                    M[3 + col] = -(double)v[7];
-                    M[6 + col] = -(double)v[8];
+                    M[col] = -v[6];
+                    M[3 + col] = -v[7];
+                    M[6 + col] = -v[8];
                     d[col] = det3(M) * idet;
                 }
                 s_pose[0] = (float)((double)s_pose[0] + d[0]);
@@ -340,13 +421,9 @@ aslam_status make_params(const aslam_soft_config *c, const float *L, const float
     p->inv_res = 1.0f / c->res_m;
     p->ds = c->sample_step_m;
     p->r_far = (float)c->n_samples * c->sample_step_m;
-    if (full_turn) {
-        p->beta0 = 0.f;
-        p->dbeta = (float)(two_pi / c->n_beams);
-    } else {
-        p->beta0 = (float)(-0.5 * fov);
-        p->dbeta = c->n_beams > 1 ? (float)(fov / (c->n_beams - 1)) : 0.f;
-    }
+    p->full_turn = full_turn ? 1 : 0;
+    p->fov = fov;
+    p->dsr = (double)c->sample_step_m / (double)c->res_m;
     p->mu = c->gn_damping;
     p->sigma2 = c->range_sigma_m * c->range_sigma_m;
     p->L = L;
