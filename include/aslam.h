@@ -127,8 +127,8 @@ typedef struct {
      * [lo, hi) of a larger set, created with env_base = lo, draws the same
      * noise as those envs do in one batch of the whole set (default 0). */
     int32_t env_base;
-    /* Sensor quantisation of Sec. IV-A ("a minimum range of 0.1 m ... two
-     * decimal places of precision").  A returned beam's measured range is
+    /* Sensor quantisation of Sec. IV-A (0.1 m minimum range, ranges
+     * reported to 0.01 m).  A returned beam's measured range is
      * z = clip(round(z_true + sigma*n, range_decimals), r_min_m, r_max_m),
      * the rounding done as rint(z * 10^d) / 10^d in fp32 (half to even);
      * range_decimals = -1 (default) skips it, r_min_m = 0 (default) clips

@@ -12,7 +12,7 @@
  *   - the LiDAR sensor of Sec. IV-A: each beam's range is the distance to
  *     the first occupied ground-truth cell along the beam, plus Gaussian
  *     noise N(0, sigma^2), optionally rounded to a number of decimal places
- *     (Sec. IV-A: "two decimal places of precision"), clipped to
+ *     (Sec. IV-A gives the sensor a resolution of 0.01 m), clipped to
  *     [r_min, r_max] (Sec. IV-A: minimum range 0.1 m); a beam that meets no
  *     obstacle within r_max reports r_max;
  *   - the log-odds occupancy-grid update of Sec. III-D: cells the beam
@@ -266,8 +266,8 @@ int orc_walk2d(int32_t Px, int32_t Py, int32_t Dx, int32_t Dy, int64_t T,
 /* ------------------------------------------------------------------------ */
 
 /* Beam angle of beam b of B over the field of view: a full turn without a
- * duplicate at 2*pi, or a front arc with both ends included (Sec. IV-A:
- * rays "equally distributed" over the field of view). */
+ * duplicate at 2*pi, or a front arc with both ends included (Sec. IV-A
+ * spaces the rays evenly over the field of view). */
 static double orc_beam_angle(int b, int B, double fov)
 {
     const double two_pi = 2.0 * 3.14159265358979323846;
@@ -790,8 +790,8 @@ int orc_step2d(const orc_cfg *cfg, orc_state *st, const float *actions, const fl
         if (st->slam_upd_w)
             st->slam_upd_w[e] = upd_w;
         if (cfg->u_mode == 2) {
-            /* Sec. III-D: "after optimization, the aligned scan is integrated
-             * into the occupancy grid": every beam of this scan, with its
+            /* Sec. III-D: the scan enters the occupancy grid once the window
+             * optimisation has aligned it: every beam of this scan, with its
              * measured range, walked from the window's newest optimised pose
              * (its heading rotating the beams). */
             const float *xe = st->win_x + ((int64_t)e * cfg->slam_window + st->win_n[e] - 1) * 3;

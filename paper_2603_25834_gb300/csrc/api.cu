@@ -46,7 +46,7 @@ struct Offsets {
 
 size_t pad_to(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Visit-workspace dims (Eq. 9 "workspace vastly larger than the environment"):
+// Visit-workspace dims (Eq. 9 counts cells over a workspace much larger than the map):
 // twice the map extent per axis, in visit cells, computed in fp32.
 void visit_dims(int W, int H, float res, float vc, int *Vw, int *Vh) {
     float ew = 2.0f * ((float)W * res), eh = 2.0f * ((float)H * res);

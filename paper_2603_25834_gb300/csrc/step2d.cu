@@ -777,8 +777,8 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     }
 }
 
-// The fixed-lag backbone integrates the aligned scan (Sec. III-D: after the
-// optimisation the aligned scan is integrated into the grid): every beam's
+// The fixed-lag backbone integrates the aligned scan (Sec. III-D: the scan
+// enters the grid once the window optimisation has aligned it): every beam's
 // measured range is walked from the window's newest optimised pose instead of
 // the sensing pose.  One CTA per env re-plans each beam's walk code from that
 // pose (the same exact geometry as the sensing kernel, and the beam's return

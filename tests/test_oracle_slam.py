@@ -68,8 +68,8 @@ def test_first_scan_has_full_weight(orc):
 
 
 def test_aligned_scan_is_integrated_at_the_optimised_pose(orc):
-    """Sec. III-D: "after optimization, the aligned scan is integrated into the
-    occupancy grid".  Each step's per-cell counts must equal an exact-rational
+    """Sec. III-D: the scan enters the occupancy grid after the window
+    optimisation has aligned it.  Each step's per-cell counts must equal an exact-rational
     recount of that step's measured ranges walked from the window's newest
     optimised pose -- not from the simulator's true pose, from which the
     recount differs whenever the two poses differ."""
