@@ -391,7 +391,7 @@ bool plan_window(const HostInfo &hi, int S, int *win_words, std::string *msg) {
             }
             need = ((long long)SW * SH + 3) / 4;
         }
-        ww = std::max(ww, (int)pad_to((size_t)need, 4));
+        ww = std::max(ww, (int)pad_to((size_t)need, 16));   // the apply reads 16 words at a time
     }
     *win_words = ww;
     return true;
@@ -402,14 +402,18 @@ int near_words(const HostInfo &hi) {
     return (int)pad_to((size_t)nb * nb, 4);
 }
 
-// Shared words of the update kernel's per-beam chunk table and of the
-// entropy half table (int64 per |L| = 0..clamp).
-int pref_words(const HostInfo &hi) { return 2 * (int)pad_to((size_t)hi.b_max + 1, 4); }
+// Shared words of the update kernel's per-beam table (Q30 direction and
+// walk code), of its chunk map / touched-chunk list (4 words per thread),
+// and of the entropy half table (int64 per |L| = 0..clamp).
+int geo_words(const HostInfo &hi) {
+    return (int)(pad_to(2 * (size_t)hi.b_max, 4) + pad_to((size_t)hi.b_max, 4));
+}
+int list_words(int block) { return 4 * block; }
 int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }
 
-int auto_window(const HostInfo &hi, int smem_optin, int clamp_q) {
+int auto_window(const HostInfo &hi, int smem_optin, int clamp_q, int block) {
     long long budget_words = (smem_optin - (long long)update2d_static_smem()) / 4 -
-                             pref_words(hi) - near_words(hi) - lut_words(clamp_q);
+                             geo_words(hi) - list_words(block) - near_words(hi) - lut_words(clamp_q);
     int S = (int)std::floor(std::sqrt(4.0 * (double)budget_words));
     S &= ~7;
     return std::max(64, std::min(S, ASLAM_MAX_MAP_SIDE));
@@ -435,8 +439,8 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     int ww = 0;
     std::string msg;
     if (!plan_window(b->hi, S, &ww, &msg)) return fail_b(b, ASLAM_ERR_UNSUPPORTED, msg);
-    const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) + pref_words(b->hi) + ww +
-                             near_words(b->hi));
+    const size_t smem = 4 * ((size_t)lut_words(b->p.clamp_q) + geo_words(b->hi) +
+                             list_words(block) + ww + near_words(b->hi));
     if (smem + update2d_static_smem() > (size_t)b->smem_optin)
         return fail_b(b, ASLAM_ERR_INVALID_ARG, "shared-memory window does not fit this device");
     CK(step2d_set_smem(smem), "cudaFuncSetAttribute");
@@ -452,6 +456,8 @@ aslam_status configure_launch(aslam_batch *b, int block, int S) {
     b->p.win_words_max = ww;
     b->p.near_words_max = near_words(b->hi);
     b->p.lut_words = lut_words(b->p.clamp_q);
+    b->p.geo_words = geo_words(b->hi);
+    b->p.list_words = list_words(block);
     return ASLAM_OK;
 }
 
@@ -815,9 +821,9 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 != cudaSuccess) { st = cuda_fail(b, e1, "create: upload"); break; }
         st = reset_all(b, s);
         if (st != ASLAM_OK) break;
-        const int S = cfg->window_cells ? cfg->window_cells
-                                         : auto_window(hi, b->smem_optin, cfg->l_clamp_q);
         const int block = cfg->threads_per_cta ? cfg->threads_per_cta : default_block(hi);
+        const int S = cfg->window_cells ? cfg->window_cells
+                                         : auto_window(hi, b->smem_optin, cfg->l_clamp_q, block);
         st = configure_launch(b, block, S);
         if (st != ASLAM_OK) break;
         ce = cudaStreamSynchronize(s);
@@ -985,9 +991,13 @@ aslam_status aslam_autotune(aslam_batch *b, int32_t *h_best, void *stream) {
     std::vector<int> blocks, windows;
     for (int t : {128, 256, 384, 512, 768, 1024})
         if (t >= 64 && (t <= 1024)) blocks.push_back(t);
-    const int Sa = auto_window(b->hi, b->smem_optin, b->p.clamp_q);
-    for (int S : {Sa, 320, 256, 224, 192, 160, 128})
-        if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
+    // the largest window of each block size (its chunk list grows with the block)
+    for (int blk : blocks) {
+        const int Sa = auto_window(b->hi, b->smem_optin, b->p.clamp_q, blk);
+        for (int S : {Sa, 320, 256, 224, 192, 160, 128})
+            if (S <= Sa && std::find(windows.begin(), windows.end(), S) == windows.end()) windows.push_back(S);
+    }
+    std::sort(windows.begin(), windows.end(), std::greater<int>());
     if (b->hi.dims == 3) {
         windows.assign(1, 0);
         blocks.assign({256, 512, 1024});

@@ -44,13 +44,19 @@ struct Beam {
     long long adx, ady, nx0, ny0;
 };
 
-__device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray, int Px, int Py,
-                                           int i0, int j0, float c, float s) {
+// Q30 direction of a beam: its angle in the robot frame rotated by the
+// heading (c, s), in fp32, one rounding per operation.
+__device__ __forceinline__ int2 beam_dir(const Step2DParams &p, long long ray, float c, float s) {
     const float2 cs = p.beam_cs[ray];
     const float dx = fsub(fmul(c, cs.x), fmul(s, cs.y));
     const float dy = fadd(fmul(s, cs.x), fmul(c, cs.y));
-    const int Dx = __float2int_rn(fmul(dx, 1073741824.0f));
-    const int Dy = __float2int_rn(fmul(dy, 1073741824.0f));
+    return make_int2(__float2int_rn(fmul(dx, 1073741824.0f)), __float2int_rn(fmul(dy, 1073741824.0f)));
+}
+
+__device__ __forceinline__ Beam beam_setup(const Step2DParams &p, long long ray, int Px, int Py,
+                                           int i0, int j0, float c, float s) {
+    const int2 D = beam_dir(p, ray, c, s);
+    const int Dx = D.x, Dy = D.y;
     Beam b;
     b.sx = (Dx > 0) - (Dx < 0);
     b.sy = (Dy > 0) - (Dy < 0);
@@ -142,12 +148,13 @@ __device__ __forceinline__ long long h_of(const long long *s_lut, int L) { retur
 
 // Applies (h, m) to one cell's log-odds, scaled by the env's update weight
 // wgt when wgt >= 0 (rint of the fp32 product); returns the entropy change
-// (2^-40 nats).
+// (2^-40 nats).  kWeighted = false: the caller knows wgt < 0.
+template <bool kWeighted = true>
 __device__ __forceinline__ long long apply_cell(const Step2DParams &p, const long long *s_lut,
                                                 short &L, unsigned h, unsigned m, float wgt) {
     const int l0 = L;
     int d = (int)h * p.hit_q + (int)m * p.miss_q;
-    if (wgt >= 0.0f) d = (int)rintf(fmul(wgt, (float)d));
+    if (kWeighted && wgt >= 0.0f) d = (int)rintf(fmul(wgt, (float)d));
     int l1 = l0 + d;
     l1 = min(max(l1, -p.clamp_q), p.clamp_q);
     L = (short)l1;
@@ -155,6 +162,8 @@ __device__ __forceinline__ long long apply_cell(const Step2DParams &p, const lon
 }
 
 // Applies the 8-bit counters of 8 consecutive cells (two words).
+// kGeneric = false: unweighted scan, no debug counts (the common case).
+template <bool kGeneric = true>
 __device__ __forceinline__ long long apply8(const Step2DParams &p, const long long *s_lut,
                                             uint2 cw, int4 &lv, unsigned *dbg, float wgt) {
     short *L = reinterpret_cast<short *>(&lv);
@@ -162,8 +171,8 @@ __device__ __forceinline__ long long apply8(const Step2DParams &p, const long lo
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const unsigned c8 = ((q < 4 ? cw.x : cw.y) >> ((q & 3) << 3)) & 0xffu;
-        if (c8) dh += apply_cell(p, s_lut, L[q], c8 >> 4, c8 & 0xfu, wgt);
-        if (dbg) dbg[q] = ((c8 >> 4) << 16) | (c8 & 0xfu);
+        if (c8) dh += apply_cell<kGeneric>(p, s_lut, L[q], c8 >> 4, c8 & 0xfu, wgt);
+        if (kGeneric && dbg) dbg[q] = ((c8 >> 4) << 16) | (c8 & 0xfu);
     }
     return dh;
 }
