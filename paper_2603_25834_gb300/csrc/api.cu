@@ -32,7 +32,7 @@ struct HostInfo {
 
 struct Offsets {
     size_t W, H, B, Vw, Vh, R8, Dd, elev, order, map_off, gtb_off, ray_off, visit_off, src_off;
-    size_t beam_cs, lut, gt_bits;
+    size_t beam_cs, beam_df, lut, gt_bits;
     size_t x, y, th, u_prev, t, g, ep, done, Hq;
     size_t belief, visit, spawn;
     size_t z, z_true, hit, dbg, ray_cells, gt_cells, terms, reward;
@@ -237,6 +237,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.visit_off = add(8 * (E + 1));
     o.src_off = add(8 * (E + 1));
     o.beam_cs = add(8 * rays);
+    o.beam_df = add(c->u_mode == ASLAM_U_SCANMATCH ? 16 * rays : 0);
     o.lut = add(8 * (2 * (size_t)c->l_clamp_q + 1));
     o.gt_bits = add(4 * (size_t)hi.gtb_off[E]);
     o.x = add(4 * E);
@@ -693,6 +694,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.ray_off = at<long long>(b, o.ray_off);
         p.visit_off = at<long long>(b, o.visit_off);
         p.beam_cs = at<float2>(b, o.beam_cs);
+        p.beam_df = cfg->u_mode == ASLAM_U_SCANMATCH ? at<float4>(b, o.beam_df) : nullptr;
         p.lut = at<long long>(b, o.lut);
         p.gt_bits = at<unsigned>(b, o.gt_bits);
         p.x = at<float>(b, o.x);
@@ -730,6 +732,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
 
         // Host-built tables: beam directions, entropy table, work order.
         std::vector<float2> cs((size_t)std::max<long long>(hi.ray_off[E], 1));
+        std::vector<float4> df(cfg->u_mode == ASLAM_U_SCANMATCH ? cs.size() : 0);
         const double two_pi = 2.0 * 3.14159265358979323846;
         const double fov = (double)cfg->fov_rad;
         const bool full_turn = fov <= 0.0 || fov >= two_pi - 1e-9;
@@ -744,6 +747,14 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                 else if (A == 1) a = 0.0;
                 else a = -0.5 * fov + ((double)k * fov) / (double)(A - 1);
                 cs[(size_t)hi.ray_off[e] + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+                if (cfg->u_mode == ASLAM_U_SCANMATCH) {
+                    // the soft range model of the in-step U walks the beam at
+                    // its fp64 angle: (cos, sin) as hi + lo pairs of floats
+                    const double ca = std::cos(a), sa = std::sin(a);
+                    const float ch = (float)ca, sh = (float)sa;
+                    df[(size_t)hi.ray_off[e] + k] = make_float4(ch, (float)(ca - (double)ch), sh,
+                                                                (float)(sa - (double)sh));
+                }
             }
         }
         std::vector<float2> elev((size_t)hi.n_rings);
@@ -808,6 +819,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         if (e1 == cudaSuccess) e1 = h2d((void *)p.visit_off, hi.visit_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d(at<void>(b, o.src_off), src_off.data(), 8 * (size_t)(E + 1));
         if (e1 == cudaSuccess) e1 = h2d((void *)p.beam_cs, cs.data(), 8 * cs.size());
+        if (e1 == cudaSuccess && !df.empty()) e1 = h2d((void *)p.beam_df, df.data(), 16 * df.size());
         if (e1 == cudaSuccess) e1 = h2d((void *)p.lut, lut.data(), 8 * lut.size());
         if (e1 == cudaSuccess)
             e1 = cudaMemcpyAsync((void *)p.spawn, d_spawn, 12 * (size_t)E * cfg->n_spawn,

@@ -196,6 +196,7 @@ struct Step2DParams {
     const float2 *elev_cs;       // 3-D: (cos, sin) of each ring's elevation
     const long long *map_off, *gtb_off, *ray_off, *visit_off;
     const float2 *beam_cs;
+    const float4 *beam_df;       // in-step U: per ray (cos, sin) of its angle as double-floats (hi, lo, hi, lo)
     const long long *lut;        // [2*clamp_q + 1], entropy of L in 2^-40 nats
     const unsigned *gt_bits;
     // mutable state

@@ -11,6 +11,13 @@
 // (the last block of a two-pose window with an odometry factor):
 //   Sigma_t = ((Sigma_{t-1} + Q)^-1 + A)^-1,   U_t = det(Sigma_t)^(1/3) / scale.
 //
+// Accuracy (the model of soft_model.cuh): each beam's direction comes from
+// the fp64 heading and beam angle as double-floats, each sample's bilinear
+// fraction is one rounding of a number below 1, the sigmoid uses the
+// correctly rounded exp and reciprocal, the transmittance is a double-float,
+// and J J^T is summed in fp64; U then agrees with an fp64 evaluation to
+// about 1e-5 relative.
+//
 // Runs between the sensing and the update kernels, so the map is the one
 // built before this scan.  One CTA per env, one thread per beam.  Every
 // sample lies within K*ds of the robot, so the CTA first copies the map
@@ -25,6 +32,7 @@
 
 #include "aslam_internal.cuh"
 #include "env_common.cuh"
+#include "soft_model.cuh"
 
 namespace aslam {
 namespace {
@@ -40,12 +48,10 @@ struct MapView {
     int W, H, x0, y0, ww;
 };
 
-__device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, float scale,
-                                           float px, float py, Tap &t) {
-    const float u = px * inv_res - 0.5f, v = py * inv_res - 0.5f;
-    const float fu = floorf(u), fv = floorf(v);
-    const float ax = u - fu, ay = v - fv;
-    const int i0 = (int)fu, j0 = (int)fv;
+// Bilinear log-odds (nats) and gradient (per metre) at the sample whose
+// lower-left tap is (i0, j0) with fractions (ax, ay); taps clamped to the map.
+__device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, float scale, int i0,
+                                           int j0, float ax, float ay, Tap &t) {
     const int ia = min(max(i0, 0), m.W - 1) - m.x0, ib = min(max(i0 + 1, 0), m.W - 1) - m.x0;
     const int ja = min(max(j0, 0), m.H - 1) - m.y0, jb = min(max(j0 + 1, 0), m.H - 1) - m.y0;
     const float l00 = (float)m.L[ja * m.ww + ia] * scale;
@@ -56,6 +62,14 @@ __device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, floa
           ax * ay * l11;
     t.gx = ((1.f - ay) * (l10 - l00) + ay * (l11 - l01)) * inv_res;
     t.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * inv_res;
+}
+
+// The double-float transmittance times one more factor q.
+__device__ __forceinline__ DF trans_mul_q(DF T, float q) {
+    const float p = __fmul_rn(T.hi, q);
+    const float l = __fmaf_rn(T.lo, q, __fmaf_rn(T.hi, q, -p));
+    const float h = __fadd_rn(p, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, p))};
 }
 
 __device__ __forceinline__ double det3d(const double *M) {
@@ -88,11 +102,15 @@ constexpr int kUqBlockMax = 512;
 __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams p, int R, bool staged,
                                                               int split) {
     extern __shared__ __align__(16) short s_win[];
-    __shared__ float red[6][32];
+    __shared__ double red[6][32];
+    __shared__ double s_uv[2];
+    __shared__ DF s_cs[2];
     const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int W = p.W[e], H = p.H[e], B = p.B[e];
     const bool reset = p.done[e] != 0;
+    // a thread's own terms of J J^T in fp32 (one beam per thread up to the
+    // block size; each product is one rounding), the sums over beams in fp64
     float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (!reset) {
         const short *Lq = p.belief + p.map_off[e];
@@ -111,10 +129,21 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
                 s_win[q] = __ldg(Lq + (long long)(y0 + jj) * W + x0 + ii);
             }
             m = MapView{s_win, W, H, x0, y0, ww};
-            __syncthreads();
         }
-        float s, c;
-        det_sincos(th, s, c);
+        if (tid == 0) {
+            // the bilinear frame's origin u0 = x/res - 1/2 (and v0) and the
+            // heading's cos / sin, in fp64
+            s_uv[0] = (double)x / (double)p.res - 0.5;
+            s_uv[1] = (double)y / (double)p.res - 0.5;
+            double sd, cd;
+            sincos((double)th, &sd, &cd);
+            s_cs[0] = df_of(cd);
+            s_cs[1] = df_of(sd);
+        }
+        __syncthreads();
+        const double u0 = s_uv[0], v0 = s_uv[1];
+        const DF ct = s_cs[0], st_ = s_cs[1];
+        const DF dsr = df_of((double)p.uq_ds / (double)p.res);
         const float inv_res = 1.0f / p.res, scale = p.logodds_scale;
         const float r_far = (float)p.uq_K * p.uq_ds;
         // The sweep is linear in (T, dT): the second half runs from T = 1,
@@ -128,21 +157,24 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
         for (int b0 = 0; b0 < B; b0 += nt / split) {
             const int b = b0 + tid / split;
             const bool live = b < B;
-            float2 cs = make_float2(1.f, 0.f);
-            if (live) cs = p.beam_cs[p.ray_off[e] + b];
-            const float cp = c * cs.x - s * cs.y, sp = s * cs.x + c * cs.y;
-            float T = 1.f, A = 0.f;
+            float4 bd = make_float4(1.f, 0.f, 0.f, 0.f);
+            if (live) bd = p.beam_df[p.ray_off[e] + b];
+            const SoftRay ry = soft_ray(u0, v0, ct, st_, DF{bd.x, bd.y}, DF{bd.z, bd.w}, dsr);
+            const float cp = ry.cp, sp = ry.sp;
+            DF Td = {1.f, 0.f};
+            float A = 0.f;
             float dT0 = 0.f, dT1 = 0.f, dT2 = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
             Tap t;
             for (int k = k0; live && k < k1; ++k) {
                 const float sk = (float)(k + 1) * p.uq_ds;
-                bilinear_q(m, inv_res, scale, x + sk * cp, y + sk * sp, t);
-                // p = sigmoid(l), q = 1 - p, without cancellation (fast exp and
-                // divide: U carries a 1e-2 relative tolerance)
-                const float ex = __expf(-fabsf(t.l));
-                const float inv = __fdividef(1.0f, 1.0f + ex);
-                const float pr = t.l >= 0.f ? inv : ex * inv;
-                const float q = t.l >= 0.f ? ex * inv : inv;
+                int i0, j0;
+                float ax, ay;
+                sample_coord(ry.iu, ry.fu, ry.du, (float)(k + 1), i0, ax);
+                sample_coord(ry.iv, ry.fv, ry.dv, (float)(k + 1), j0, ay);
+                bilinear_q(m, inv_res, scale, i0, j0, ax, ay, t);
+                float pr, q;
+                sigmoid_pq_accurate(t.l, pr, q);
+                const float T = Td.hi;
                 const float dpl = pr * q;
                 const float d0 = dpl * t.gx, d1 = dpl * t.gy;
                 const float d2 = dpl * (t.gx * (-sk * sp) + t.gy * (sk * cp));
@@ -153,8 +185,9 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
                 dT0 = dT0 * q - T * d0;
                 dT1 = dT1 * q - T * d1;
                 dT2 = dT2 * q - T * d2;
-                T *= q;
+                Td = trans_mul_q(Td, q);
             }
+            const float T = Td.hi;
             // the second half's sums to its first half (the lane below); one
             // thread per beam combines with an empty second half
             float Q2 = 1.f, A2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
@@ -184,7 +217,7 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        float v = a[q];
+        double v = (double)a[q];
 #pragma unroll
         for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[q][warp] = v;
@@ -194,7 +227,7 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
         double A[6];
         for (int q = 0; q < 6; ++q) {
             double v = 0.0;
-            for (int w = 0; w < nw; ++w) v += (double)red[q][w];
+            for (int w = 0; w < nw; ++w) v += red[q][w];
             A[q] = v * p.uq_inv_s2;
         }
         double *S = p.pose_cov + 6 * (long long)e;

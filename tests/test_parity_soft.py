@@ -2,13 +2,22 @@
 forward-mode Jacobian and Gauss-Newton (through the C ABI) against the
 fp64 oracle.
 
-Tolerances, from the fp32 arithmetic of the kernels: a sample position
-x + s*cos(phi) carries an absolute error of about one fp32 ulp of the map
-extent (<= 1e-6 m at 12.8 m, i.e. 2e-5 cells at 0.05 m); with log-odds
-jumping by up to 6 per cell this moves l by <= 1.2e-4 and p by <= 3e-5,
-and a range sums such changes over the few samples where p changes,
-weighted by s <= 3.2 m: |dr| <= 5e-4 m.  Gradients scale the same relative
-error by the gradient's own magnitude: |dg| <= 2e-3 * max|g| + 1e-3 |g|.
+Tolerances, from the kernels' arithmetic (the model of soft_model.cuh):
+* each sample's bilinear fraction is one fp32 rounding of a number below 1
+  (the origin is split in fp64, the per-sample step is a double-float), so
+  the taps' weights are exact to 2^-24 and l_k (|l| <= 6) to a few ulp,
+  about 1e-6; the sigmoid's correctly rounded exp and reciprocal add two
+  ulp to p_k; the range's 64 terms are summed with Kahan's compensation and
+  the transmittance is a double-float.  Each p_k is off by <= ~5e-7, and a
+  range moves by T_k |s_k - R_{k+1}| <= 3.2 m per unit of p_k, over the few
+  samples where p changes: a few 1e-6 m.  The bound is the target accuracy
+  itself: |dr| <= 1e-5 r + 1e-6 m (measured on GB300: <= 5.1e-6 m);
+* the tangents and the adjoint run in plain fp32 on the same samples, so
+  their error is a few ulp of the largest terms they sum: |dg| <= 5e-5
+  max|g| (measured: <= 1.7e-5 max|g|);
+* Gauss-Newton: the converged pose moves by the range error over the
+  Jacobian, <= 5e-6 m (measured 5.4e-7 m); the covariance and U, from an
+  A = J^T J within ~1e-4 relative, agree to 1e-4 (measured ~1e-6).
 """
 import math
 
@@ -20,7 +29,16 @@ from paper_2603_25834_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-R_TOL = 5e-4
+R_REL, R_ABS = 1e-5, 1e-6          # |dr| <= R_REL * r + R_ABS (metres)
+G_TOL = 5e-5                        # |dg| <= G_TOL * max|g|
+
+
+def range_ok(r, ro):
+    return np.all(np.abs(np.asarray(r, np.float64) - ro) <= R_REL * np.abs(ro) + R_ABS)
+
+
+def grad_ok(g, go):
+    return np.all(np.abs(np.asarray(g, np.float64) - go) <= G_TOL * np.abs(go).max())
 
 
 @pytest.fixture(scope="module")
@@ -49,11 +67,9 @@ def test_forward_and_jacobian(aslam_gpu, orc, soft, textured):
     rj, J = soft.soft_range_jac(cfg, Lt, pt)
     ocfg = orc.soft_cfg(W, W, B)
     ro, Jo = orc.soft_jacobian(ocfg, L, pose)
-    assert np.abs(r - ro).max() <= R_TOL
-    assert np.abs(rj.cpu().numpy() - ro).max() <= R_TOL
-    J = J.cpu().numpy()
-    scale = np.abs(Jo).max()
-    assert np.all(np.abs(J - Jo) <= 2e-3 * scale + 1e-3 * np.abs(Jo))
+    assert range_ok(r, ro)
+    assert range_ok(rj.cpu().numpy(), ro)
+    assert grad_ok(J.cpu().numpy(), Jo)
 
 
 @pytest.mark.parametrize("textured", [False, True])
@@ -68,8 +84,8 @@ def test_adjoint_pose_and_map(aslam_gpu, orc, soft, textured):
     _, gpo, gmo = orc.soft_ranges(orc.soft_cfg(W, W, B), L, pose, gr=gr.astype(np.float64),
                                   grad_pose=True, grad_map=True)
     gp, gm = gp.cpu().numpy(), gm.cpu().numpy()
-    assert np.all(np.abs(gp - gpo) <= 2e-3 * np.abs(gpo).max() + 1e-3 * np.abs(gpo))
-    assert np.all(np.abs(gm - gmo) <= 2e-3 * np.abs(gmo).max() + 1e-3 * np.abs(gmo))
+    assert grad_ok(gp, gpo)
+    assert grad_ok(gm, gmo)
 
 
 def test_autograd_function_matches_adjoint(aslam_gpu, orc, soft):
@@ -84,8 +100,8 @@ def test_autograd_function_matches_adjoint(aslam_gpu, orc, soft):
                                   gr=w.cpu().numpy().astype(np.float64), grad_pose=True,
                                   grad_map=True)
     gp, gm = pt.grad.cpu().numpy(), Lt.grad.cpu().numpy()
-    assert np.all(np.abs(gp - gpo) <= 2e-3 * np.abs(gpo).max() + 1e-3 * np.abs(gpo))
-    assert np.all(np.abs(gm - gmo) <= 2e-3 * np.abs(gmo).max() + 1e-3 * np.abs(gmo))
+    assert grad_ok(gp, gpo)
+    assert grad_ok(gm, gmo)
 
 
 def test_adjoint_against_gpu_finite_differences(aslam_gpu, soft):
@@ -121,11 +137,11 @@ def test_gauss_newton_matches_oracle(aslam_gpu, orc, soft):
     pg, cov, u = pg.cpu().numpy(), cov.cpu().numpy(), u.cpu().numpy()
     conv = np.all(np.abs(po - true) < 1e-3, axis=1)
     assert conv.sum() >= 4
-    assert np.all(np.abs(pg[conv] - po[conv]) <= 1e-4)
+    assert np.all(np.abs(pg[conv] - po[conv]) <= 5e-6)
     cov_o = 0.01 ** 2 * np.linalg.inv(Ao)
     u_o = np.cbrt(np.linalg.det(cov_o))
-    np.testing.assert_allclose(cov[conv], cov_o[conv], rtol=2e-2, atol=1e-3 * np.abs(cov_o).max())
-    np.testing.assert_allclose(u[conv], u_o[conv], rtol=2e-2)
+    np.testing.assert_allclose(cov[conv], cov_o[conv], rtol=1e-4, atol=1e-5 * np.abs(cov_o).max())
+    np.testing.assert_allclose(u[conv], u_o[conv], rtol=1e-4)
 
 
 def test_full_size_gn_sampled(aslam_gpu, orc, soft):
@@ -146,9 +162,9 @@ def test_full_size_gn_sampled(aslam_gpu, orc, soft):
     ocfg = orc.soft_cfg(W, W, B)
     for e in (0, 511, 1023):
         zo, _, _ = orc.soft_ranges(ocfg, L[e:e + 1], true[e:e + 1])
-        assert np.abs(z[e].cpu().numpy() - zo[0]).max() <= R_TOL
+        assert range_ok(z[e].cpu().numpy(), zo[0])
         po, _ = orc.gn(ocfg, L[e:e + 1], start[e:e + 1], z[e:e + 1].cpu().numpy(), iters=5)
         if np.all(np.abs(po[0] - true[e]) < 1e-3):
-            assert np.all(np.abs(pg[e] - po[0]) <= 1e-4)
+            assert np.all(np.abs(pg[e] - po[0]) <= 5e-6)
     # most envs converge
     assert np.mean(np.all(np.abs(pg - true) < 2e-3, axis=1)) > 0.8

@@ -3,11 +3,16 @@ Sec. III-D, Eq. 5-6) through the C ABI against the oracle.
 
 The map, ranges, counts and poses stay bit-exact (U_t feeds only the reward
 and the observation).  Tolerances for what U_t touches, from the arithmetic:
-* the kernel's soft-range Jacobian is fp32 against the oracle's fp64; the
-  soft-range parity bound on gradients (2e-3 max|g| + 1e-3 |g|) gives A = J^T J
-  within about 4e-3 relative, and the fp64 fusion keeps that relative error
-  on Sigma_t, so det^(1/3) is within about 4e-3 relative -> U within
-  1e-2 relative, Sigma entries within 2e-2 of the largest diagonal entry;
+* the kernel evaluates the soft-range Jacobian with the accurate model of
+  the differentiable form (fp64 directions, exact sample fractions,
+  correctly rounded sigmoid), within 5e-5 of its largest entry (the
+  soft-range parity bound; measured 1.7e-5), and sums J J^T in fp64: A is
+  within ~1e-4 relative of the oracle's fp64 A.  The fp64 fusion
+  ((Sigma_{t-1} + Q)^-1 + A)^-1 keeps that relative error on Sigma_t (A is
+  added to a positive definite prior, so no direction is amplified), and
+  det^(1/3) divides it by three: U within 1e-4 relative, Sigma entries within
+  1e-4 of the largest diagonal entry (measured on GB300: <= 1.8e-6 and
+  2.0e-6);
 * the reward terms that read U (I, R_explore*, R_abs, R_delta*, R_t) move
   by at most |dR/dU| * dU with |dR/dU| <= lam_explore (2/U_hi + 1/kappa) +
   lam_abs e^U (1 + U) + lam_delta e^U (2 + U) per U (U_{t-1} and U_t).
@@ -23,7 +28,8 @@ from tests.parity_util import ABS, REL, compare_step, orc_params
 
 pytestmark = pytest.mark.gpu
 
-U_REL = 1e-2
+U_REL = 1e-4
+COV_TOL = 1e-4
 UQ_GPU = dict(u_mode=1, uq_samples=64, uq_range_sigma_m=0.01, uq_odo_sigma=(0.01, 0.01, 0.01),
               uq_prior_sigma=(0.01, 0.01, 0.01))
 UQ_ORC = dict(u_mode=1, uq_samples=64, uq_range_sigma=0.01, uq_odo=(0.01, 0.01, 0.01),
@@ -60,7 +66,7 @@ def run_uq(aslam, orc, inp, steps, seed, e_sample=None, act_v_max=0.5, **cfg):
         np.testing.assert_allclose(u_gpu, u_orc, rtol=U_REL, atol=1e-9, err_msg="U step %d" % s)
         cov = st["pose_cov"].cpu().numpy()[envs]
         scale = ob.sigma[:, [0, 3, 5]].max(axis=1, keepdims=True)
-        assert np.all(np.abs(cov - ob.sigma) <= 2e-2 * scale), s
+        assert np.all(np.abs(cov - ob.sigma) <= COV_TOL * scale), s
         terms = st["terms"].cpu().numpy()[envs].astype(np.float64)
         for le in range(len(envs)):
             tol = reward_bound(u_prev_orc[le], u_orc[le])
