@@ -94,7 +94,7 @@ class OrcCfg(C.Structure):
         ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
         ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth", C.c_float),
         ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
-        ("slam_weighted", C.c_int32),
+        ("slam_weighted", C.c_int32), ("slam_gn_iters", C.c_int32),
     ]
 
 
@@ -103,7 +103,7 @@ class OrcState(C.Structure):
                 ("t", P), ("g", P), ("ep", P), ("done", P), ("visit", P), ("spawn", P),
                 ("sigma", P), ("win_x", P), ("win_odo", P), ("win_meas", P), ("win_minfo", P),
                 ("win_n", P), ("slam_match", P), ("slam_pose", P), ("slam_scores", P),
-                ("slam_upd_w", P)]
+                ("slam_upd_w", P), ("slam_gn_pose", P)]
 
 
 class OrcOut(C.Structure):
@@ -162,6 +162,10 @@ def _declare(L):
     L.orc_ray_setup.argtypes = [C.c_float] * 7 + [C.POINTER(C.c_int32)] * 4
     L.orc_measured_range.argtypes = [C.c_float] * 6
     L.orc_measured_range.restype = C.c_float
+    L.orc_slam_correct_pose.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_double,
+                                        C.c_int32, C.c_float, C.c_double, C.c_int32, C.c_int32,
+                                        C.c_float, P, P, C.c_int, P]
+    L.orc_slam_correct_pose.restype = None
     L.orc_csm.argtypes = [P, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_double,
                           P, C.c_float, C.c_float, C.c_float, C.c_int32, C.c_int32, C.c_int32,
                           C.c_float, P, P, P]
@@ -268,6 +272,20 @@ def measured_range(z_true, g, sigma, r_min, r_max, decimals=-1):
                                     C.c_float(dec_scale(decimals)))
 
 
+def slam_correct(belief, res, fov, z, pose, iters=2, K=64, ds=0.0, logodds_scale=1.0 / 1024.0,
+                 n_xy=5, n_th=5, dth=0.01):
+    """Scan-to-map Gauss-Newton correction of a matched pose on the soft
+    range model of an int16 belief [H, W] (orc_slam_correct_pose)."""
+    Lb = np.ascontiguousarray(belief, dtype=np.int16)
+    H, W = Lb.shape
+    zz = np.ascontiguousarray(z, dtype=np.float32).ravel()
+    pm = np.ascontiguousarray(pose, dtype=np.float32).ravel()
+    out = np.zeros(3, np.float32)
+    lib().orc_slam_correct_pose(_ptr(Lb), W, H, zz.size, res, fov, K, ds, logodds_scale, n_xy,
+                                n_th, dth, _ptr(zz), _ptr(pm), int(iters), _ptr(out))
+    return out
+
+
 def csm(belief, res, r_max, fov, z, pose, n_xy=5, n_th=5, sep=1, dth=0.01):
     """Correlative scan match of one env: belief int16 [H, W], ranges z [B],
     predicted pose (x, y, th).  Returns (pose_out [3] fp32, match [3] fp32,
@@ -316,7 +334,7 @@ DEFAULTS = dict(r_max=5.0, r_min=0.0, decimals=-1, fov=0.0, sigma=0.0, dt=0.1, v
                 uq_range_sigma=0.01, uq_odo=(0.01, 0.01, 0.01), uq_prior=(0.01, 0.01, 0.01),
                 uq_u_scale=0.0, slam_window=8, slam_iters=3, csm_n_xy=5, csm_n_th=5, csm_sep=1,
                 csm_dth=0.01, slam_meas_info=(4e4, 4e4, 1e6), slam_prior_info=(1e4, 1e4, 1e4),
-                slam_weighted=0)
+                slam_weighted=0, slam_gn_iters=0)
 
 
 class OracleBatch2D:
@@ -367,6 +385,7 @@ class OracleBatch2D:
         self.slam_pose = np.zeros((E, 3), np.float32)
         self.slam_scores = np.zeros((E, 3), np.int64)
         self.slam_upd_w = np.zeros(E, np.float32)
+        self.slam_gn_pose = np.zeros((E, 3), np.float32)
         self.cfg = OrcCfg(
             n_envs=E, b_max=self.b_max, n_spawn=self.spawn.shape[1],
             hit_q=p["hit_q"], miss_q=p["miss_q"], clamp_q=p["clamp_q"],
@@ -386,7 +405,7 @@ class OracleBatch2D:
             csm_n_xy=p["csm_n_xy"], csm_n_th=p["csm_n_th"], csm_sep=p["csm_sep"],
             csm_dth=p["csm_dth"], slam_meas_info=(C.c_float * 3)(*p["slam_meas_info"]),
             slam_prior_info=(C.c_float * 3)(*p["slam_prior_info"]),
-            slam_weighted=p["slam_weighted"])
+            slam_weighted=p["slam_weighted"], slam_gn_iters=p["slam_gn_iters"])
 
     def _state(self):
         return OrcState(gt=_ptr(self.gt), belief=_ptr(self.belief), x=_ptr(self.x),
@@ -397,7 +416,7 @@ class OracleBatch2D:
                         win_meas=_ptr(self.win_meas), win_minfo=_ptr(self.win_minfo),
                         win_n=_ptr(self.win_n), slam_match=_ptr(self.slam_match),
                         slam_pose=_ptr(self.slam_pose), slam_scores=_ptr(self.slam_scores),
-                        slam_upd_w=_ptr(self.slam_upd_w))
+                        slam_upd_w=_ptr(self.slam_upd_w), slam_gn_pose=_ptr(self.slam_gn_pose))
 
     def step(self, actions, u=None, counts=False):
         """One step for all envs; returns a dict of this step's outputs."""

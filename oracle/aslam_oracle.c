@@ -359,6 +359,7 @@ typedef struct {
     int32_t slam_window, slam_iters, csm_n_xy, csm_n_th, csm_sep;
     float csm_dth, slam_meas_info[3], slam_prior_info[3];
     int32_t slam_weighted;
+    int32_t slam_gn_iters;     /* scan-to-map Gauss-Newton steps on the match (0: none) */
 } orc_cfg;
 
 typedef struct {
@@ -375,6 +376,7 @@ typedef struct {
     float *slam_match, *slam_pose;                    /* [E, 3] this step's scan match */
     int64_t *slam_scores;      /* [E, 3] */
     float *slam_upd_w;         /* [E] this step's map-update weight */
+    float *slam_gn_pose;       /* [E, 3] this step's corrected match (or NULL) */
 } orc_state;
 
 enum { ORC_NT = 12 };          /* reward terms per env */
@@ -554,12 +556,104 @@ int orc_fixed_lag_gn(int L, int iters, double *x, const double *odo, const doubl
                      const double *wm, const double *prior, const double *wp, const double *wo,
                      double *cov_last);
 
+/* Scan-to-map Gauss-Newton correction of a matched pose (Sec. III-D, Eq. 5)
+ * on the soft expected-range model of the belief before this scan (the
+ * model of orc_soft_range: cfg->uq_samples samples of uq_step, the log-odds
+ * in nats).  Residuals e_b = r_b(xi) - z_b over the inliers: beams whose
+ * measured range lies within the model's reach (z_b < K ds) and whose model
+ * range at the match is within two cells of it (a reading: an unknown or
+ * barely observed cell (p near 1/2) ends the model's range early, and such
+ * beams would pull the pose toward the map's gaps).  Starting at the match
+ * pm, `iters` damped steps
+ * xi <- xi - (J^T J + mu I)^-1 J^T e (mu = 1e-6, Cramer's rule), all in
+ * fp64.  The correction is abandoned, and pm kept, when an iterate leaves
+ * the matcher's search box (|dx|, |dy| <= (n_xy + 1) res, |dth| <=
+ * (n_th + 1) dth) or is not finite.  The result is reported on a lattice
+ * of 1 mm and 1 mrad: rint(v * 1000) / 1000 in fp64, then fp32 (a reading;
+ * far below the 1 cm range noise, and it keeps the downstream integer map
+ * independent of the last bits of the arithmetic). */
+void orc_slam_correct_pose(const int16_t *belief, int32_t W, int32_t H, int32_t B, float res,
+                           double fov, int32_t K, float ds, double logodds_scale, int32_t n_xy,
+                           int32_t n_th, float dth, const float *z, const float pm[3], int iters,
+                           float out[3])
+{
+    const int64_t n = (int64_t)W * H;
+    float *Lf = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k)
+        Lf[k] = (float)((double)belief[k] * logodds_scale);
+    orc_soft_cfg sc;
+    sc.W = W;
+    sc.H = H;
+    sc.B = B;
+    sc.K = K;
+    sc.res = res;
+    sc.ds = ds > 0.0f ? (double)ds : (double)res;
+    sc.fov = fov;
+    const double r_far = (double)sc.K * sc.ds, mu = 1e-6;
+    const double box_xy = (double)(n_xy + 1) * (double)res;
+    const double box_th = (double)(n_th + 1) * (double)dth;
+    double xi[3] = {pm[0], pm[1], pm[2]};
+    int ok = 1;
+    /* the beams that inform the correction: a measured range within the
+     * model's reach (K ds) that the model at the match already explains to
+     * within two cells */
+    const double gate = 2.0 * (double)res;
+    char *use = (char *)malloc((size_t)(B > 0 ? B : 1));
+    for (int b = 0; b < B; ++b) {
+        const double r0 = orc_soft_range(&sc, Lf, xi[0], xi[1], xi[2], b, 1.0, NULL, NULL);
+        use[b] = (double)z[b] < r_far && fabs(r0 - (double)z[b]) < gate;
+    }
+    for (int it = 0; it < iters && ok; ++it) {
+        double A[9] = {0}, g[3] = {0};
+        for (int b = 0; b < B; ++b) {
+            if (!use[b]) continue;
+            double J[3] = {0.0, 0.0, 0.0};
+            const double r = orc_soft_range(&sc, Lf, xi[0], xi[1], xi[2], b, 1.0, J, NULL);
+            const double eb = r - (double)z[b];
+            for (int i = 0; i < 3; ++i) {
+                g[i] += J[i] * eb;
+                for (int j = 0; j < 3; ++j)
+                    A[3 * i + j] += J[i] * J[j];
+            }
+        }
+        for (int i = 0; i < 3; ++i)
+            A[4 * i] += mu;
+        const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                           A[2] * (A[3] * A[7] - A[4] * A[6]);
+        for (int col = 0; col < 3; ++col) {
+            double M[9];
+            memcpy(M, A, sizeof(M));
+            for (int row = 0; row < 3; ++row)
+                M[3 * row + col] = -g[row];
+            xi[col] += (M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                        M[2] * (M[3] * M[7] - M[4] * M[6])) / det;
+        }
+        ok = fabs(xi[0] - (double)pm[0]) <= box_xy && fabs(xi[1] - (double)pm[1]) <= box_xy &&
+             fabs(xi[2] - (double)pm[2]) <= box_th;     /* false for NaN */
+    }
+    free(Lf);
+    free(use);
+    for (int q = 0; q < 3; ++q)
+        out[q] = ok ? (float)(rint(xi[q] * 1000.0) / 1000.0) : pm[q];
+}
+
+static void orc_slam_correct(const orc_cfg *cfg, const orc_state *st, int e, const float *z,
+                             const float pm[3], int iters, float out[3])
+{
+    orc_slam_correct_pose(st->belief + cfg->map_off[e], cfg->map_w[e], cfg->map_h[e],
+                          cfg->n_beams[e], cfg->res, cfg->fov, cfg->uq_samples, cfg->uq_step,
+                          cfg->logodds_scale, cfg->csm_n_xy, cfg->csm_n_th, cfg->csm_dth, z, pm,
+                          iters, out);
+}
+
 /* The SLAM backbone of one env in the step (Sec. III-D), on the map before
  * this scan: the pose predicted from the window's newest estimate and the
  * odometry (v dt, 0, w dt) (the integrated pose when the window is fresh)
- * is matched against the grid by orc_csm; the window of at most L poses
- * slides, takes the prediction, the odometry factor and the match as a pose
- * factor of information w * meas_info (none for an episode's first scan),
+ * is matched against the grid by orc_csm, and the match corrected by
+ * orc_slam_correct (slam_gn_iters > 0, not on an episode's first scan); the
+ * window of at most L poses slides, takes the prediction, the odometry
+ * factor and the (corrected) match as a pose factor of information
+ * w * meas_info (none for an episode's first scan),
  * anchors its oldest pose at the current estimate with prior_info, and is
  * solved by orc_fixed_lag_gn.  Returns U_t = det(Sigma_last)^(1/3) / scale
  * and writes this scan's map-update weight (the normalised match score, 1
@@ -592,6 +686,14 @@ static double orc_slam_backbone(const orc_cfg *cfg, orc_state *st, int e, float 
     orc_csm(st->belief + cfg->map_off[e], W, H, cfg->res, cfg->r_max, B, cfg->fov, z, pred[0],
             pred[1], pred[2], cfg->csm_n_xy, cfg->csm_n_th, cfg->csm_sep, cfg->csm_dth, pm, mt,
             st->slam_scores + 3 * (int64_t)e);
+    /* the window's pose measurement: the match, corrected against the map
+     * when there is one (an episode's first scan has an empty map) */
+    float meas[3] = {pm[0], pm[1], pm[2]};
+    if (cfg->slam_gn_iters > 0 && n > 0)
+        orc_slam_correct(cfg, st, e, z, pm, cfg->slam_gn_iters, meas);
+    if (st->slam_gn_pose)
+        for (int q = 0; q < 3; ++q)
+            st->slam_gn_pose[3 * (int64_t)e + q] = meas[q];
     if (n == L) {
         for (int i = 0; i + 1 < L; ++i)
             for (int q = 0; q < 3; ++q) {
@@ -608,7 +710,7 @@ static double orc_slam_backbone(const orc_cfg *cfg, orc_state *st, int e, float 
     const float odo_step[3] = {ux, 0.0f, uth};
     for (int q = 0; q < 3; ++q) {
         wx[3 * n + q] = pred[q];
-        wm[3 * n + q] = pm[q];
+        wm[3 * n + q] = meas[q];
         wi[3 * n + q] = wgt * cfg->slam_meas_info[q];
         if (n > 0) wo_[3 * (n - 1) + q] = odo_step[q];
     }
