@@ -519,7 +519,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default/tuned)")
     ap.add_argument("--window", type=int, default=0, help="shared window side (0: default/tuned)")
     ap.add_argument("--u-mode", default="caller",
-                    choices=["caller", "scanmatch", "fixedlag", "fixedlag_weighted"],
+                    choices=["caller", "scanmatch", "fixedlag", "fixedlag_weighted", "fixedlag_gn",
+                             "fixedlag_weighted_gn"],
                     help="U_t from the caller (a synthetic signal), the in-step scan-match "
                          "covariance, or the in-step SLAM backbone (CSM + fixed-lag window; "
                          "_weighted: confidence-weighted map update)")
@@ -601,12 +602,15 @@ def main():
                         u_t="in-step scan-match covariance (64 samples of one cell, Eq. 5-6)")
     elif args.u_mode.startswith("fixedlag"):
         cfg_kw["u_mode"] = aslam.U_FIXEDLAG
-        cfg_kw["slam_weighted_update"] = int(args.u_mode == "fixedlag_weighted")
+        cfg_kw["slam_weighted_update"] = int(args.u_mode.startswith("fixedlag_weighted"))
+        cfg_kw["slam_gn_iters"] = 2 if args.u_mode.endswith("_gn") else 0
         workload = dict(workload,
-                        u_t="in-step SLAM backbone: CSM 11x11x11 + 8-pose fixed-lag window, "
+                        u_t="in-step SLAM backbone: CSM 11x11x11%s + 8-pose fixed-lag window, "
                             "3 GN iterations (Eq. 5-6)%s"
-                            % (", confidence-weighted map update"
-                               if args.u_mode == "fixedlag_weighted" else ""))
+                            % (" + 2 scan-to-map Gauss-Newton steps of the soft range model"
+                               if args.u_mode.endswith("_gn") else "",
+                               ", confidence-weighted map update"
+                               if args.u_mode.startswith("fixedlag_weighted") else ""))
     batch = aslam.Batch2D(inp, device=dev, reward_mode=aslam.REWARD_COMPOSITE,
                           threads_per_cta=args.threads, window_cells=args.window, **cfg_kw)
     tuned = None

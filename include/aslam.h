@@ -76,7 +76,7 @@ typedef enum {
  * 7 R_t (Eq. 7)          8 collision (0/1)   9 d_min of the measured ranges
  * 10 d_min of the noise-free ranges          11 H_t (nats) */
 
-#define ASLAM_CONFIG_VERSION 1u
+#define ASLAM_CONFIG_VERSION 2u
 
 /*
  * Batch configuration (POD).  Fill with aslam_config_init() and override.
@@ -179,6 +179,18 @@ typedef struct {
     float slam_meas_info[3];       /* > 0 (default 4e4 m^-2, 4e4 m^-2, 1e6 rad^-2) */
     float slam_prior_info[3];      /* > 0 (default 1e4) */
     int32_t slam_weighted_update;  /* 0 (default) or 1 */
+    /* Scan-to-map Gauss-Newton correction of the match inside the step
+     * (u_mode = ASLAM_U_FIXEDLAG; Sec. III-D, Eq. 5): slam_gn_iters damped
+     * steps xi <- xi - (J^T J + 1e-6 I)^-1 J^T e of the soft expected-range
+     * model (uq_samples samples of uq_step_m, the belief before this scan in
+     * nats) from the correlative match, over the beams whose measured range
+     * lies within the model's reach and within two cells of the model's range
+     * at the match.  An iterate outside the matcher's search box
+     * (+-(csm_n_xy + 1) cells, +-(csm_n_th + 1) csm_dth_rad) keeps the match;
+     * otherwise the result, rounded to 1 mm and 1 mrad, replaces the match as
+     * the window's pose measurement.  An episode's first scan keeps the
+     * match.  0 (default) switches the correction off. */
+    int32_t slam_gn_iters;         /* 0 .. 10 */
 } aslam_config;
 
 #define ASLAM_U_CALLER    0
@@ -214,6 +226,8 @@ typedef struct {
     float *slam_match;             /* [E, 3] this step's (score_norm, margin, w) */
     int64_t *slam_scores;          /* [E, 3] this step's (best, second, best index) */
     float *slam_match_pose;        /* [E, 3] this step's matched pose */
+    float *slam_gn_pose;           /* [E, 3] this step's corrected match (slam_gn_iters > 0),
+                                    * else NULL */
 } aslam_state_ptrs;
 
 /* Fill `cfg` with defaults (version, struct_size, constants). */

@@ -33,7 +33,7 @@ U_FIXEDLAG = 2
 N_TERMS = 12
 TERM_NAMES = ["dH", "dcells", "I", "alpha_hug", "r_explore", "r_abs", "r_delta", "R",
               "collision", "dmin_meas", "dmin_true", "H"]
-CONFIG_VERSION = 1
+CONFIG_VERSION = 2
 
 
 class AslamError(RuntimeError):
@@ -66,7 +66,7 @@ class AslamConfig(C.Structure):
         ("slam_window", C.c_int32), ("slam_iters", C.c_int32), ("csm_n_xy", C.c_int32),
         ("csm_n_th", C.c_int32), ("csm_sep", C.c_int32), ("csm_dth_rad", C.c_float),
         ("slam_meas_info", C.c_float * 3), ("slam_prior_info", C.c_float * 3),
-        ("slam_weighted_update", C.c_int32),
+        ("slam_weighted_update", C.c_int32), ("slam_gn_iters", C.c_int32),
     ]
 
 
@@ -75,7 +75,8 @@ class AslamStatePtrs(C.Structure):
                 ("done", P), ("belief", P), ("z", P), ("z_true", P), ("hit", P), ("counts", P),
                 ("ray_cells", P), ("gt_cells", P), ("terms", P), ("h_map_off", P),
                 ("h_ray_off", P), ("b_max", C.c_int32), ("pose_cov", P), ("slam_window", P),
-                ("slam_count", P), ("slam_match", P), ("slam_scores", P), ("slam_match_pose", P)]
+                ("slam_count", P), ("slam_match", P), ("slam_scores", P), ("slam_match_pose", P),
+                ("slam_gn_pose", P)]
 
 
 class AslamCsmConfig(C.Structure):
@@ -316,7 +317,9 @@ class Batch2D:
             slam_scores=(self._view(sp.slam_scores, 3 * E, torch.int64).view(E, 3)
                          if sp.slam_scores else None),
             slam_match_pose=(self._view(sp.slam_match_pose, 3 * E, torch.float32).view(E, 3)
-                             if sp.slam_match_pose else None))
+                             if sp.slam_match_pose else None),
+            slam_gn_pose=(self._view(sp.slam_gn_pose, 3 * E, torch.float32).view(E, 3)
+                          if sp.slam_gn_pose else None))
 
     def env_belief(self, e):
         st = self.state()["belief"]

@@ -40,11 +40,18 @@ struct Offsets {
     size_t io_in, io_out;        // aslam_step_host staging: [3E] in, [E (b_max + 3)] out
     size_t pose_cov, u_scan;
     size_t win_x, win_odo, win_meas, win_minfo, win_n, slam_pred, slam_odo, csm_pose, csm_match,
-        csm_scores, slam_upd_w;
+        csm_scores, slam_upd_w, slam_gn_pose;
     size_t total;
 };
 
 size_t pad_to(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Does a step evaluate the soft range model in the step (in-step U or the
+// match correction)?  Those kernels read the beams' fp64 directions.
+bool soft_dirs(const aslam_config *c) {
+    return c->dims == 2 && (c->u_mode == ASLAM_U_SCANMATCH ||
+                            (c->u_mode == ASLAM_U_FIXEDLAG && c->slam_gn_iters > 0));
+}
 
 // Visit-workspace dims (Eq. 9 counts cells over a workspace much larger than the map):
 // twice the map extent per axis, in visit cells, computed in fp32.
@@ -144,6 +151,7 @@ bool validate(const aslam_config *c, std::string *msg) {
                 return fail("slam_meas_info and slam_prior_info must be > 0");
         if (c->slam_weighted_update != 0 && c->slam_weighted_update != 1)
             return fail("slam_weighted_update must be 0 or 1");
+        if (c->slam_gn_iters < 0 || c->slam_gn_iters > 10) return fail("slam_gn_iters out of [0, 10]");
     }
     if (c->u_mode != ASLAM_U_CALLER) {
         if (c->dims != 2) return fail("an in-step u_mode needs dims = 2");
@@ -237,7 +245,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.visit_off = add(8 * (E + 1));
     o.src_off = add(8 * (E + 1));
     o.beam_cs = add(8 * rays);
-    o.beam_df = add(c->u_mode == ASLAM_U_SCANMATCH ? 16 * rays : 0);
+    o.beam_df = add(soft_dirs(c) ? 16 * rays : 0);
     o.lut = add(8 * (2 * (size_t)c->l_clamp_q + 1));
     o.gt_bits = add(4 * (size_t)hi.gtb_off[E]);
     o.x = add(4 * E);
@@ -292,6 +300,7 @@ Offsets build_layout(const aslam_config *c, const HostInfo &hi) {
     o.csm_match = add(sl ? 12 * E : 0);
     o.csm_scores = add(sl ? 24 * E : 0);
     o.slam_upd_w = add(sl ? 4 * E : 0);
+    o.slam_gn_pose = add(sl && c->slam_gn_iters > 0 ? 12 * E : 0);
     o.total = pad_to(cur, kAlign);
     return o;
 }
@@ -362,7 +371,8 @@ namespace {
 
 int step_kernels(const aslam_batch *b) {
     if (b->hi.dims == 3) return kStep3DKernels;
-    return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : b->p.u_mode == ASLAM_U_FIXEDLAG ? 4 : 0);
+    if (b->p.u_mode == ASLAM_U_FIXEDLAG) return kStep2DKernels + (b->p.slam_gn_iters > 0 ? 5 : 4);
+    return kStep2DKernels + (b->p.u_mode == ASLAM_U_SCANMATCH ? 1 : 0);
 }
 
 void release_profile(aslam_batch *b) {
@@ -536,6 +546,7 @@ aslam_status aslam_config_init(aslam_config *c) {
     c->slam_meas_info[2] = 1e6f;                             // sigma 1 mrad
     for (int q = 0; q < 3; ++q) c->slam_prior_info[q] = 1e4f;
     c->slam_weighted_update = 0;
+    c->slam_gn_iters = 0;
     return ASLAM_OK;
 }
 
@@ -646,6 +657,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
             p.csm_sep = cfg->csm_sep;
             p.csm_dth = cfg->csm_dth_rad;
             p.slam_weighted = cfg->slam_weighted_update;
+            p.slam_gn_iters = cfg->slam_gn_iters;
             for (int q = 0; q < 3; ++q) {
                 p.slam_meas_info[q] = cfg->slam_meas_info[q];
                 p.slam_prior_info[q] = cfg->slam_prior_info[q];
@@ -668,6 +680,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
             p.csm_match = at<float>(b, o.csm_match);
             p.csm_scores = at<long long>(b, o.csm_scores);
             p.slam_upd_w = at<float>(b, o.slam_upd_w);
+            p.slam_gn_pose = cfg->slam_gn_iters > 0 ? at<float>(b, o.slam_gn_pose) : nullptr;
         }
         p.lam_col = (float)cfg->lam_col;
         p.lam_explore = (float)cfg->lam_explore;
@@ -694,7 +707,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.ray_off = at<long long>(b, o.ray_off);
         p.visit_off = at<long long>(b, o.visit_off);
         p.beam_cs = at<float2>(b, o.beam_cs);
-        p.beam_df = cfg->u_mode == ASLAM_U_SCANMATCH ? at<float4>(b, o.beam_df) : nullptr;
+        p.beam_df = soft_dirs(cfg) ? at<float4>(b, o.beam_df) : nullptr;
         p.lut = at<long long>(b, o.lut);
         p.gt_bits = at<unsigned>(b, o.gt_bits);
         p.x = at<float>(b, o.x);
@@ -732,7 +745,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
 
         // Host-built tables: beam directions, entropy table, work order.
         std::vector<float2> cs((size_t)std::max<long long>(hi.ray_off[E], 1));
-        std::vector<float4> df(cfg->u_mode == ASLAM_U_SCANMATCH ? cs.size() : 0);
+        std::vector<float4> df(soft_dirs(cfg) ? cs.size() : 0);
         const double two_pi = 2.0 * 3.14159265358979323846;
         const double fov = (double)cfg->fov_rad;
         const bool full_turn = fov <= 0.0 || fov >= two_pi - 1e-9;
@@ -747,7 +760,7 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
                 else if (A == 1) a = 0.0;
                 else a = -0.5 * fov + ((double)k * fov) / (double)(A - 1);
                 cs[(size_t)hi.ray_off[e] + k] = make_float2((float)std::cos(a), (float)std::sin(a));
-                if (cfg->u_mode == ASLAM_U_SCANMATCH) {
+                if (soft_dirs(cfg)) {
                     // the soft range model of the in-step U walks the beam at
                     // its fp64 angle: (cos, sin) as hi + lo pairs of floats
                     const double ca = std::cos(a), sa = std::sin(a);
@@ -953,6 +966,7 @@ aslam_status aslam_get_state(aslam_batch *b, aslam_state_ptrs *o) {
     o->slam_match = p.csm_match;
     o->slam_scores = reinterpret_cast<int64_t *>(p.csm_scores);
     o->slam_match_pose = p.csm_pose;
+    o->slam_gn_pose = p.slam_gn_pose;
     return ASLAM_OK;
 }
 
@@ -1268,7 +1282,13 @@ const char *aslam_kernel_name(const aslam_batch *b, int32_t k) {
                                       "slam_predict2d_kernel", "csm2d_kernel",
                                       "slam_window2d_kernel", "slam_replan2d_kernel",
                                       "update2d_kernel"};
+    static const char *const k2g[] = {"sense2d_kernel",
+                                      "slam_predict2d_kernel", "csm2d_kernel",
+                                      "slam_correct2d_kernel", "slam_window2d_kernel",
+                                      "slam_replan2d_kernel", "update2d_kernel"};
     if (b->p.u_mode == ASLAM_U_SCANMATCH) return k < kStep2DKernels + 1 ? k2u[k] : nullptr;
+    if (b->p.u_mode == ASLAM_U_FIXEDLAG && b->p.slam_gn_iters > 0)
+        return k < kStep2DKernels + 5 ? k2g[k] : nullptr;
     if (b->p.u_mode == ASLAM_U_FIXEDLAG) return k < kStep2DKernels + 4 ? k2s[k] : nullptr;
     return k < kStep2DKernels ? k2[k] : nullptr;
 }

@@ -189,6 +189,8 @@ struct Step2DParams {
     float *csm_pose, *csm_match;                      // [E, 3]
     long long *csm_scores;                            // [E, 3]
     float *slam_upd_w;           // [E] this step's scan weight (u_mode 2)
+    int slam_gn_iters;           // scan-to-map Gauss-Newton steps on the match (0: none)
+    float *slam_gn_pose;         // [E, 3] the corrected match, the window's measurement
     const float *upd_w;          // per-env update weight, or null (unweighted)
     // per-env static description
     const int *W, *H, *B, *Vw, *Vh, *R8, *Dd;
@@ -245,7 +247,7 @@ float range_scale(int d);
 // Launchers (defined next to their kernels).
 // `ev` (optional) receives an event record before the first kernel and
 // after each kernel of the step: 4 events for 2-D, 2 for 3-D.
-constexpr int kStep2DKernels = 2, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1, +4 with u_mode 2
+constexpr int kStep2DKernels = 2, kStep3DKernels = 1;   // 2-D: +1 with u_mode 1, +4 with u_mode 2 (+5 with its correction)
 cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t smem,
                           cudaStream_t s, const cudaEvent_t *ev = nullptr);
 cudaError_t step2d_set_smem(size_t smem);

@@ -136,4 +136,94 @@ __device__ __forceinline__ void sigmoid_pq_accurate(float l, float &pr, float &q
     }
 }
 
+// ---------------------------------------------------------------------------
+// The model on an int16 log-odds belief (the in-step forms): the map as a
+// kernel reads it, bilinear taps, and one beam's range with its pose tangents.
+// ---------------------------------------------------------------------------
+struct Tap {
+    float l, gx, gy;       // log-odds (nats) and its gradient per metre
+};
+
+// The map as the kernel reads it: the whole env grid in global memory, or
+// the window [x0, x0+ww) x [y0, y0+wh) of it staged in shared memory.
+struct MapView {
+    const short *L;
+    int W, H, x0, y0, ww;
+};
+
+// Bilinear log-odds (nats) and gradient (per metre) at the sample whose
+// lower-left tap is (i0, j0) with fractions (ax, ay); taps clamped to the map.
+__device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, float scale, int i0,
+                                           int j0, float ax, float ay, Tap &t) {
+    const int ia = min(max(i0, 0), m.W - 1) - m.x0, ib = min(max(i0 + 1, 0), m.W - 1) - m.x0;
+    const int ja = min(max(j0, 0), m.H - 1) - m.y0, jb = min(max(j0 + 1, 0), m.H - 1) - m.y0;
+    const float l00 = (float)m.L[ja * m.ww + ia] * scale;
+    const float l10 = (float)m.L[ja * m.ww + ib] * scale;
+    const float l01 = (float)m.L[jb * m.ww + ia] * scale;
+    const float l11 = (float)m.L[jb * m.ww + ib] * scale;
+    t.l = (1.f - ax) * (1.f - ay) * l00 + ax * (1.f - ay) * l10 + (1.f - ax) * ay * l01 +
+          ax * ay * l11;
+    t.gx = ((1.f - ay) * (l10 - l00) + ay * (l11 - l01)) * inv_res;
+    t.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * inv_res;
+}
+
+// The double-float transmittance times one more factor q.
+__device__ __forceinline__ DF trans_mul_q(DF T, float q) {
+    const float p = __fmul_rn(T.hi, q);
+    const float l = __fmaf_rn(T.lo, q, __fmaf_rn(T.hi, q, -p));
+    const float h = __fadd_rn(p, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, p))};
+}
+
+// Kahan step: (r, c) <- r + y with the running compensation c.
+__device__ __forceinline__ void kahan_step(float &r, float &c, float y) {
+    const float yc = __fsub_rn(y, c);
+    const float t = __fadd_rn(r, yc);
+    c = __fsub_rn(__fsub_rn(t, r), yc);
+    r = t;
+}
+
+// Soft range of one beam on the belief view, and (J != nullptr) its
+// derivatives d r / d(x, y, th) by forward-mode tangents.  K samples of ds
+// metres; the range is summed with Kahan's compensation and the
+// transmittance carried as a double-float.
+__device__ __forceinline__ float soft_range_q(const MapView &m, float inv_res, float scale,
+                                             const SoftRay &ry, int K, float ds, float r_far,
+                                             float *J) {
+    DF T = {1.f, 0.f};
+    float r = 0.f, rc = 0.f;
+    float dT0 = 0.f, dT1 = 0.f, dT2 = 0.f, dr0 = 0.f, dr1 = 0.f, dr2 = 0.f;
+    Tap t;
+    for (int k = 0; k < K; ++k) {
+        const float sk = (float)(k + 1) * ds;
+        int i0, j0;
+        float ax, ay;
+        sample_coord(ry.iu, ry.fu, ry.du, (float)(k + 1), i0, ax);
+        sample_coord(ry.iv, ry.fv, ry.dv, (float)(k + 1), j0, ay);
+        bilinear_q(m, inv_res, scale, i0, j0, ax, ay, t);
+        float pr, q;
+        sigmoid_pq_accurate(t.l, pr, q);
+        kahan_step(r, rc, __fmul_rn(__fmul_rn(T.hi, pr), sk));
+        if (J) {
+            const float dpl = pr * q;
+            const float d0 = dpl * t.gx, d1 = dpl * t.gy;
+            const float d2 = dpl * (t.gx * (-sk * ry.sp) + t.gy * (sk * ry.cp));
+            dr0 += (dT0 * pr + T.hi * d0) * sk;
+            dr1 += (dT1 * pr + T.hi * d1) * sk;
+            dr2 += (dT2 * pr + T.hi * d2) * sk;
+            dT0 = dT0 * q - T.hi * d0;
+            dT1 = dT1 * q - T.hi * d1;
+            dT2 = dT2 * q - T.hi * d2;
+        }
+        T = trans_mul_q(T, q);
+    }
+    kahan_step(r, rc, __fmaf_rn(T.hi, r_far, T.lo * r_far));
+    if (J) {
+        J[0] = dr0 + dT0 * r_far;
+        J[1] = dr1 + dT1 * r_far;
+        J[2] = dr2 + dT2 * r_far;
+    }
+    return r;
+}
+
 }  // namespace aslam

@@ -1167,16 +1167,17 @@ cudaError_t launch_step2d(const Step2DParams &p, int grid, int block, size_t sme
         // the scan is then integrated at the optimised pose
         e = launch_slam2d(p, s, ev ? ev + 2 : nullptr);
         if (e != cudaSuccess) return e;
+        const int nb = p.slam_gn_iters > 0 ? 4 : 3;      // backbone kernels launched
         slam_replan2d_kernel<<<p.E, 128, 0, s>>>(p);
         e = cudaGetLastError();
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2 + nb], s);
         if (e != cudaSuccess) return e;
         Step2DParams q = p;
         q.u_in = p.u_scan;
         q.upd_w = p.slam_weighted ? p.slam_upd_w : nullptr;
         update<<<grid, block, smem, s>>>(q);
         e = cudaGetLastError();
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[6], s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3 + nb], s);
         return e;
     }
     if (p.u_mode == 1) {

@@ -37,41 +37,6 @@
 namespace aslam {
 namespace {
 
-struct Tap {
-    float l, gx, gy;       // log-odds (nats) and its gradient per metre
-};
-
-// The map as the kernel reads it: the whole env grid in global memory, or
-// the window [x0, x0+ww) x [y0, y0+wh) of it staged in shared memory.
-struct MapView {
-    const short *L;
-    int W, H, x0, y0, ww;
-};
-
-// Bilinear log-odds (nats) and gradient (per metre) at the sample whose
-// lower-left tap is (i0, j0) with fractions (ax, ay); taps clamped to the map.
-__device__ __forceinline__ void bilinear_q(const MapView &m, float inv_res, float scale, int i0,
-                                           int j0, float ax, float ay, Tap &t) {
-    const int ia = min(max(i0, 0), m.W - 1) - m.x0, ib = min(max(i0 + 1, 0), m.W - 1) - m.x0;
-    const int ja = min(max(j0, 0), m.H - 1) - m.y0, jb = min(max(j0 + 1, 0), m.H - 1) - m.y0;
-    const float l00 = (float)m.L[ja * m.ww + ia] * scale;
-    const float l10 = (float)m.L[ja * m.ww + ib] * scale;
-    const float l01 = (float)m.L[jb * m.ww + ia] * scale;
-    const float l11 = (float)m.L[jb * m.ww + ib] * scale;
-    t.l = (1.f - ax) * (1.f - ay) * l00 + ax * (1.f - ay) * l10 + (1.f - ax) * ay * l01 +
-          ax * ay * l11;
-    t.gx = ((1.f - ay) * (l10 - l00) + ay * (l11 - l01)) * inv_res;
-    t.gy = ((1.f - ax) * (l01 - l00) + ax * (l11 - l10)) * inv_res;
-}
-
-// The double-float transmittance times one more factor q.
-__device__ __forceinline__ DF trans_mul_q(DF T, float q) {
-    const float p = __fmul_rn(T.hi, q);
-    const float l = __fmaf_rn(T.lo, q, __fmaf_rn(T.hi, q, -p));
-    const float h = __fadd_rn(p, l);
-    return {h, __fsub_rn(l, __fsub_rn(h, p))};
-}
-
 __device__ __forceinline__ double det3d(const double *M) {
     return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
            M[2] * (M[3] * M[7] - M[4] * M[6]);

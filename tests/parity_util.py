@@ -37,7 +37,7 @@ def orc_params(cfg):
                  kappa="kappa", u_hi="u_hi", seed="seed", r_min_m="r_min",
                  range_decimals="decimals", slam_window="slam_window",
                  slam_iters="slam_iters", csm_n_xy="csm_n_xy", csm_n_th="csm_n_th",
-                 csm_sep="csm_sep", csm_dth_rad="csm_dth")
+                 csm_sep="csm_sep", csm_dth_rad="csm_dth", slam_gn_iters="slam_gn_iters")
     return {names[k]: v for k, v in cfg.items() if k in names}
 
 
