@@ -81,6 +81,36 @@ int near_radius(int B, double fov) {
     return 4096;
 }
 
+// 3-D: smallest Chebyshev distance d (>= 2) from the sensor's voxel beyond
+// which no voxel can be crossed by more than 255 of the rings x azimuths
+// beams.  A voxel at distance d has its centre >= d - 1/2 voxels from the
+// sensor and lies in a ball of radius sqrt(3)/2 about it, so every beam
+// crossing it is within alpha = asin(0.86603 / (d - 1/2)) of one direction,
+// and any two of them within 2 alpha of each other.  Two beams differ in
+// angle by at least their elevation difference, so they come from at most
+// floor(2 alpha / de) + 1 rings (de: ring spacing); two beams of one ring at
+// elevation e and azimuth difference dphi are 2 asin(cos(e) sin(dphi / 2))
+// apart, so one ring contributes at most floor(2 asin(sin(alpha) /
+// cos(e_abs)) / dphi_a) + 1 of them (e_abs: the largest |elevation|, dphi_a:
+// the azimuth spacing), +2e-6 rad for the fp32 direction rounding.
+int near_radius_3d(int A, int R, double el_min, double el_max) {
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const double dphi = two_pi / std::max(A, 1);
+    const double de = R > 1 ? (el_max - el_min) / (double)(R - 1) : 0.0;
+    const double cmin = std::cos(std::max(std::fabs(el_min), std::fabs(el_max)));
+    for (int d = 2; d < 4096; ++d) {
+        const double x = 0.86603 / ((double)d - 0.5);
+        if (x >= 1.0) continue;
+        const double alpha = std::asin(x) + 1e-6;
+        const long long rings = R > 1 ? std::min<long long>(R, (long long)std::floor(2.0 * alpha / de) + 1) : 1;
+        const double sa = std::sin(alpha) / cmin;
+        const long long az = sa >= 1.0 ? A
+                                        : std::min<long long>(A, (long long)std::floor((2.0 * std::asin(sa) + 2e-6) / dphi) + 1);
+        if (rings * az <= 255) return d;
+    }
+    return 4096;
+}
+
 bool validate(const aslam_config *c, std::string *msg) {
     auto fail = [&](const char *m) { *msg = m; return false; };
     if (!c) return fail("config is NULL");
@@ -213,7 +243,9 @@ void host_info(const aslam_config *c, HostInfo *hi) {
         visit_dims(hi->W[e], hi->H[e], c->res_m, c->visit_cell_m, &hi->Vw[e], &hi->Vh[e]);
         hi->visit_off[e + 1] = hi->visit_off[e] + (long long)hi->Vw[e] * hi->Vh[e];
         hi->gt_words_max = std::max(hi->gt_words_max, (int)words);
-        hi->R8[e] = c->dims == 3 ? 1 : near_radius(hi->B[e], (double)c->fov_rad);
+        hi->R8[e] = c->dims == 3 ? near_radius_3d(hi->B[e] / hi->n_rings, hi->n_rings,
+                                                  (double)c->elev_min_rad, (double)c->elev_max_rad)
+                                 : near_radius(hi->B[e], (double)c->fov_rad);
         hi->r8_max = std::max(hi->r8_max, hi->R8[e]);
     }
 }
@@ -433,9 +465,15 @@ int auto_window(const HostInfo &hi, int smem_optin, int clamp_q, int block) {
 aslam_status configure_launch(aslam_batch *b, int block, int S) {
     if (b->hi.dims == 3) {
         // voxel batches: ground-truth bits in shared memory, global counters
-        const size_t smem = 4 * (size_t)b->hi.gt_words_max;
+        // ground-truth bits, then the 32-bit near block (a cube of side 2R - 1)
+        const long long nb = 2LL * b->hi.r8_max - 1;
+        const long long near = nb * nb * nb;
+        if (nb > 31)
+            return fail_b(b, ASLAM_ERR_UNSUPPORTED, "beams too dense for the voxel near block");
+        const size_t smem = 4 * ((size_t)pad_to((size_t)b->hi.gt_words_max, 4) + pad_to((size_t)near, 4));
         if (smem + step3d_static_smem() > (size_t)b->smem_optin)
             return fail_b(b, ASLAM_ERR_UNSUPPORTED, "voxel map too large for shared memory");
+        b->p.near_words_max = (int)pad_to((size_t)near, 4);
         CK(step3d_set_smem(smem), "cudaFuncSetAttribute");
         int per_sm = 0;
         CK(step3d_occupancy(block, smem, &per_sm), "occupancy");

@@ -14,12 +14,18 @@
 //     floor(e / 2^16) (same sign; a term is ax ay (t_x - t_y) scaled, both
 //     next crossings within one interval, so it stays in [-2^30, 2^30]) and
 //     the voxel index in 32 bits (the ground truth fits shared memory);
-//   * counts go to global 32-bit (hits << 16 | misses) counters plus a
-//     bitmap of touched 8-voxel chunks.  The belief walk runs warp-
-//     synchronously: the 32 lanes of a warp are 32 adjacent azimuths of one
-//     ring, which cross the same voxels near the sensor, so adjacent lanes
-//     in the same voxel are merged into one atomic;
-//   * the CTA then applies the touched chunks and sums the entropy change.
+//   * counts: voxels within Chebyshev distance R - 1 of the sensor's voxel
+//     (R from the ring and azimuth spacing, computed on the host: beyond it
+//     no voxel is crossed by more than 255 beams) go to a 32-bit
+//     (hits << 16 | misses) block in shared memory; every other voxel to a
+//     global 16-bit (hits:8 | misses:8) counter, two per word, which never
+//     carries (half the L2 footprint of 32-bit counters), plus a bitmap of
+//     touched 8-voxel chunks.  The belief walk runs warp-synchronously: the 32
+//     lanes of a warp are 32 adjacent azimuths of one ring, which cross the
+//     same voxels near the sensor, so adjacent lanes in the same voxel are
+//     merged into one atomic;
+//   * the CTA then applies the touched chunks, then the near block, and sums
+//     the entropy change.
 #include "aslam_internal.cuh"
 #include "env_common.cuh"
 
@@ -27,7 +33,7 @@ namespace aslam {
 namespace {
 
 struct Env3 {
-    int e, W, H, Dd, B, A;
+    int e, W, H, Dd, B, A, R, NB;   // R: near radius (voxels), NB = 2R - 1
     int Px, Py, ri, rj, rk, col_cell;
     float c, s;
     long long map_off, gtb_off, ray_off, ncell;
@@ -102,6 +108,7 @@ __device__ __forceinline__ float ring_reach(const Step2DParams &p, int Dd, int r
 __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     unsigned *s_gt = smem;
+    unsigned *s_near = smem + ((p.gt_words_max + 3) & ~3);    // [NB^3], zero between envs
     __shared__ Env3 sh;
     __shared__ long long r_dh[32], r_rc[32], r_gc[32];
     __shared__ float r_dm[32], r_dt[32];
@@ -112,6 +119,7 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const bool debug = (p.flags & ASLAM_FLAG_DEBUG) != 0;
 
+    for (int q = tid; q < p.near_words_max; q += nt) s_near[q] = 0u;
     if (tid == 0) s_next = (int)atomicAdd(p.queue, 1u);
     for (;;) {
         __syncthreads();
@@ -137,6 +145,8 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
             sh.Dd = Dd;
             sh.B = p.B[e];
             sh.A = sh.B / p.n_rings;
+            sh.R = p.R8[e];
+            sh.NB = 2 * sh.R - 1;
             sh.map_off = p.map_off[e];
             sh.gtb_off = p.gtb_off[e];
             sh.ray_off = p.ray_off[e];
@@ -296,7 +306,8 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
             // atomic.  The touched-chunk bit is set only by a leader that has
             // just entered its 8-voxel chunk: the chunk of its previous voxel
             // was marked by the leader that counted that voxel one step
-            // earlier (and a walk's first voxel always marks).
+            // earlier (a walk's first voxel always marks, and so does the
+            // first far voxel after a near one: near voxels mark nothing).
             bool active = valid && in0;
             Walk3 w = w0;
             int s = 0, prev_chunk = -1;
@@ -313,6 +324,10 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                 const unsigned hits = __ballot_sync(0xffffffffu, last && hit);
                 if (active) {
                     const int chunk = w.flat >> 3;
+                    const int ni = w.i - sh.ri + sh.R - 1, nj = w.j - sh.rj + sh.R - 1,
+                              nk = w.k - sh.rk + sh.R - 1;
+                    const bool near = (unsigned)ni < (unsigned)sh.NB &&
+                                      (unsigned)nj < (unsigned)sh.NB && (unsigned)nk < (unsigned)sh.NB;
                     if (start) {
                         // the run: this lane up to the next start or inactive lane
                         const unsigned above = lane == 31 ? 0u : ~((2u << lane) - 1u);
@@ -320,11 +335,18 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                         const unsigned upto = stop ? (stop & (0u - stop)) - 1u : 0xffffffffu;
                         const unsigned run = upto & ~((1u << lane) - 1u);
                         const unsigned nh = __popc(hits & run), nm = __popc(run) - nh;
-                        red_add(&p.far_cnt[sh.map_off + w.flat], (nh << 16) | nm);
-                        if (chunk != prev_chunk)
-                            red_or(&p.far_bits[(sh.map_off + w.flat) >> 8], 1u << (chunk & 31));
+                        if (near) {
+                            atomicAdd(&s_near[(nk * sh.NB + nj) * sh.NB + ni], (nh << 16) | nm);
+                        } else {
+                            // 16-bit field (hits:8 | misses:8) of the voxel; map_off is even
+                            const long long v = sh.map_off + w.flat;
+                            red_add(&p.far_cnt[v >> 1], ((nh << 8) | nm) << ((v & 1) << 4));
+                            if (chunk != prev_chunk)
+                                red_or(&p.far_bits[v >> 8], 1u << (chunk & 31));
+                        }
                     }
-                    prev_chunk = chunk;
+                    // a near voxel marks nothing: the next far voxel of its chunk must
+                    prev_chunk = near ? -1 : chunk;
                     ++rc;
                     ++s;
                     if (last) active = false;
@@ -349,20 +371,41 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
                     const long long k = wq * 256 + bit * 8;
-                    uint4 *cp = reinterpret_cast<uint4 *>(p.far_cnt + sh.map_off + k);
-                    const uint4 c0 = __ldcg(cp), c1 = __ldcg(cp + 1);
-                    cp[0] = make_uint4(0u, 0u, 0u, 0u);
-                    cp[1] = make_uint4(0u, 0u, 0u, 0u);
+                    // eight 16-bit counters: 16 bytes, aligned (map_off and k are
+                    // multiples of 8)
+                    uint4 *cp = reinterpret_cast<uint4 *>(p.far_cnt + ((sh.map_off + k) >> 1));
+                    const uint4 cw = __ldcg(cp);
+                    *cp = make_uint4(0u, 0u, 0u, 0u);
                     int4 lv = *reinterpret_cast<const int4 *>(Lenv + k);
                     short *L = reinterpret_cast<short *>(&lv);
-                    const unsigned c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                    const unsigned c4[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        if (c[q]) dh += apply_cell3(p, L[q], c[q] >> 16, c[q] & 0xffffu);
-                        if (dbg) dbg[k + q] = c[q];
+                        const unsigned c = (c4[q >> 1] >> ((q & 1) << 4)) & 0xffffu;
+                        if (c) dh += apply_cell3(p, L[q], c >> 8, c & 0xffu);
+                        if (dbg) dbg[k + q] = ((c >> 8) << 16) | (c & 0xffu);
                     }
                     *reinterpret_cast<int4 *>(Lenv + k) = lv;
                 }
+            }
+        }
+        // the near block, after every far chunk (a chunk may hold voxels of both)
+        __syncthreads();
+        {
+            short *Lenv = p.belief + sh.map_off;
+            unsigned *dbg = debug ? p.dbg_counts + sh.map_off : nullptr;
+            const int nb = sh.NB, nb3 = nb * nb * nb;
+            for (int q = tid; q < nb3; q += nt) {
+                const unsigned c = s_near[q];
+                if (!c) continue;
+                s_near[q] = 0u;
+                const int ni = q % nb, nj = (q / nb) % nb, nk = q / (nb * nb);
+                const int i = sh.ri + ni - (sh.R - 1), j = sh.rj + nj - (sh.R - 1),
+                          k = sh.rk + nk - (sh.R - 1);
+                // counted voxels lie in the volume
+                const long long v = ((long long)k * H + j) * W + i;
+                dh += apply_cell3(p, Lenv[v], c >> 16, c & 0xffffu);
+                if (dbg) dbg[v] = c;
             }
         }
 
