@@ -352,6 +352,33 @@ __global__ void __launch_bounds__(1024, 1) step3d_kernel(const Step2DParams p) {
                     if (last) active = false;
                     else if (!step3(r, sh, w)) active = false;
                 }
+                // Merging pays while adjacent lanes share voxels (near the
+                // sensor); once the runs are most of the active lanes the warp
+                // stops merging, and every lane walks on alone.  The decision
+                // is uniform (it reads ballots only).
+                if (4 * __popc(starts) >= 3 * __popc(act)) break;
+            }
+            // each lane alone: one reduction per voxel; the chunk of a lane's
+            // previous voxel is marked (by its run's leader, or by this lane)
+            while (active) {
+                const bool last = s == Ku;
+                const int chunk = w.flat >> 3;
+                const int ni = w.i - sh.ri + sh.R - 1, nj = w.j - sh.rj + sh.R - 1,
+                          nk = w.k - sh.rk + sh.R - 1;
+                const bool near = (unsigned)ni < (unsigned)sh.NB &&
+                                  (unsigned)nj < (unsigned)sh.NB && (unsigned)nk < (unsigned)sh.NB;
+                const unsigned nh = last && hit ? 1u : 0u, nm = 1u - nh;
+                if (near) {
+                    atomicAdd(&s_near[(nk * sh.NB + nj) * sh.NB + ni], (nh << 16) | nm);
+                } else {
+                    const long long v = sh.map_off + w.flat;
+                    red_add(&p.far_cnt[v >> 1], ((nh << 8) | nm) << ((v & 1) << 4));
+                    if (chunk != prev_chunk) red_or(&p.far_bits[v >> 8], 1u << (chunk & 31));
+                }
+                prev_chunk = near ? -1 : chunk;
+                ++rc;
+                ++s;
+                if (last || !step3(r, sh, w)) active = false;
             }
         }
         __syncthreads();
