@@ -59,35 +59,29 @@ constexpr int kSenseSmemMax = 200 * 1024;   // ground truth of up to 1.6 M cells
 // largest; a counting sort writes the order (order within a class is
 // arbitrary: each env is still updated whole by exactly one CTA).  Run by one
 // CTA once every sensing CTA has added its cells.
-constexpr int kOrderSmem = 1024;  // envs whose costs are kept in shared memory
-
+// s_cost holds n_cost ints (the sensing CTA's ground-truth words, free once
+// its beams are walked); with more envs the costs are read from the L2 twice.
 __device__ void order_envs_by_cost(const Step2DParams &p, unsigned *s_hist, int *s_cost,
-                                   int *s_max) {
+                                   int n_cost, int *s_max) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const EnvSense *es = reinterpret_cast<const EnvSense *>(p.env_sense);
-    const bool staged = p.E <= kOrderSmem;
+    const bool staged = p.E <= n_cost;
     for (int q = tid; q < 256; q += nt) s_hist[q] = 0u;
     if (tid == 0) *s_max = 1;
     int m = 0;
-    if (staged && p.E <= 8 * nt) {
-        // every load of this thread in flight at once
+    for (int e0 = tid; e0 < p.E; e0 += 8 * nt) {
+        // eight loads of this thread in flight at once
         int c[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = tid + u * nt;
+            const int e = e0 + u * nt;
             c[u] = e < p.E ? __ldcg(&es[e].upd_cells) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = tid + u * nt;
-            if (e < p.E) s_cost[e] = c[u];
+            const int e = e0 + u * nt;
+            if (staged && e < p.E) s_cost[e] = c[u];
             m = max(m, c[u]);
-        }
-    } else {
-        for (int e = tid; e < p.E; e += nt) {
-            const int c = __ldcg(&es[e].upd_cells);
-            if (staged) s_cost[e] = c;
-            m = max(m, c);
         }
     }
     __syncthreads();
@@ -324,7 +318,6 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     // then fences (acquire), and the barrier after it extends that to the
     // whole CTA.
     __shared__ unsigned s_hist[256];
-    __shared__ int s_cost[kOrderSmem];
     __shared__ int s_max, s_last;
     __syncthreads();
     if (tid == 0) {
@@ -336,7 +329,8 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
     }
     __syncthreads();
     if (s_last) {
-        order_envs_by_cost(p, s_hist, s_cost, &s_max);
+        // the costs go to the ground-truth words (every walk of this CTA is done)
+        order_envs_by_cost(p, s_hist, reinterpret_cast<int *>(s_gt), p.gt_words_max, &s_max);
         if (tid == 0) p.queue[2] = 0u;
     }
 }
