@@ -11,14 +11,13 @@
 //   * the bilinear fraction of q_k: formed as x/res + s_k cos(phi)/res in
 //     fp32 it carries one ulp of the map coordinate (7.6e-6 cells at 128
 //     cells), and a log-odds step of 6 per cell turns that into 5e-5 in l.
-//     Here the origin's coordinate u0 = x/res - 1/2 is split in fp64 into an
-//     integer cell and a fraction once per beam, the per-sample step
-//     ds cos(phi)/res is a double-float (hi + lo) pair, and each sample's
-//     fraction is formed with the error-free TwoProd (FMA) and TwoSum of
-//     Dekker and Knuth: its error is one rounding of a number below 1;
+//     Here the origin u0 = x/res - 1/2 and the per-sample step ds cos(phi)/res
+//     are rounded once from fp64 to Q32.32 fixed point; a sample's position
+//     is the exact integer u0 + m du, so its fraction is one rounding of a
+//     number below 1 (and the origin and step add 2^-27 cells at most);
 //   * the direction: phi = th + beta rounded to fp32 moves a sample at
 //     3.2 m by ~3e-7 m; cos/sin of th (fp64, once per env) and of beta
-//     (fp64, once per beam) are combined by a double-float rotation;
+//     (fp64, once per beam) are rotated in fp64;
 //   * the sigmoid: exp and the reciprocal are the correctly rounded library
 //     forms (a few ulp), not the approximate intrinsics;
 //   * the sums: the range is summed with Kahan's compensation and the
@@ -70,56 +69,48 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 __device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
 
 // The geometry of one beam in the bilinear frame (u = x/res - 1/2, the
-// coordinate whose integer part is the lower-left tap's column).
+// coordinate whose integer part is the lower-left tap's column), in Q32.32
+// fixed point: sample m sits at u0 + m du exactly (integer arithmetic), so
+// its fraction is one rounding of a number below 1.  The origin and the
+// step are rounded once from fp64 (2^-33 cells each; 64 steps add 2^-27
+// cells).
 struct SoftRay {
-    int iu, iv;       // integer parts of the origin's u0, v0
-    float fu, fv;     // their fractions, in [0, 1)
-    DF du, dv;        // per-sample steps ds cos(phi)/res, ds sin(phi)/res
-    float cp, sp;     // cos(phi), sin(phi) in fp32 (the th tangent)
+    long long u0, v0;     // origin, Q32.32 cells
+    long long du, dv;     // per-sample steps ds cos(phi)/res, ds sin(phi)/res, Q32.32
+    float cp, sp;         // cos(phi), sin(phi) in fp32 (the th tangent)
 };
 
 // (ct, st) = cos/sin of the heading and (cb, sb) = cos/sin of the beam's
-// angle, each a double-float of its fp64 value; dsr = ds/res.
+// angle, each a double-float of its fp64 value; dsr = ds/res.  The
+// direction is rotated in fp64.
 __device__ __forceinline__ SoftRay soft_ray(double u0, double v0, DF ct, DF st, DF cb, DF sb,
                                             DF dsr) {
+    const double c = (double)ct.hi + (double)ct.lo, s = (double)st.hi + (double)st.lo;
+    const double cbd = (double)cb.hi + (double)cb.lo, sbd = (double)sb.hi + (double)sb.lo;
+    const double cphi = c * cbd - s * sbd, sphi = s * cbd + c * sbd;
+    const double d = (double)dsr.hi + (double)dsr.lo;
+    const double q32 = 4294967296.0;
     SoftRay r;
-    const double fu = floor(u0), fv = floor(v0);
-    r.iu = (int)fu;
-    r.iv = (int)fv;
-    r.fu = __double2float_rn(u0 - fu);
-    r.fv = __double2float_rn(v0 - fv);
-    if (r.fu >= 1.0f) { r.fu = 0.0f; r.iu += 1; }     // a fraction that rounds up to 1
-    if (r.fv >= 1.0f) { r.fv = 0.0f; r.iv += 1; }
-    const DF cphi = df_add(df_mul(ct, cb), df_neg(df_mul(st, sb)));
-    const DF sphi = df_add(df_mul(st, cb), df_mul(ct, sb));
-    r.du = df_mul(dsr, cphi);
-    r.dv = df_mul(dsr, sphi);
-    r.cp = cphi.hi;
-    r.sp = sphi.hi;
+    r.u0 = __double2ll_rn(u0 * q32);
+    r.v0 = __double2ll_rn(v0 * q32);
+    r.du = __double2ll_rn(d * cphi * q32);
+    r.dv = __double2ll_rn(d * sphi * q32);
+    r.cp = __double2float_rn(cphi);
+    r.sp = __double2float_rn(sphi);
     return r;
 }
 
-// Cell and fraction of the m-th sample along one axis: f0 + m * (d.hi +
-// d.lo) with m an exact integer; the fraction is one rounding of a number
-// in [0, 1).
-__device__ __forceinline__ void sample_coord(int i0, float f0, DF d, float m, int &cell,
+// Cell and fraction of the m-th sample along one axis: the Q32.32 position
+// u0 + m d, its integer part (floor) and its fraction in [0, 1).
+__device__ __forceinline__ void sample_coord(long long u0, long long d, int m, int &cell,
                                              float &frac) {
-    const float p = __fmul_rn(m, d.hi);
-    const float pe = __fmaf_rn(m, d.hi, -p);
-    const DF s = two_sum(f0, p);
-    const float lo = __fadd_rn(s.lo, __fmaf_rn(m, d.lo, pe));
-    const float fl = floorf(s.hi);
-    float fr = __fadd_rn(__fsub_rn(s.hi, fl), lo);     // s.hi - fl is exact
-    int c = (int)fl;
-    if (fr < 0.0f) {
-        fr = __fadd_rn(fr, 1.0f);
-        c -= 1;
-    } else if (fr >= 1.0f) {
-        fr = __fsub_rn(fr, 1.0f);
-        c += 1;
+    const long long u = u0 + (long long)m * d;
+    cell = (int)(u >> 32);
+    frac = __fmul_rn(__uint2float_rn((unsigned)u), 2.3283064365386963e-10f);   // 2^-32
+    if (frac >= 1.0f) {                  // a fraction that rounds up to 1
+        frac = 0.0f;
+        cell += 1;
     }
-    cell = i0 + c;
-    frac = fr;
 }
 
 // p = sigmoid(l) and q = 1 - p, each without cancellation, from the
@@ -198,8 +189,8 @@ __device__ __forceinline__ float soft_range_q(const MapView &m, float inv_res, f
         const float sk = (float)(k + 1) * ds;
         int i0, j0;
         float ax, ay;
-        sample_coord(ry.iu, ry.fu, ry.du, (float)(k + 1), i0, ax);
-        sample_coord(ry.iv, ry.fv, ry.dv, (float)(k + 1), j0, ay);
+        sample_coord(ry.u0, ry.du, k + 1, i0, ax);
+        sample_coord(ry.v0, ry.dv, k + 1, j0, ay);
         bilinear_q(m, inv_res, scale, i0, j0, ax, ay, t);
         float pr, q;
         sigmoid_pq_accurate(t.l, pr, q);

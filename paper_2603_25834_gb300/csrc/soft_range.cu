@@ -88,11 +88,10 @@ struct Sample {
 // fractions (ax, ay), taps clamped to the map.
 __device__ __forceinline__ void soft_sample(const SoftParams &p, const float *L, const SoftRay &ry,
                                             int k, Sample &s) {
-    const float m = (float)(k + 1);
     int i0, j0;
     float ax, ay;
-    sample_coord(ry.iu, ry.fu, ry.du, m, i0, ax);
-    sample_coord(ry.iv, ry.fv, ry.dv, m, j0, ay);
+    sample_coord(ry.u0, ry.du, k + 1, i0, ax);
+    sample_coord(ry.v0, ry.dv, k + 1, j0, ay);
     const int ia = min(max(i0, 0), p.W - 1), ib = min(max(i0 + 1, 0), p.W - 1);
     const int ja = min(max(j0, 0), p.H - 1), jb = min(max(j0 + 1, 0), p.H - 1);
     s.idx[0] = ja * p.W + ia;

@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(kUqBlockMax, 3) uq2d_kernel(const Step2DParams
                 const float sk = (float)(k + 1) * p.uq_ds;
                 int i0, j0;
                 float ax, ay;
-                sample_coord(ry.iu, ry.fu, ry.du, (float)(k + 1), i0, ax);
-                sample_coord(ry.iv, ry.fv, ry.dv, (float)(k + 1), j0, ay);
+                sample_coord(ry.u0, ry.du, k + 1, i0, ax);
+                sample_coord(ry.v0, ry.dv, k + 1, j0, ay);
                 bilinear_q(m, inv_res, scale, i0, j0, ax, ay, t);
                 float pr, q;
                 sigmoid_pq_accurate(t.l, pr, q);
