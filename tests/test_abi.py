@@ -136,3 +136,22 @@ def test_timeout_status_is_reserved(lib):
     for f in os.listdir(os.path.join(ROOT, "paper_2603_25834_gb300", "csrc")):
         src = open(os.path.join(ROOT, "paper_2603_25834_gb300", "csrc", f)).read()
         assert "return ASLAM_ERR_TIMEOUT" not in src and "kErrTimeout" not in src, f
+
+
+@pytest.mark.parametrize("iters", [-1, 11])
+def test_scan_to_map_iterations_out_of_range_are_rejected(lib, iters):
+    from paper_2603_25834_gb300 import aslam
+    c, keep = small_config(aslam, u_mode=aslam.U_FIXEDLAG, slam_gn_iters=iters)
+    n = C.c_size_t()
+    assert lib.aslam_workspace_bytes(C.byref(c), C.byref(n)) == 1
+    assert b"slam_gn_iters" in lib.aslam_last_error(None)
+
+
+def test_scan_to_map_correction_adds_its_workspace(lib):
+    from paper_2603_25834_gb300 import aslam
+    c0, keep0 = small_config(aslam, u_mode=aslam.U_FIXEDLAG)
+    c1, keep1 = small_config(aslam, u_mode=aslam.U_FIXEDLAG, slam_gn_iters=2)
+    n0, n1 = C.c_size_t(), C.c_size_t()
+    assert lib.aslam_workspace_bytes(C.byref(c0), C.byref(n0)) == 0
+    assert lib.aslam_workspace_bytes(C.byref(c1), C.byref(n1)) == 0
+    assert n1.value > n0.value          # the corrected poses and the beams' fp64 directions
