@@ -346,7 +346,7 @@ struct EnvShared {
     float c, s;
     long long map_off, ray_off;
     EnvStart start;
-    int gt_cells;
+    int gt_cells, upd_cells;     // this step's ground-truth and belief-walk cells
     float dmin_meas, dmin_true;
 };
 
@@ -566,6 +566,7 @@ __device__ __forceinline__ void load_env(const Step2DParams &p, int item, EnvSha
     sh.c = es.c;
     sh.s = es.s;
     sh.gt_cells = es.gt_cells;
+    sh.upd_cells = es.upd_cells;
     sh.dmin_meas = es.dmin_meas;
     sh.dmin_true = es.dmin_true;
     const int S = p.window;
@@ -692,20 +693,18 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         }
         if (debug)
             for (long long q = tid; q < ncell; q += nt) p.dbg_counts[sh.map_off + q] = 0u;
-        int ncells_sum = 0;
         for (int b = tid; b < B; b += nt) {
             const long long ray = sh.ray_off + b;
-            const int code = p.ray_code[ray];
-            s_code[b] = code;
+            s_code[b] = p.ray_code[ray];
             s_geo[b] = beam_dir(p, ray, sh.c, sh.s);
-            if (code >= 0) ncells_sum += (code & kCodeCells) + 1;
         }
-        int tot_cells;
-        block_exclusive_scan(ncells_sum, s_ws, &tot_cells);
         // chunk size: later chunks start >= ch >= 2*R8 steps out (after s
         // steps a walk is >= s/2 cells from the robot, outside the near
-        // block), and sum_b floor((n_b - 1) / ch) <= tot_cells / ch <= cap_map
-        const int ch = max(p.chunk, (tot_cells + cap_map - 1) / cap_map);
+        // block), and sum_b floor((n_b - 1) / ch) <= upd_cells / ch <= cap_map
+        // (upd_cells: the walks' total cells, summed by the sensing kernel, or
+        // by the re-planning kernel that rewrote the walk codes; the map
+        // writes below stay in bounds whatever it holds)
+        const int ch = max(p.chunk, (sh.upd_cells + cap_map - 1) / cap_map);
         // Later chunk m of a beam covers cells m*ch .. m*ch + ch - 1 of its
         // walk; all are full but possibly the last.  The map holds the full
         // ones first, then the short last ones, so that the two chunks a
@@ -726,10 +725,16 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             int tot;
             const int off = block_exclusive_scan(vf | (vs << 16), s_ws, &tot);
             const int of = nfull + (off & 0xffff), os = nshort + (off >> 16);
-            for (int m = 0; m < vf; ++m) s_list[of + m] = (unsigned)b | ((unsigned)(m + 1) << 16);
-            if (vs) s_list[cap_map - 1 - os] = (unsigned)b | ((unsigned)(vf + 1) << 16);
+            for (int m = 0; m < vf && of + m < cap_map; ++m)
+                s_list[of + m] = (unsigned)b | ((unsigned)(m + 1) << 16);
+            if (vs && os < cap_map) s_list[cap_map - 1 - os] = (unsigned)b | ((unsigned)(vf + 1) << 16);
             nfull += tot & 0xffff;
             nshort += tot >> 16;
+        }
+        if (nfull + nshort > cap_map) {            // uniform; impossible with a true upd_cells
+            if (tid == 0) atomicOr(p.err, kErrChecks);
+            nfull = min(nfull, cap_map);
+            nshort = min(nshort, cap_map - nfull);
         }
         __syncthreads();
         // entry q of the later chunks: the full ones from the bottom of the
@@ -958,6 +963,7 @@ __global__ void __launch_bounds__(128) slam_replan2d_kernel(const Step2DParams p
     const int W = p.W[e], H = p.H[e], B = p.B[e];
     const int i0 = Px >> 16, j0 = Py >> 16;
     const bool in0 = (unsigned)i0 < (unsigned)W && (unsigned)j0 < (unsigned)H;
+    int cells = 0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const long long ray = p.ray_off[e] + b;
         const int c0 = p.ray_code[ray];
@@ -970,15 +976,25 @@ __global__ void __launch_bounds__(128) slam_replan2d_kernel(const Step2DParams p
             const int Ku = crossings_le(bm.nx0, bm.adx, Tz) + crossings_le(bm.ny0, bm.ady, Tz);
             const int ncells = min(Ku + 1, nm);
             code = (ncells - 1) | ((ret && Ku < nm) ? kCodeHit : 0) | (ret ? kCodeRet : 0);
+            cells += ncells;
         }
         p.ray_code[ray] = code;
     }
+    // the re-planned walks' total cells, for the update kernel's chunk size
+    __shared__ int s_cells;
+    if (threadIdx.x == 0) s_cells = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cells += __shfl_down_sync(0xffffffffu, cells, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_cells, cells);
+    __syncthreads();
     if (threadIdx.x == 0) {
         EnvSense *esp = reinterpret_cast<EnvSense *>(p.env_sense) + e;
         esp->Px = Px;
         esp->Py = Py;
         esp->c = c;
         esp->s = sn;
+        esp->upd_cells = s_cells;
     }
 }
 
