@@ -800,21 +800,26 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                               : apply8<false>(p, s_lut, c, lv, nullptr, wgt);
                 *reinterpret_cast<int4 *>(Lenv + k) = lv;
             };
-            // scan: 8 chunks (16 counter words) per thread; the touched ones go
-            // to a compacted list (one shared atomic per warp).  Entries past
-            // the list's capacity are applied at once by the thread that found them.
-            for (int o0 = 32 * warp; 8 * o0 < nchunk; o0 += nt) {
-                const int o = o0 + lane;
+            // scan: a warp tests 256 chunks (128 16-byte counter words) per
+            // round, lane l the words 128 r + 32 v + l (v < 4): each load reads
+            // 32 consecutive words (no bank conflicts; with a lane's four words
+            // adjacent, each load hit two bank groups); bit 2v + h of a lane's
+            // mask is chunk 2 (128 r + 32 v + l) + h.  The touched ones go to a
+            // compacted list (one shared atomic per warp).  Entries past the
+            // list's capacity are applied at once by the thread that found them.
+            const uint4 *w4 = reinterpret_cast<const uint4 *>(s_win);
+            const int nw4 = (nchunk + 1) >> 1;           // 16-byte words holding counters
+            for (int r0 = 128 * warp; r0 < nw4; r0 += 4 * nt) {
                 unsigned mask = 0u;
-                if (8 * o < nchunk) {
-                    const uint4 *w4 = reinterpret_cast<const uint4 *>(s_win) + 4 * o;
-                    const uint4 a = w4[0], b2 = w4[1], c2 = w4[2], d2 = w4[3];
-                    mask = (unsigned)((a.x | a.y) != 0u) | ((unsigned)((a.z | a.w) != 0u) << 1) |
-                           ((unsigned)((b2.x | b2.y) != 0u) << 2) | ((unsigned)((b2.z | b2.w) != 0u) << 3) |
-                           ((unsigned)((c2.x | c2.y) != 0u) << 4) | ((unsigned)((c2.z | c2.w) != 0u) << 5) |
-                           ((unsigned)((d2.x | d2.y) != 0u) << 6) | ((unsigned)((d2.z | d2.w) != 0u) << 7);
-                    if (nchunk - 8 * o < 8) mask &= (1u << (nchunk - 8 * o)) - 1u;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int q4 = r0 + 32 * v + lane;
+                    if (q4 < nw4) {
+                        const uint4 a = w4[q4];
+                        mask |= ((unsigned)((a.x | a.y) != 0u) | ((unsigned)((a.z | a.w) != 0u) << 1)) << (2 * v);
+                    }
                 }
+                // (a chunk past nchunk has zero counters: nothing counts there)
                 const int cnt = __popc(mask);
                 int incl = cnt;
 #pragma unroll
@@ -829,8 +834,9 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                 while (mask) {
                     const int bit = __ffs(mask) - 1;
                     mask &= mask - 1u;
-                    if (pos < cap_list) lst[pos] = (unsigned short)(8 * o + bit);
-                    else apply_one(8 * o + bit);
+                    const int q = 2 * (r0 + 32 * (bit >> 1) + lane) + (bit & 1);
+                    if (pos < cap_list) lst[pos] = (unsigned short)q;
+                    else apply_one(q);
                     ++pos;
                 }
             }
