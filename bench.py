@@ -761,7 +761,10 @@ def main():
         "batched_4096": batched,
         "cpu_baseline": cpu,
         "e2e": {"value": E_all * K2 / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "aslam_step_host on page-locked host buffers: the step's kernels read the "
+                        "actions and U and write the reward and observation through the buffers' "
+                        "device mapping (NVLink-C2C), inside the timed region"},
         "graph": {"value": E_all / (g_ms / 1e3), "unit": UNIT, "steps": gk,
                   "ms_per_step": g_ms},
         "gpu_launches": K * len(kernel_ms),

@@ -267,13 +267,14 @@ aslam_status aslam_step_fused(aslam_batch *b, const float *d_actions, const floa
                               float *d_reward, float *d_obs, void *stream);
 
 /* aslam_step_fused from and to HOST memory: h_actions [E, 2] and h_u [E]
- * (may be NULL) are copied into a staging area of the workspace, the step
- * runs, and the reward [E] and observation [E, b_max+2] (either may be NULL)
- * are copied back, all in order on `stream`.  With page-locked host buffers
- * every copy is asynchronous and the results are valid once the stream has
- * been synchronised; with pageable memory the CUDA runtime may stage and
- * block.  The host buffers must stay valid until then.  Errors as
- * aslam_step_fused, plus ASLAM_ERR_CUDA for a failed copy. */
+ * (may be NULL) in, the reward [E] and observation [E, b_max+2] (either may
+ * be NULL) out, in order on `stream`.  A page-locked buffer (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) is read or written by the step's
+ * kernels in place, through its device mapping; any other buffer is copied
+ * through a staging area of the workspace (the CUDA runtime may then stage
+ * and block).  The results are valid once the stream has been synchronised,
+ * and the inputs must stay unchanged and every buffer valid until then.
+ * Errors as aslam_step_fused, plus ASLAM_ERR_CUDA for a failed copy. */
 aslam_status aslam_step_host(aslam_batch *b, const float *h_actions, const float *h_u,
                              float *h_reward, float *h_obs, void *stream);
 

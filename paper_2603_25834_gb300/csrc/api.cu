@@ -926,6 +926,18 @@ aslam_status aslam_step(aslam_batch *b, const float *d_actions, const float *d_u
     return aslam_step_fused(b, d_actions, d_u, nullptr, nullptr, stream);
 }
 
+// The device address of page-locked host memory (mapped into the device's
+// address space), or NULL for any other host memory.
+static float *mapped_host(const float *h) {
+    if (!h) return nullptr;
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<float *>(h), 0) != cudaSuccess) {
+        (void)cudaGetLastError();        // not page-locked: not an error of this call
+        return nullptr;
+    }
+    return static_cast<float *>(d);
+}
+
 aslam_status aslam_step_host(aslam_batch *b, const float *h_actions, const float *h_u,
                              float *h_reward, float *h_obs, void *stream) {
     if (!b) return fail_b(nullptr, ASLAM_ERR_INVALID_ARG, "batch is NULL");
@@ -934,18 +946,29 @@ aslam_status aslam_step_host(aslam_batch *b, const float *h_actions, const float
     const cudaStream_t s = (cudaStream_t)stream;
     float *d_in = at<float>(b, b->off.io_in);
     float *d_out = at<float>(b, b->off.io_out);
-    CK(cudaMemcpyAsync(d_in, h_actions, 8 * E, cudaMemcpyHostToDevice, s), "aslam_step_host: actions");
-    const float *d_u = nullptr;
-    if (h_u) {
+    // Page-locked buffers are read and written by the kernels in place (over
+    // NVLink-C2C on a Grace-Blackwell node): the inputs by one thread per
+    // sensing CTA and the finishing warp, the outputs as each kernel produces
+    // them, so no copy sits before or after the step.  Any other host memory
+    // goes through the workspace's staging arrays with copies.
+    const float *d_act = mapped_host(h_actions);
+    if (!d_act) {
+        CK(cudaMemcpyAsync(d_in, h_actions, 8 * E, cudaMemcpyHostToDevice, s), "aslam_step_host: actions");
+        d_act = d_in;
+    }
+    const float *d_u = mapped_host(h_u);
+    if (h_u && !d_u) {
         CK(cudaMemcpyAsync(d_in + 2 * E, h_u, 4 * E, cudaMemcpyHostToDevice, s), "aslam_step_host: U");
         d_u = d_in + 2 * E;
     }
-    const aslam_status st = aslam_step_fused(b, d_in, d_u, h_reward ? d_out : nullptr,
-                                             h_obs ? d_out + E : nullptr, stream);
+    float *m_reward = mapped_host(h_reward), *m_obs = mapped_host(h_obs);
+    const aslam_status st =
+        aslam_step_fused(b, d_act, d_u, h_reward ? (m_reward ? m_reward : d_out) : nullptr,
+                         h_obs ? (m_obs ? m_obs : d_out + E) : nullptr, stream);
     if (st != ASLAM_OK) return st;
-    if (h_reward)
+    if (h_reward && !m_reward)
         CK(cudaMemcpyAsync(h_reward, d_out, 4 * E, cudaMemcpyDeviceToHost, s), "aslam_step_host: reward");
-    if (h_obs)
+    if (h_obs && !m_obs)
         CK(cudaMemcpyAsync(h_obs, d_out + E, 4 * E * ((size_t)b->hi.b_max + 2), cudaMemcpyDeviceToHost, s),
            "aslam_step_host: obs");
     return ASLAM_OK;

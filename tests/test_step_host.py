@@ -2,8 +2,10 @@
 (aslam_step_fused): two batches built from the same seeded worlds and
 stepped with the same actions and U give bit-identical rewards,
 observations, reward terms and maps.  Every fourth step omits U and both
-outputs on both sides.  A device tensor passed as a host buffer is
-rejected by the binding."""
+outputs on both sides.  Page-locked host buffers are read and written by
+the kernels in place, pageable ones go through copies: both, and a mix of
+the two, are checked.  A device tensor passed as a host buffer is rejected
+by the binding."""
 import numpy as np
 import pytest
 import torch
@@ -13,7 +15,13 @@ from paper_2603_25834_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_host_step_matches_device_step(aslam_gpu):
+def _host(shape, pinned):
+    t = torch.empty(*shape)
+    return t.pin_memory() if pinned else t
+
+
+@pytest.mark.parametrize("mode", ["pinned", "pageable", "mixed"])
+def test_host_step_matches_device_step(aslam_gpu, mode):
     inp = synth.paper_scale(E=24, W=256, B=360, seed=2101)
     cfg = dict(r_max_m=12.0, noise_sigma_m=0.01, reward_mode=aslam_gpu.REWARD_COMPOSITE)
     gd = aslam_gpu.Batch2D(inp, **cfg)
@@ -23,10 +31,12 @@ def test_host_step_matches_device_step(aslam_gpu):
     uu = synth.random_uncertainty(12, E, 62)
     d_rew = torch.empty(E, device="cuda")
     d_obs = torch.empty(E, nb, device="cuda")
-    h_act = torch.empty(E, 2).pin_memory()
-    h_u = torch.empty(E).pin_memory()
-    h_rew = torch.empty(E).pin_memory()
-    h_obs = torch.empty(E, nb).pin_memory()
+    pin_in = mode in ("pinned", "mixed")
+    pin_out = mode == "pinned"
+    h_act = _host((E, 2), pin_in)
+    h_u = _host((E,), pin_in)
+    h_rew = _host((E,), pin_out)
+    h_obs = _host((E, nb), pin_out)
     for s in range(12):
         bare = s % 4 == 3
         h_act.copy_(torch.from_numpy(acts[s]))
