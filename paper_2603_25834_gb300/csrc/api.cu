@@ -445,11 +445,11 @@ int near_words(const HostInfo &hi) {
     return (int)pad_to((size_t)nb * nb, 4);
 }
 
-// Shared words of the update kernel's per-beam table (Q30 direction and
-// walk code), of its chunk map / touched-chunk list (4 words per thread),
+// Shared words of the update kernel's per-beam table (Q30 direction, walk
+// code and the walk's decision term at the origin), of its chunk map / touched-chunk list (4 words per thread),
 // and of the entropy half table (int64 per |L| = 0..clamp).
 int geo_words(const HostInfo &hi) {
-    return (int)(pad_to(2 * (size_t)hi.b_max, 4) + pad_to((size_t)hi.b_max, 4));
+    return (int)(pad_to(2 * (size_t)hi.b_max, 4) + 2 * pad_to((size_t)hi.b_max, 4));
 }
 int list_words(int block) { return 4 * block; }
 int lut_words(int clamp_q) { return (int)pad_to(2 * ((size_t)clamp_q + 1), 4); }

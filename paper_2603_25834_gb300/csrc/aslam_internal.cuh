@@ -220,7 +220,7 @@ struct Step2DParams {
     void *env_sense;             // [E] EnvSense: what the sensing kernel hands to the update kernel
     int chunk;                   // cells per update-walk chunk
     int lut_words;               // shared words of the entropy half table
-    int geo_words;               // shared words of the per-beam directions and walk codes
+    int geo_words;               // shared words of the per-beam directions, walk codes and h0
     int list_words;              // shared words of the chunk map / touched-chunk list
     const int2 *bundles;         // [n_bundles] (env, first beam) of each sensing CTA
     int n_bundles, sense_block;

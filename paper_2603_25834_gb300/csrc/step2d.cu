@@ -363,6 +363,61 @@ __device__ __forceinline__ Beam beam_of(const EnvShared &sh, int2 D) {
     return b;
 }
 
+// The walk geometry of a beam in 32-bit form: the step signs, |Dx| and |Dy|
+// (Q30, so |Dx| + |Dy| < 2^31), and h0 = floor(e0 / 2^16), e0 = nx0*ady -
+// ny0*adx the traversal's decision term at the origin.  The walk carries
+// h = floor(e / 2^16); after kx x-steps and ky y-steps e has grown by
+// (kx*ady - ky*adx) * 2^16, so h is exactly h0 + kx*ady - ky*adx, and the
+// m-th x-crossing comes strictly before the n-th y-crossing (e < 0 at
+// (m-1, n-1)) exactly when h0 + (m-1)*ady - (n-1)*adx < 0, since e's low
+// 16 bits lie in [0, 2^16).  A later chunk's start then takes 32 x 32-bit
+// products instead of the 64 x 64-bit ones of the Q16 form.
+struct BeamQ {
+    int sx, sy, adx, ady, h0;
+};
+
+__device__ __forceinline__ BeamQ beam_q(int2 D, int h0) {
+    BeamQ b;
+    b.sx = (D.x > 0) - (D.x < 0);
+    b.sy = (D.y > 0) - (D.y < 0);
+    b.adx = abs(D.x);
+    b.ady = abs(D.y);
+    b.h0 = h0;
+    return b;
+}
+
+// h0 of a beam from its Q30 direction and the env's origin.
+__device__ __forceinline__ int beam_h0(const EnvShared &sh, int2 D) {
+    const Beam b = beam_of(sh, D);
+    return dda_hi(b.nx0 * b.ady - b.ny0 * b.adx);
+}
+
+// Number of x-steps among the first s steps of the walk (the float estimate
+// of x_steps_after, fixed by the exact test above).
+__device__ __forceinline__ int x_steps_q(const BeamQ &b, int s) {
+    if (b.adx == 0) return 0;
+    if (b.ady == 0) return s;
+    auto x_first = [&](int m, int n) {
+        return (long long)b.h0 + (long long)(m - 1) * b.ady - (long long)(n - 1) * b.adx < 0;
+    };
+    int kx = __float2int_rd(__fdividef((float)s * (float)b.adx, (float)(b.adx + b.ady)));
+    kx = min(max(kx, 0), s);
+    if (kx == 0 || x_first(kx, s - kx + 1)) {
+        while (kx < s && x_first(kx + 1, s - kx)) ++kx;
+    } else {
+        do {
+            --kx;
+        } while (kx > 0 && !x_first(kx, s - kx + 1));
+    }
+    return kx;
+}
+
+// h after kx x-steps and ky y-steps of the walk.  On the walk h lies in
+// [-2^30, 2^30], so 32-bit wrap-around arithmetic gives it exactly.
+__device__ __forceinline__ int h_at(const BeamQ &b, int kx, int ky) {
+    return (int)((unsigned)b.h0 + (unsigned)kx * (unsigned)b.ady - (unsigned)ky * (unsigned)b.adx);
+}
+
 // Adds one hit or miss of cell (i, j) (flat k) to its counter.  kNear:
 // the cell may lie in the 32-bit block around the robot.  kChecks: a cell
 // outside the env's grid records kErrChecks and is skipped.
@@ -401,16 +456,16 @@ __device__ __forceinline__ void add_count(const Step2DParams &p, const EnvShared
 // walk, all in the map; the last one takes the hit of a returned beam).
 template <bool kPartial, bool kNear, bool kChecks>
 __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared &sh,
-                                          const Beam &bm, int code, int s0, int ch,
+                                          const BeamQ &bm, int code, int s0, int ch,
                                           unsigned *s_win, unsigned *s_near) {
     const int last = code & kCodeCells;              // index of the last cell
     const bool hit = (code & kCodeHit) != 0;
-    const int kx = s0 ? x_steps_after(bm, s0) : 0, ky = s0 - kx;
+    const int kx = s0 ? x_steps_q(bm, s0) : 0, ky = s0 - kx;
     const int W = sh.W;
     int i = sh.ri + bm.sx * kx, j = sh.rj + bm.sy * ky;
     int k = j * W + i;
-    int eh = dda_hi((bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx);
-    const int ady = (int)bm.ady, adx = (int)bm.adx;
+    int eh = h_at(bm, kx, ky);
+    const int ady = bm.ady, adx = bm.adx;
     const int syW = bm.sy * W;
     const int s_end = min(last, s0 + ch - 1);
     const bool hit_end = hit && s_end == last;
@@ -436,8 +491,8 @@ __device__ __forceinline__ int walk_chunk(const Step2DParams &p, const EnvShared
 // independent traversal chains (later chunks never touch the near block).
 template <bool kPartial, bool kChecks>
 __device__ __forceinline__ int walk_two(const Step2DParams &p, const EnvShared &sh,
-                                        const int2 *s_geo, const int *s_code, int ch,
-                                        unsigned ma, unsigned mb, unsigned *s_win) {
+                                        const int2 *s_geo, const int *s_code, const int *s_h0,
+                                        int ch, unsigned ma, unsigned mb, unsigned *s_win) {
     int nA = 0, nB = 0, kA = 0, kB = 0, eA = 0, eB = 0, iA = 0, iB = 0, jA = 0, jB = 0;
     int dxA = 0, dxB = 0, dyA = 0, dyB = 0, sxA = 0, sxB = 0, syA = 0, syB = 0, wA = 0, wB = 0;
     bool hA = false, hB = false;
@@ -448,15 +503,15 @@ __device__ __forceinline__ int walk_two(const Step2DParams &p, const EnvShared &
         const int b = (int)(m & 0xffffu), s0 = (int)(m >> 16) * ch;
         const int code = s_code[b];
         if (code < 0) return;
-        const Beam bm = beam_of(sh, s_geo[b]);
+        const BeamQ bm = beam_q(s_geo[b], s_h0[b]);
         const int last = code & kCodeCells;
-        const int kx = x_steps_after(bm, s0), ky = s0 - kx;
+        const int kx = x_steps_q(bm, s0), ky = s0 - kx;
         i = sh.ri + bm.sx * kx;
         j = sh.rj + bm.sy * ky;
         k = j * W + i;
-        eh = dda_hi((bm.nx0 + ((long long)kx << 16)) * bm.ady - (bm.ny0 + ((long long)ky << 16)) * bm.adx);
-        ady = (int)bm.ady;
-        adx = (int)bm.adx;
+        eh = h_at(bm, kx, ky);
+        ady = bm.ady;
+        adx = bm.adx;
         sx = bm.sx;
         sy = bm.sy;
         syW = bm.sy * W;
@@ -631,9 +686,10 @@ template <bool kChecks>
 __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p) {
     extern __shared__ __align__(16) unsigned smem[];
     long long *s_lut = reinterpret_cast<long long *>(smem);              // [clamp_q + 1]
-    const int geo_pad = (2 * p.b_max + 3) & ~3;
+    const int geo_pad = (2 * p.b_max + 3) & ~3, code_pad = (p.b_max + 3) & ~3;
     int2 *s_geo = reinterpret_cast<int2 *>(smem + p.lut_words);          // [b_max] (Dx, Dy)
     int *s_code = reinterpret_cast<int *>(smem + p.lut_words + geo_pad); // [b_max]
+    int *s_h0 = s_code + code_pad;                                       // [b_max]
     unsigned *s_list = smem + p.lut_words + p.geo_words;                 // [list_words]
     unsigned *s_win = s_list + p.list_words;
     unsigned *s_near = s_win + p.win_words_max;
@@ -696,7 +752,9 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         for (int b = tid; b < B; b += nt) {
             const long long ray = sh.ray_off + b;
             s_code[b] = p.ray_code[ray];
-            s_geo[b] = beam_dir(p, ray, sh.c, sh.s);
+            const int2 D = beam_dir(p, ray, sh.c, sh.s);
+            s_geo[b] = D;
+            s_h0[b] = beam_h0(sh, D);
         }
         // chunk size: later chunks start >= ch >= 2*R8 steps out (after s
         // steps a walk is >= s/2 cells from the robot, outside the near
@@ -757,7 +815,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             for (int b = tid; b < B; b += nwalk) {
                 const int code = s_code[b];
                 if (code < 0) continue;
-                const Beam bm = beam_of(sh, s_geo[b]);
+                const BeamQ bm = beam_q(s_geo[b], s_h0[b]);
                 rc += sh.partial ? walk_chunk<true, true, kChecks>(p, sh, bm, code, 0, ch, s_win, s_near)
                                  : walk_chunk<false, true, kChecks>(p, sh, bm, code, 0, ch, s_win, s_near);
             }
@@ -768,13 +826,13 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             for (int q = tid; q < nlater; q += per * nwalk) {
                 if (per == 2) {
                     const unsigned mb = q + nwalk < nlater ? later(q + nwalk) : ~0u;
-                    rc += walk_two<false, kChecks>(p, sh, s_geo, s_code, ch, later(q), mb, s_win);
+                    rc += walk_two<false, kChecks>(p, sh, s_geo, s_code, s_h0, ch, later(q), mb, s_win);
                 } else {
                     const unsigned m = later(q);
                     const int b = (int)(m & 0xffffu), s0 = (int)(m >> 16) * ch;
                     const int code = s_code[b];
                     if (code < 0) continue;
-                    const Beam bm = beam_of(sh, s_geo[b]);
+                    const BeamQ bm = beam_q(s_geo[b], s_h0[b]);
                     rc += walk_chunk<true, false, kChecks>(p, sh, bm, code, s0, ch, s_win, s_near);
                 }
             }
