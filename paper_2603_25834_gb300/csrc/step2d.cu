@@ -672,9 +672,10 @@ __device__ __forceinline__ long long chunk_cell(const EnvShared &sh, int q) {
 //          later chunks fit the chunk map); the map of later chunks (beam,
 //          index), beam-major;
 //   walk   the first chunks (one per beam), then the later chunks from the
-//          map, two per thread walked together (two independent traversal
-//          chains per thread; the map lists full chunks before the short
-//          last ones so that pairs match in length);
+//          map, claimed 64 entries per warp from a shared counter and walked
+//          two per lane together (two independent traversal chains per
+//          thread; the map lists full chunks before the short last ones so
+//          that pairs match in length);
 //   apply  every thread tests 8 chunks of counters (four 16-byte loads) and
 //          appends the touched ones to a compacted list (one shared atomic per
 //          warp; past the list's capacity a thread applies its chunk at once);
@@ -700,6 +701,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     __shared__ int s_rc;
     __shared__ int s_ws[33];                     // block scans
     __shared__ int s_ln[1];                      // touched-list length
+    __shared__ int s_next;                       // next unclaimed later-chunk entry
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -740,7 +742,10 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         const int e = sh.e, W = sh.W, H = sh.H, B = sh.B;
         const long long ncell = (long long)W * H;
         const int nch = (int)((ncell + 7) >> 3);
-        if (tid == 0) s_ln[0] = 0;
+        if (tid == 0) {
+            s_ln[0] = 0;
+            s_next = 0;
+        }
         if (sh.reset) {
             int4 *bz = reinterpret_cast<int4 *>(p.belief + sh.map_off);
             for (int q = tid; q < nch; q += nt) bz[q] = make_int4(0, 0, 0, 0);
@@ -819,13 +824,23 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
                 rc += sh.partial ? walk_chunk<true, true, kChecks>(p, sh, bm, code, 0, ch, s_win, s_near)
                                  : walk_chunk<false, true, kChecks>(p, sh, bm, code, 0, ch, s_win, s_near);
             }
-            // later chunks: two per thread walked together when the map sits
-            // whole in shared memory; one at a time in a windowed map, where
-            // every cell also tests the window
+            // later chunks: a warp claims 32 * per map entries at a time from
+            // a shared counter, so that the warps that walked fewer first
+            // chunks take more.  Two per lane walked together when the map sits
+            // whole in shared memory (entries base + 2l, base + 2l + 1: the map
+            // lists full chunks before short ones, so a pair mostly matches in
+            // length); one per lane in a windowed map, where every cell also
+            // tests the window
             const int per = sh.partial ? 1 : 2;
-            for (int q = tid; q < nlater; q += per * nwalk) {
+            for (;;) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_next, 32 * per);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= nlater) break;                   // uniform over the warp
+                const int q = base + per * lane;
+                if (q >= nlater) continue;
                 if (per == 2) {
-                    const unsigned mb = q + nwalk < nlater ? later(q + nwalk) : ~0u;
+                    const unsigned mb = q + 1 < nlater ? later(q + 1) : ~0u;
                     rc += walk_two<false, kChecks>(p, sh, s_geo, s_code, s_h0, ch, later(q), mb, s_win);
                 } else {
                     const unsigned m = later(q);
