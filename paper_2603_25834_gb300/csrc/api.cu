@@ -773,11 +773,12 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.far_bits = at<unsigned>(b, o.far_bits);
         p.ray_code = at<int>(b, o.ray_code);
         p.env_sense = at<void>(b, o.env_sense);
-        // later chunks must start outside the near block: chunk >= 2*R8.
-        // 16 cells balance the walking threads best (timed: 8 / 12 / 16 /
-        // 24 / 32 / 48 cells -> 81.9 / 81.7 / 80.6 / 82.4 / 84.0 / 89.0 us
-        // of update2d at 750 paper-scale envs)
-        p.chunk = std::max(16, 2 * hi.r8_max);
+        // the smallest chunk; an env's later chunks must also start outside
+        // its near block, so the kernel takes at least 2*R8 of the env.  16
+        // cells balance the walking threads best (timed: 8 / 12 / 16 / 24 /
+        // 32 / 48 cells -> 81.9 / 81.7 / 80.6 / 82.4 / 84.0 / 89.0 us of
+        // update2d at 750 paper-scale envs)
+        p.chunk = 16;
         p.queue = at<unsigned>(b, o.queue);
         p.err = at<unsigned>(b, o.err);
 

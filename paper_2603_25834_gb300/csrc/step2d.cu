@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         // (upd_cells: the walks' total cells, summed by the sensing kernel, or
         // by the re-planning kernel that rewrote the walk codes; the map
         // writes below stay in bounds whatever it holds)
-        const int ch = max(p.chunk, (sh.upd_cells + cap_map - 1) / cap_map);
+        const int ch = max(max(p.chunk, 2 * sh.R8), (sh.upd_cells + cap_map - 1) / cap_map);
         // Later chunk m of a beam covers cells m*ch .. m*ch + ch - 1 of its
         // walk; all are full but possibly the last.  The map holds the full
         // ones first, then the short last ones, so that the two chunks a
