@@ -774,11 +774,11 @@ aslam_status aslam_create_batch(const aslam_config *cfg, void *d_workspace, size
         p.ray_code = at<int>(b, o.ray_code);
         p.env_sense = at<void>(b, o.env_sense);
         // the smallest chunk; an env's later chunks must also start outside
-        // its near block, so the kernel takes at least 2*R8 of the env.  16
-        // cells balance the walking threads best (timed: 8 / 12 / 16 / 24 /
-        // 32 / 48 cells -> 81.9 / 81.7 / 80.6 / 82.4 / 84.0 / 89.0 us of
-        // update2d at 750 paper-scale envs)
-        p.chunk = 16;
+        // its near block, so the kernel takes at least 2*R8 of the env.
+        // Timed with the later chunks claimed per warp: a floor of 12 / 16 /
+        // 20 cells -> step 0.1157 / 0.1164 / 0.1172 ms at 750 paper-scale
+        // envs, 0.6410 / 0.6407 / 0.6421 ms at 4096 uneven envs
+        p.chunk = 12;
         p.queue = at<unsigned>(b, o.queue);
         p.err = at<unsigned>(b, o.err);
 
