@@ -774,8 +774,16 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         // thread walks together (entries q and q + nwalk) mostly match in
         // length.  One scan of (full count | short flag << 16) places both.
         int nfull = 0, nshort = 0;
+        // The map lists the beams by a stride coprime with B (slot t holds
+        // beam t * stride mod B), so that the entries a warp claims together
+        // are chunks of beams far apart: adjacent beams at the same chunk
+        // index hit the same counter words at the same time, and the walk's
+        // shared atomics serialised on them.  The slots read the codes of
+        // other threads' beams, hence the barrier.
+        const int bstride = B % 97 ? 97 : (B % 89 ? 89 : 1);
+        __syncthreads();
         for (int b0 = 0; b0 < B; b0 += nt) {
-            const int b = b0 + tid;
+            const int b = b0 + tid < B ? (int)(((long long)(b0 + tid) * bstride) % B) : b0 + tid;
             int vf = 0, vs = 0;
             if (b < B) {
                 const int code = s_code[b];
