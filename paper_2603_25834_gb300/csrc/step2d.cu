@@ -392,8 +392,9 @@ __device__ __forceinline__ int beam_h0(const EnvShared &sh, int2 D) {
     return dda_hi(b.nx0 * b.ady - b.ny0 * b.adx);
 }
 
-// Number of x-steps among the first s steps of the walk (the float estimate
-// of x_steps_after, fixed by the exact test above).
+// Number of x-steps among the first s steps of the walk: a float estimate
+// (relative error ~2^-22, so within a step or two), fixed by the exact test
+// above.
 __device__ __forceinline__ int x_steps_q(const BeamQ &b, int s) {
     if (b.adx == 0) return 0;
     if (b.ady == 0) return s;
@@ -402,6 +403,9 @@ __device__ __forceinline__ int x_steps_q(const BeamQ &b, int s) {
     };
     int kx = __float2int_rd(__fdividef((float)s * (float)b.adx, (float)(b.adx + b.ady)));
     kx = min(max(kx, 0), s);
+    // kx is the largest value whose kx-th x-crossing precedes the
+    // (s-kx+1)-th y-crossing (ties go Y first, as in the walk); that
+    // predicate falls from true to false as kx grows
     if (kx == 0 || x_first(kx, s - kx + 1)) {
         while (kx < s && x_first(kx + 1, s - kx)) ++kx;
     } else {
@@ -695,10 +699,8 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
     unsigned *s_win = s_list + p.list_words;
     unsigned *s_near = s_win + p.win_words_max;
     __shared__ EnvShared shb[2];
-    __shared__ long long r_dh[32];
-    __shared__ int r_rc[32];
-    __shared__ long long s_dHq;
-    __shared__ int s_rc;
+    __shared__ long long r_dh[32];               // per-warp partial sums of the env's ...
+    __shared__ int r_rc[32];                     // ... entropy change and walk cells
     __shared__ int s_ws[33];                     // block scans
     __shared__ int s_ln[1];                      // touched-list length
     __shared__ int s_next;                       // next unclaimed later-chunk entry
@@ -730,6 +732,16 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         for (int q = tid; q < (p.win_words_max >> 2); q += nt) wz[q] = make_uint4(0, 0, 0, 0);
         for (int q = tid; q < p.near_words_max; q += nt) s_near[q] = 0u;
     }
+    // the finished env's totals from the warps' partial sums (one thread)
+    auto finish_prev = [&](const EnvShared &done) {
+        long long a = 0;
+        int c = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            a += r_dh[w];
+            c += r_rc[w];
+        }
+        finish_pending(p, done, a, c);
+    };
     pdl_wait();                          // the sensing kernel's ray codes are complete
     if (tid == 0) load_env(p, (int)atomicAdd(p.queue, 1u), shb[0]);
     __syncthreads();
@@ -817,7 +829,7 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         int rc = 0;
         if (control) {
             if (lane == 0) {
-                if (it > 0) finish_pending(p, shb[(it - 1) & 1], s_dHq, s_rc);
+                if (it > 0) finish_prev(shb[(it - 1) & 1]);
                 load_env(p, (int)atomicAdd(p.queue, 1u), shb[(it + 1) & 1]);
             }
         } else {
@@ -996,21 +1008,13 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
             float *o = p.out_obs + (long long)e * (p.b_max + 2);
             for (int b = B + tid; b < p.b_max; b += nt) o[b] = p.r_max;
         }
+        // r_dh/r_rc and shb[(it+1)&1] visible.  The control warp sums the
+        // partials during the next walk, before any warp writes them again
+        // (after that walk's barrier).
         __syncthreads();
-        if (tid == 0) {
-            long long a = 0;
-            int c = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                a += r_dh[w];
-                c += r_rc[w];
-            }
-            s_dHq = a;
-            s_rc = c;
-        }
-        __syncthreads();                 // s_dHq/s_rc and shb[(it+1)&1] visible
     }
     if (tid == 0) {
-        if (it > 0) finish_pending(p, shb[(it - 1) & 1], s_dHq, s_rc);
+        if (it > 0) finish_prev(shb[(it - 1) & 1]);
         // Every CTA took exactly one out-of-range item; the last CTA to leave
         // re-arms the queue for the next launch.
         __threadfence();

@@ -1,6 +1,6 @@
 // walk2d.cuh -- device helpers of the 2-D step kernels: the exact
 // fixed-point beam geometry (Q16 origin, Q30 direction, the walk's in-map
-// length and the jump to its s-th step), the walk code handed from sensing to
+// length), the walk code handed from sensing to
 // the update, ground-truth bit tests, L2 prefetch, programmatic dependent
 // launch, and the per-cell log-odds apply with its entropy change.
 #pragma once
@@ -118,29 +118,6 @@ __device__ __forceinline__ int cells_in_map(const Beam &b, int i0, int j0, int W
     const long long D = NY * b.adx - b.nx0 * b.ady;
     const long long cx = D <= 0 ? 0 : floor_div_q16(D - 1, b.ady) + 1;
     return ry + (int)cx + 1;
-}
-
-// Is the m-th x-crossing (m >= 1) strictly earlier than the n-th
-// y-crossing (n >= 1)?  Ties are taken Y first, as in the walk.
-__device__ __forceinline__ bool x_before_y(const Beam &b, int m, int n) {
-    return (b.nx0 + ((long long)(m - 1) << 16)) * b.ady <
-           (b.ny0 + ((long long)(n - 1) << 16)) * b.adx;
-}
-
-// Number of x-crossings among the first s crossings of the walk.
-__device__ __forceinline__ int x_steps_after(const Beam &b, int s) {
-    if (b.adx == 0) return 0;
-    if (b.ady == 0) return s;
-    int kx = __float2int_rd(__fdividef((float)s * (float)(int)b.adx, (float)(int)(b.adx + b.ady)));
-    kx = min(max(kx, 0), s);
-    // kx is the largest value whose kx-th x-crossing precedes the
-    // (s-kx+1)-th y-crossing; that predicate falls from true to false
-    if (kx == 0 || x_before_y(b, kx, s - kx + 1)) {
-        while (kx < s && x_before_y(b, kx + 1, s - kx)) ++kx;
-    } else {
-        do { --kx; } while (kx > 0 && !x_before_y(b, kx, s - kx + 1));
-    }
-    return kx;
 }
 
 // Entropy of log-odds L in 2^-40 nats from the half table h(|L|) (h is even).
