@@ -54,6 +54,17 @@ def test_paper_scale_small_batch(aslam_gpu, orc):
                noise_sigma_m=0.01)
 
 
+@pytest.mark.parametrize("B", [97, 194])
+def test_beam_counts_with_the_fallback_map_stride(aslam_gpu, orc, B):
+    """The update kernel lists an env's beams in its chunk map by a stride
+    coprime with B: 97, or 89 when 97 divides B.  Beam counts that take the
+    fallback stride, bit-exact against the oracle."""
+    inp = synth.paper_scale(E=4, B=B, seed=4242)
+    acts = synth.random_actions(6, 4, 43)
+    run_parity(aslam_gpu, orc, inp, acts, tag="stride-B%d" % B, r_max_m=12.0,
+               noise_sigma_m=0.01)
+
+
 @pytest.mark.parametrize("window,threads", [(64, 128), (128, 160), (200, 256)])
 def test_partial_window_and_global_counters(aslam_gpu, orc, window, threads):
     inp = synth.paper_scale(E=4, seed=777)

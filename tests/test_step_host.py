@@ -20,7 +20,7 @@ def _host(shape, pinned):
     return t.pin_memory() if pinned else t
 
 
-@pytest.mark.parametrize("mode", ["pinned", "pageable", "mixed"])
+@pytest.mark.parametrize("mode", ["pinned", "pageable", "mixed", "outputs-pinned"])
 def test_host_step_matches_device_step(aslam_gpu, mode):
     inp = synth.paper_scale(E=24, W=256, B=360, seed=2101)
     cfg = dict(r_max_m=12.0, noise_sigma_m=0.01, reward_mode=aslam_gpu.REWARD_COMPOSITE)
@@ -32,7 +32,7 @@ def test_host_step_matches_device_step(aslam_gpu, mode):
     d_rew = torch.empty(E, device="cuda")
     d_obs = torch.empty(E, nb, device="cuda")
     pin_in = mode in ("pinned", "mixed")
-    pin_out = mode == "pinned"
+    pin_out = mode in ("pinned", "outputs-pinned")
     h_act = _host((E, 2), pin_in)
     h_u = _host((E,), pin_in)
     h_rew = _host((E,), pin_out)
