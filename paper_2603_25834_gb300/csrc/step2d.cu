@@ -671,10 +671,10 @@ __device__ __forceinline__ long long chunk_cell(const EnvShared &sh, int q) {
 // of a two-slot shared buffer, so neither serial step delays the CTA.
 //
 // Per env:
-//   table  every beam's Q30 direction and walk code into shared memory; the
+//   table  every beam's Q30 direction, walk code and h0 into shared memory; the
 //          env's chunk size (at least p.chunk, and large enough that its
 //          later chunks fit the chunk map); the map of later chunks (beam,
-//          index), beam-major;
+//          index), grouped by beam, the beams in a stride order;
 //   walk   the first chunks (one per beam), then the later chunks from the
 //          map, claimed 64 entries per warp from a shared counter and walked
 //          two per lane together (two independent traversal chains per
