@@ -782,9 +782,9 @@ __global__ void __launch_bounds__(1024, 1) update2d_kernel(const Step2DParams p)
         const int ch = max(max(p.chunk, 2 * sh.R8), (sh.upd_cells + cap_map - 1) / cap_map);
         // Later chunk m of a beam covers cells m*ch .. m*ch + ch - 1 of its
         // walk; all are full but possibly the last.  The map holds the full
-        // ones first, then the short last ones, so that the two chunks a
-        // thread walks together (entries q and q + nwalk) mostly match in
-        // length.  One scan of (full count | short flag << 16) places both.
+        // ones first, then the short last ones, so that the two chunks a lane
+        // walks together (consecutive entries) mostly match in length.  One
+        // scan of (full count | short flag << 16) places both.
         int nfull = 0, nshort = 0;
         // The map lists the beams by a stride coprime with B (slot t holds
         // beam t * stride mod B), so that the entries a warp claims together
