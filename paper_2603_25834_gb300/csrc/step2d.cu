@@ -162,7 +162,20 @@ __global__ void __launch_bounds__(256) sense2d_kernel(const Step2DParams p) {
         }
         const uint4 *src = reinterpret_cast<const uint4 *>(p.gt_bits + p.gtb_off[e]);
         uint4 *dst = reinterpret_cast<uint4 *>(s_gt);
-        for (int q = tid; q < (words + 3) >> 2; q += blockDim.x) dst[q] = __ldg(&src[q]);
+        const int n4 = (words + 3) >> 2, nt = blockDim.x;
+        if (n4 <= 2 * nt) {
+            // at most two words per thread: both loads in flight before the
+            // stores (750 paper-scale envs -1 %; with larger grids, two or four
+            // loads at a time were slower than the plain loop below)
+            uint4 v0, v1;
+            const bool a = tid < n4, b = tid + nt < n4;
+            if (a) v0 = __ldg(&src[tid]);
+            if (b) v1 = __ldg(&src[tid + nt]);
+            if (a) dst[tid] = v0;
+            if (b) dst[tid + nt] = v1;
+        } else {
+            for (int q = tid; q < n4; q += nt) dst[q] = __ldg(&src[q]);
+        }
     }
     __syncthreads();
     if (tid == itid && bundle.y == 0) {
