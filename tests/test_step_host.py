@@ -4,8 +4,8 @@ stepped with the same actions and U give bit-identical rewards,
 observations, reward terms and maps.  Every fourth step omits U and both
 outputs on both sides.  Page-locked host buffers are read and written by
 the kernels in place, pageable ones go through copies: both, and a mix of
-the two, are checked.  A device tensor passed as a host buffer is rejected
-by the binding."""
+the two, are checked, for a 2-D batch and for a voxel batch.  A device
+tensor passed as a host buffer is rejected by the binding."""
 import numpy as np
 import pytest
 import torch
@@ -58,5 +58,33 @@ def test_host_step_matches_device_step(aslam_gpu, mode):
                                           err_msg="%s step %d" % (k, s))
     with pytest.raises(aslam_gpu.AslamError):
         gh.step_host(torch.zeros(E, 2, device="cuda"))
+    gd.close()
+    gh.close()
+
+
+def test_voxel_host_step_matches_device_step(aslam_gpu):
+    """The 3-D step writes its reward and observation through the same
+    pointers: page-locked host buffers in place against device buffers."""
+    inp = synth.voxel_batch(E=3, W=32, H=32, D=8, n_az=24, K=4, seed=2102)
+    cfg = dict(n_rings=4, reward_mode=aslam_gpu.REWARD_COMPOSITE)
+    gd = aslam_gpu.Batch2D(inp, **cfg)
+    gh = aslam_gpu.Batch2D(inp, **cfg)
+    E, nb = inp.n_envs, gd.b_max + 2
+    acts = synth.random_actions(6, E, 63)
+    uu = synth.random_uncertainty(6, E, 64)
+    d_rew = torch.empty(E, device="cuda")
+    d_obs = torch.empty(E, nb, device="cuda")
+    h_act, h_u = torch.empty(E, 2).pin_memory(), torch.empty(E).pin_memory()
+    h_rew, h_obs = torch.empty(E).pin_memory(), torch.empty(E, nb).pin_memory()
+    for s in range(6):
+        h_act.copy_(torch.from_numpy(acts[s]))
+        h_u.copy_(torch.from_numpy(uu[s]))
+        gd.step_fused(torch.from_numpy(acts[s]).cuda(), torch.from_numpy(uu[s]).cuda(), d_rew, d_obs)
+        gh.step_host(h_act, h_u, h_rew, h_obs)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(h_rew.numpy(), d_rew.cpu().numpy(), err_msg="reward %d" % s)
+        np.testing.assert_array_equal(h_obs.numpy(), d_obs.cpu().numpy(), err_msg="obs %d" % s)
+        np.testing.assert_array_equal(gd.state()["belief"].cpu().numpy(),
+                                      gh.state()["belief"].cpu().numpy(), err_msg="belief %d" % s)
     gd.close()
     gh.close()
