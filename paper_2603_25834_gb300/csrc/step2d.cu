@@ -685,8 +685,9 @@ __device__ __forceinline__ long long chunk_cell(const EnvShared &sh, int q) {
 //
 // Per env:
 //   table  every beam's Q30 direction, walk code and h0 into shared memory; the
-//          env's chunk size (at least p.chunk, and large enough that its
-//          later chunks fit the chunk map); the map of later chunks (beam,
+//          env's chunk size (at least p.chunk and twice the env's near
+//          radius, and large enough that its later chunks fit the chunk
+//          map); the map of later chunks (beam,
 //          index), grouped by beam, the beams in a stride order;
 //   walk   the first chunks (one per beam), then the later chunks from the
 //          map, claimed 64 entries per warp from a shared counter and walked
