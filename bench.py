@@ -55,10 +55,12 @@ WORKLOAD = dict(workload="paper_scale: 750 envs x 256^2 cells @0.05 m, 360 beams
 KERNEL_SOURCES = {"2d": ["paper_2603_25834_gb300/csrc/step2d.cu",
                          "paper_2603_25834_gb300/csrc/walk2d.cuh",
                          "paper_2603_25834_gb300/csrc/aslam_internal.cuh",
-                         "paper_2603_25834_gb300/csrc/env_common.cuh"],
+                         "paper_2603_25834_gb300/csrc/env_common.cuh",
+                         "include/aslam.h"],
                   "3d": ["paper_2603_25834_gb300/csrc/step3d.cu",
                          "paper_2603_25834_gb300/csrc/aslam_internal.cuh",
-                         "paper_2603_25834_gb300/csrc/env_common.cuh"]}
+                         "paper_2603_25834_gb300/csrc/env_common.cuh",
+                         "include/aslam.h"]}
 
 
 def traffic_file(kernel, workload):
